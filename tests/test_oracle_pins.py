@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute-force
+sums, closed forms, a dense Kronecker solve, finite differences, textbook
+special cases, the paper's printed matrix and its operation-count tables.
+CPU only.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fctn_oracle as O
+from paper_2510_22506_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_factors(dims, R, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal(O.factor_shape(dims, R, k)) for k in range(len(dims))]
+
+
+def _Rmat(N, vals):
+    """Rank matrix from the upper-triangle list (R12, R13, ..., R_{N-1,N})."""
+    R = np.zeros((N, N), dtype=np.int64)
+    it = iter(vals)
+    for a in range(N):
+        for b in range(a + 1, N):
+            R[a, b] = R[b, a] = next(it)
+    return R
+
+
+# ---------------------------------------------------------------- P1 -----
+def _brute_fctn(factors, dims, R):
+    """Element-wise definition of the FCTN format: nested sums over every bond."""
+    N = len(dims)
+    bonds = [(a, b) for a in range(N) for b in range(a + 1, N)]
+    out = np.zeros(dims)
+    for idx in itertools.product(*[range(d) for d in dims]):
+        acc = 0.0
+        for rv in itertools.product(*[range(int(R[a, b])) for a, b in bonds]):
+            r = dict(zip(bonds, rv))
+            term = 1.0
+            for k in range(N):
+                sub = tuple(idx[k] if t == k else r[(min(k, t), max(k, t))] for t in range(N))
+                term *= factors[k][sub]
+            acc += term
+        out[idx] = acc
+    return out
+
+
+@pytest.mark.parametrize("dims,rvals", [((3, 4, 5), (2, 3, 2)), ((2, 3, 2, 3), (2,) * 6), ((3, 4), (3,))])
+def test_p1_fctn_matches_bruteforce(dims, rvals):
+    R = _Rmat(len(dims), rvals)
+    fs = _rand_factors(dims, R, 1)
+    ref = _brute_fctn(fs, dims, R)
+    got = O.fctn_full(fs)
+    assert got.shape == tuple(dims)
+    np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- P2 -----
+@pytest.mark.parametrize("dims,rvals", [((3, 4), (3,)), ((3, 4, 5), (2, 3, 2)), ((2, 3, 2, 3), (2, 3, 2, 2, 3, 2)),
+                                        ((2, 2, 3, 2, 2), (2,) * 10)])
+def test_p2_property1_every_mode(dims, rvals):
+    """Property 1: X_(k) = A_k(k) M_k for every k, for both merged-tensor routes."""
+    N = len(dims)
+    R = _Rmat(N, rvals)
+    fs = _rand_factors(dims, R, 2)
+    X = O.fctn_full(fs)
+    for k in range(N):
+        M = O.merged_matrix(O.merged_sequential(fs, k), dims, R, k)
+        assert M.shape == (O.s_k(dims, R, k), X.size // dims[k])
+        Xk = O.unfold_factor(fs[k], k) @ M
+        np.testing.assert_allclose(O.fold_tensor(Xk, dims, k), X, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(O.unfold_tensor(X, k), Xk, rtol=1e-12, atol=1e-12)
+        if N == 4:
+            (c, d), _ = O.pair_of(N, k)
+            T, Tl = O.pair_intermediate(fs, c, d)
+            M2 = O.merged_matrix(O.merged_from_pair(fs, k, T, Tl), dims, R, k)
+            np.testing.assert_allclose(M2, M, rtol=1e-12, atol=1e-12)
+
+
+def test_p2_fold_unfold_roundtrip_and_layout():
+    dims, R = (3, 4, 5), _Rmat(3, (2, 3, 2))
+    fs = _rand_factors(dims, R, 3)
+    for k in range(3):
+        A = fs[k]
+        Am = O.unfold_factor(A, k)
+        assert Am.shape == (dims[k], O.s_k(dims, R, k))
+        np.testing.assert_array_equal(O.fold_factor(Am, dims, R, k), A)
+    # A_2(2)[i2, (r12, r23)] = A_2[r12, i2, r23]: explicit index check
+    A = fs[1]
+    Am = O.unfold_factor(A, 1)
+    for i2, r12, r23 in itertools.product(range(4), range(2), range(2)):
+        assert Am[i2, r12 * 2 + r23] == A[r12, i2, r23]
+
+
+# ---------------------------------------------------------------- P3 -----
+@pytest.mark.parametrize("I", [1, 2, 3, 10, 30, 144])
+@pytest.mark.parametrize("sign", ["psd", "printed"])
+def test_p3_laplacian_closed_form_eigenvalues(I, sign):
+    delta = 0.5
+    L = O.laplacian(I, delta, sign)
+    np.testing.assert_array_equal(L, L.T)
+    ev = np.sort(np.linalg.eigvalsh(L))
+    mu = 2.0 + delta - 2.0 * np.cos(2.0 * np.pi * np.arange(I) / I)
+    if sign == "printed":
+        mu = -mu
+    np.testing.assert_allclose(ev, np.sort(mu), rtol=0, atol=1e-13)
+
+
+def test_p3_laplacian_printed_matrix_golden():
+    ref = np.loadtxt(os.path.join(GOLDEN, "laplacian_printed_delta0.5_I6.txt"))
+    np.testing.assert_array_equal(O.laplacian(6, 0.5, "printed"), ref)
+    np.testing.assert_array_equal(O.laplacian(6, 0.5, "psd"), -ref)
+
+
+# ---------------------------------------------------------------- P4 -----
+@pytest.mark.parametrize("sign", ["psd", "printed"])
+@pytest.mark.parametrize("I,s,P", [(5, 6, 20), (12, 9, 40), (1, 4, 7), (2, 3, 5)])
+def test_p4_eigen_route_equals_kronecker_solve(sign, I, s, P):
+    rng = np.random.default_rng(I * 100 + s)
+    M = rng.standard_normal((s, P))
+    Xk = rng.standard_normal((I, P))
+    A0 = rng.standard_normal((I, s))
+    lam, rho = 0.01, 0.1
+    L = O.laplacian(I, 0.5, sign)
+    G, Y = O.gram_rhs(Xk, M, A0, rho)
+    A = O.solve_factor(G, Y, L, lam, rho)
+    # Eq. (6): column-major vec, vec(L A) = (I_s kron L) vec A, vec(A G) = (G kron I_q) vec A
+    K = lam * np.kron(np.eye(s), L) + np.kron(G, np.eye(I)) + rho * np.eye(s * I)
+    vecA = np.linalg.solve(K, Y.reshape(-1, order="F"))
+    np.testing.assert_allclose(A, vecA.reshape(I, s, order="F"), rtol=1e-10, atol=1e-11)
+    # Eq. (5) residual
+    res = A @ G + lam * L @ A + rho * A - Y
+    assert np.linalg.norm(res) <= 1e-12 * np.linalg.norm(Y)
+
+
+def test_p4_singular_system_rejected():
+    """Printed sign with a large lambda makes T non-positive: reported, not solved."""
+    I, s = 6, 3
+    G = np.zeros((s, s))
+    L = O.laplacian(I, 0.5, "printed")
+    with pytest.raises(ValueError):
+        O.solve_factor(G, np.ones((I, s)), L, 1.0, 0.1)
+
+
+# ---------------------------------------------------------------- P5 -----
+def test_p5_x_update_keeps_observed_and_is_stationary():
+    rng = np.random.default_rng(5)
+    F = rng.standard_normal((7, 8, 9))
+    Xo = rng.standard_normal((7, 8, 9))
+    mask = rng.random((7, 8, 9)) < 0.3
+    rho = 0.1
+    Xn = O.x_update(F, Xo, mask, rho)
+    np.testing.assert_array_equal(Xn[mask], Xo[mask])
+    g = (Xn - F) + rho * (Xn - Xo)
+    assert np.max(np.abs(g[~mask])) < 1e-14
+
+
+# ---------------------------------------------------------------- P6 -----
+def _small_problem(dims, r, sign="psd", seed=11, lam=0.01, p=0.4):
+    truth, Y, mask, init, R = synth.workload_inputs(None, O.fctn_full, dims=dims, r=r, p=p, idx=seed, noise=0.0, cap=None)
+    prob = O.Problem(dims=dims, R=R, lam=(lam,) * len(dims), delta=(0.5,) * len(dims), rho=0.1, sign=sign)
+    return truth, Y, mask, init, prob
+
+
+@pytest.mark.parametrize("sign", ["psd", "printed"])
+@pytest.mark.parametrize("dims,r,reuse", [((8, 9, 5), 3, True), ((8, 9, 5), 3, False), ((5, 6, 3, 4), 2, True)])
+def test_p6_sufficient_decrease_every_block(sign, dims, r, reuse):
+    """Condition 4 of Theorem 2: f(new) + (rho/2)||Delta||^2 <= f(old) per block."""
+    _, Y, mask, init, prob = _small_problem(dims, r, sign)
+    st = O.init_state(Y, mask, init)
+    for _ in range(6):
+        info = O.pam_sweep(st, prob, reuse=reuse, policy=O.ORDER_ALTERNATE, trace_blocks=True)
+        for kind, k, f0, f1, d2 in info["blocks"]:
+            assert f1 + 0.5 * prob.rho * d2 <= f0 + 1e-10 * abs(f0), (kind, k, f0, f1, d2)
+
+
+def test_p6_relative_error_identity_by_finite_differences():
+    """Condition 5: grad_{A_k} f at the new block point = -rho (A_k^{t+1} - A_k^t).
+
+    The gradient is probed by central differences of the objective along
+    random directions (f is quadratic in one block, so they are exact up to
+    rounding).
+    """
+    dims, r = (6, 7, 4), 2
+    _, Y, mask, init, prob = _small_problem(dims, r)
+    st = O.init_state(Y, mask, init)
+    O.pam_sweep(st, prob)  # move away from the random start
+    N = len(dims)
+    Ls = [O.laplacian(dims[k], 0.5, "psd") for k in range(N)]
+    rng = np.random.default_rng(3)
+    for k in range(N):
+        Aold = st.factors[k].copy()
+        Mt = O.merged_sequential(st.factors, k)
+        Mk = O.merged_matrix(Mt, dims, prob.R, k)
+        G, Yr = O.gram_rhs(O.unfold_tensor(st.X, k), Mk, O.unfold_factor(Aold, k), prob.rho)
+        Anew = O.fold_factor(O.solve_factor(G, Yr, Ls[k], prob.lam[k], prob.rho), dims, prob.R, k)
+        for _ in range(3):
+            D = rng.standard_normal(Anew.shape)
+            h = 1e-3
+            fs_p = list(st.factors); fs_p[k] = Anew + h * D
+            fs_m = list(st.factors); fs_m[k] = Anew - h * D
+            fd = (O.objective(st.X, fs_p, Ls, prob.lam) - O.objective(st.X, fs_m, Ls, prob.lam)) / (2 * h)
+            pred = float(np.sum(-prob.rho * (Anew - Aold) * D))
+            scale = abs(O.objective(st.X, st.factors, Ls, prob.lam)) / h
+            assert abs(fd - pred) <= 1e-7 * max(1.0, abs(pred)) + 1e-12 * scale, (k, fd, pred)
+        st.factors[k] = Anew
+
+
+# ---------------------------------------------------------------- P7 -----
+def _golden_counts():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "table1_table2_counts.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        tab, alg, trange, centre, expr = line.split(None, 4)
+        rows.append((tab, int(alg), trange, centre, expr))
+    return rows
+
+
+def _eval(expr, I, R, N):
+    return eval(expr, {"log2": math.log2, "sum": sum, "range": range, "I": I, "R": R, "N": N})
+
+
+def _sweep_counts(N, I, R, reuse, policy, nsweeps):
+    dims = (I,) * N
+    Rm = _Rmat(N, (R,) * (N * (N - 1) // 2))
+    fs = _rand_factors(dims, Rm, 4)
+    Y = O.fctn_full(fs) * 0.01
+    mask = np.random.default_rng(0).random(dims) < 0.5
+    st = O.init_state(Y, mask, _rand_factors(dims, Rm, 5))
+    prob = O.Problem(dims=dims, R=Rm, lam=(0.01,) * N, delta=(0.5,) * N)
+    per = []
+    for _ in range(nsweeps):
+        before = dict(st.counter.counts)
+        O.pam_sweep(st, prob, reuse=reuse, policy=policy)
+        per.append({c: st.counter.counts[c] - before[c] for c in O.COST_CENTRES})
+    return per
+
+
+@pytest.mark.parametrize("I,R", [(4, 2), (5, 3)])
+def test_p7_table1_counts(I, R):
+    rows = [r for r in _golden_counts() if r[0] == "T1"]
+    alg1 = _sweep_counts(4, I, R, reuse=False, policy=O.ORDER_PLAIN, nsweeps=2)
+    alg2 = _sweep_counts(4, I, R, reuse=True, policy=O.ORDER_ALTERNATE, nsweeps=3)
+    for _, alg, trange, centre, expr in rows:
+        want = _eval(expr, I, R, 4)
+        got = alg1 if alg == 1 else alg2
+        ts = [0] if trange == "t=1" else ([1, 2] if trange == "t>=2" else range(len(got)))
+        for t in ts:
+            assert got[t][centre] == pytest.approx(want, rel=1e-12), (alg, t, centre)
+
+
+@pytest.mark.parametrize("N,I,R", [(3, 4, 2), (3, 6, 3), (4, 4, 2), (5, 3, 2)])
+def test_p7_table2_alg1_counts(N, I, R):
+    per = _sweep_counts(N, I, R, reuse=False, policy=O.ORDER_PLAIN, nsweeps=1)[0]
+    for tab, alg, _, centre, expr in _golden_counts():
+        if tab == "T2":
+            assert per[centre] == pytest.approx(_eval(expr, I, R, N), rel=1e-12), centre
+
+
+# ---------------------------------------------------------------- P8 -----
+@pytest.mark.parametrize("dims,r", [((30, 30, 10), 3), ((6, 7, 3, 5), 2)])
+@pytest.mark.parametrize("policy", [O.ORDER_PLAIN, O.ORDER_ALTERNATE])
+def test_p8_reuse_on_off_agree(dims, r, policy):
+    _, Y, mask, init, prob = _small_problem(dims, r, p=0.3)
+    a, _ = O.complete(Y, mask, init, prob, tol=0, max_sweeps=20, reuse=True, policy=policy)
+    b, _ = O.complete(Y, mask, init, prob, tol=0, max_sweeps=20, reuse=False, policy=policy)
+    assert np.linalg.norm(a.X - b.X) <= 1e-12 * np.linalg.norm(b.X)
+    for fa, fb in zip(a.factors, b.factors):
+        assert np.linalg.norm(fa - fb) <= 1e-12 * np.linalg.norm(fb)
+
+
+def test_p8_alternate_order_reuses_one_pair_per_sweep():
+    """Algorithm 2 with the alternating order builds two pairs at t=1 and one after."""
+    dims, r = (4, 5, 3, 4), 2
+    _, Y, mask, init, prob = _small_problem(dims, r)
+    st = O.init_state(Y, mask, init)
+    calls = []
+    orig = O.pair_intermediate
+
+    def spy(fs, c, d, counter=None):
+        calls.append((st.t, c, d))
+        return orig(fs, c, d, counter)
+
+    O.pair_intermediate = spy
+    try:
+        for _ in range(4):
+            O.pam_sweep(st, prob, reuse=True, policy=O.ORDER_ALTERNATE)
+    finally:
+        O.pair_intermediate = orig
+    per = [sum(1 for c in calls if c[0] == t) for t in range(4)]
+    assert per == [2, 1, 1, 1]
+
+
+# ---------------------------------------------------------------- P9 -----
+@pytest.mark.slow
+def test_p9_recovers_noise_free_low_rank_tensor():
+    """Noise-free FCTN-rank-3 tensor of size 30x30x10, SR 0.8, lambda 1e-4.
+
+    The truth is the contraction of the smoothed rank-3 factors divided by
+    its largest magnitude (a pure scaling keeps the FCTN rank; the min-max
+    recipe of the workloads adds a constant tensor, which raises every bond
+    rank by one).  No exactness theorem exists (Theorem 2 gives convergence
+    to a critical point only), so this is a sanity bound: at least two of
+    three seeds must reach a relative error below 1e-2 on the unobserved
+    entries within 1000 sweeps; all three are reported.
+    """
+    dims, r = (30, 30, 10), 3
+    errs = []
+    for seed in (21, 22, 23):
+        R = synth.rank_matrix(dims, r)
+        raw = O.fctn_full(synth.smoothed_factors(dims, R, 1000 + seed))
+        truth = raw / np.abs(raw).max()
+        mask = synth.bernoulli_mask(dims, 0.8, 2000 + seed)
+        Y = np.where(mask, truth, 0.0)
+        prob = O.Problem(dims=dims, R=R, lam=(1e-4,) * 3, delta=(0.5,) * 3, rho=0.1)
+        st, hist = O.complete(Y, mask, synth.init_factors(dims, R, 3000 + seed), prob, tol=1e-9, max_sweeps=1000)
+        e = np.linalg.norm((st.X - truth)[~mask]) / np.linalg.norm(truth[~mask])
+        errs.append((seed, len(hist), float(e)))
+    assert sum(e < 1e-2 for _, _, e in errs) >= 2, errs
+
+
+# ---------------------------------------------------------------- P10 ----
+def test_p10_two_factor_lambda0_is_proximal_ridge():
+    """N = 2, lambda = 0: the factor update is ridge regression (textbook)."""
+    rng = np.random.default_rng(9)
+    dims = (9, 11)
+    R = _Rmat(2, (4,))
+    fs = _rand_factors(dims, R, 6)
+    X = rng.standard_normal(dims)
+    rho = 0.1
+    for k in range(2):
+        Mk = O.merged_matrix(O.merged_sequential(fs, k), dims, R, k)
+        B = fs[1] if k == 0 else fs[0].T          # the other factor as an s x P matrix
+        np.testing.assert_array_equal(Mk, B)
+        Ak = O.unfold_factor(fs[k], k)
+        Xk = O.unfold_tensor(X, k)
+        G, Y = O.gram_rhs(Xk, Mk, Ak, rho)
+        got = O.solve_factor(G, Y, O.laplacian(dims[k], 0.5), 0.0, rho)
+        ridge = np.linalg.solve((B @ B.T + rho * np.eye(B.shape[0])).T, (Xk @ B.T + rho * Ak).T).T
+        np.testing.assert_allclose(got, ridge, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------- misc ---
+def test_psnr_definition_hand_case():
+    truth = np.zeros((4, 4, 2))
+    X = truth.copy()
+    X[:, :, 0] += 0.1          # slice MSE 0.01 -> 20 dB
+    # slice 1 exact -> floor 1e-12 -> 120 dB
+    assert O.psnr(X, truth) == pytest.approx((20.0 + 120.0) / 2)
+
+
+def test_do_while_runs_at_least_one_sweep_and_caps():
+    dims, r = (6, 5, 4), 2
+    _, Y, mask, init, prob = _small_problem(dims, r)
+    st, hist = O.complete(Y, mask, init, prob, tol=1e9, max_sweeps=10)
+    assert len(hist) == 1
+    st, hist = O.complete(Y, mask, init, prob, tol=0, max_sweeps=7)
+    assert len(hist) == 7 and st.t == 7
