@@ -1,0 +1,345 @@
+"""Benchmark: PAM sweeps/s of trace-regularized FCTN completion on GB300.
+
+One step = one PAM sweep (every factor update of Eqs. 4-9 in the current
+order, then the X update of Eq. 10) over the full workload, inputs resident
+in device memory.  Default workload: 256 x 256 x 31 (multispectral-shaped),
+all FCTN ranks 8, Bernoulli(0.1) mask, 0.01 noise, lambda = 0.01, rho = 0.1,
+plain FP32 path.  X is 8 MB, smaller than L2, so L2 is flushed (a 256 MB
+write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c2] [--precision fp32]
+
+Under torchrun every rank runs an independent replica on its own GPU (the
+method has no data-path exchange: replicas only), value = all ranks' sweeps /
+max-over-ranks time.  `--impl reference` times the FP64 CPU oracle on the same
+workload (one oracle sweep per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_22506_gb300 import synth  # noqa: E402
+
+METRIC = "PAM sweeps/s & time-to-tol, mixed-prec+served vs plain FP32 on 1 GB300; p50/p99"
+UNIT = "sweeps/s"
+DESC = {
+    "c1": "30x30x10 FCTN rank 3, SR 0.3, FP64 parity workload",
+    "c2": "256x256x31 multispectral-shaped, FCTN rank 8, SR 0.1, noise 0.01",
+    "c3": "144x176x3x50 colour-video-shaped, FCTN rank 6 (3 on the colour mode), SR 0.05",
+    "c4": "256x256x31x8 multispectral sequence, FCTN rank 6, SR 0.1",
+}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maximum SM clock
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def gpu_inputs(F, name):
+    """Workload inputs; the ground-truth contraction runs on the library's own path."""
+    w = synth.WORKLOADS[name]
+    dims = tuple(w["dims"])
+
+    def contract(fs):
+        R = synth.rank_matrix(dims, w["r"], w["cap"])
+        p = F.make_params(dims, R, precision="fp64", reuse=False)
+        h = F.fctn_create(p)
+        try:
+            F.fctn_set_factors(h, [np.ascontiguousarray(a) for a in fs])
+            out = np.empty(dims, dtype=np.float64)
+            F.fctn_contract(h, out)
+        finally:
+            F.fctn_destroy(h)
+        return out
+
+    return synth.workload_inputs(name, contract)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2510_22506_gb300 import fctn as F
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = args.workload
+    w = synth.WORKLOADS[name]
+    truth, Y, mask, init, R = gpu_inputs(F, name)
+    N = len(w["dims"])
+    precision = args.precision
+    p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=precision,
+                      reuse=True, order_policy="alternate")
+    dt = F.elem_dtype(p)
+    torch_dt = torch.float64 if dt == np.float64 else torch.float32
+    stream = torch.cuda.Stream(device=dev)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y.astype(dt))).to(dev)
+    Md = torch.from_numpy(mask.astype(np.uint8)).to(dev)
+    initd = [torch.from_numpy(np.ascontiguousarray(a.astype(dt))).to(dev) for a in init]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    torch.cuda.synchronize()
+    h = F.fctn_create(p, stream)
+    try:
+        F.fctn_set_data(h, Yd, Md)
+        F.fctn_set_factors(h, initd)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                F.fctn_pam_sweep(h, 1, want_stats=False)
+                flush.zero_()
+        torch.cuda.synchronize()
+        # ---- timed region: K sweeps, L2 flushed between them (outside the events)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = F.fctn_launch_count(h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                ev[i][0].record(stream)
+                F.fctn_pam_sweep(h, 1, want_stats=False)
+                ev[i][1].record(stream)
+                flush.zero_()
+        torch.cuda.synchronize()
+        launches = F.fctn_launch_count(h) - l0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = float(sum(step_ms))
+        if ws > 1:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+        clk = clocks.stop()
+        st = F.fctn_pam_sweep(h, 0)
+        # ---- dominant kernel class: quick per-class pass, then K profiled eager sweeps
+        per_class = {}
+        with torch.cuda.stream(stream):
+            for cls in F.KC:
+                F.fctn_profile(h, cls)
+                for _ in range(2):
+                    F.fctn_pam_sweep(h, 1, want_stats=False)
+                    flush.zero_()
+                per_class[cls] = F.fctn_profile_read(h)
+        dom = max(per_class, key=lambda c: per_class[c]["ms"])
+        F.fctn_profile(h, dom)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                F.fctn_pam_sweep(h, 1, want_stats=False)
+                F.fctn_profile_read(h)
+                flush.zero_()
+        prof = F.fctn_profile_read(h)
+        F.fctn_profile(h, None)
+        # ---- end to end through the C ABI with host buffers
+        e2e_sweeps = 10
+        Yh = np.ascontiguousarray(Y.astype(dt))
+        Mh = np.ascontiguousarray(mask.astype(np.uint8))
+        inith = [np.ascontiguousarray(a.astype(dt)) for a in init]
+        Xh = np.empty(Y.shape, dtype=dt)
+        e2e_times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F.fctn_set_data(h, Yh, Mh)
+            F.fctn_set_factors(h, inith)
+            F.fctn_pam_sweep(h, e2e_sweeps, want_stats=False)
+            F.fctn_get_X(h, Xh)
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_s = min(e2e_times)
+        h2d = Yh.nbytes + Mh.nbytes + sum(a.nbytes for a in inith)
+        d2h = Xh.nbytes
+    finally:
+        F.fctn_destroy(h)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    value = args.steps * ws / (total_ms / 1e3)
+    peaks, peak_src = load_peaks()
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    if dom in ("gram", "merged", "solve", "eig") and prof["flops"] > 0:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = prof["flops"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS if dt == np.float32 else 1.25
+        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if dt == np.float32 else "nominal FP64"
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = prof["bytes"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        peak_note = f"{peak_src} HBM copy bandwidth"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if dt == np.float32 else "f64", "data": "synthetic",
+        "config": {"workload": f"{name}: {DESC[name]}", "dims": list(w["dims"]), "rank": w["r"], "sampling": w["p"],
+                   "precision": precision, "reuse": True, "order_policy": "alternate", "lambda": synth.LAMBDA,
+                   "delta": synth.DELTA, "rho": synth.RHO, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{ws}", "graphs": True},
+        "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
+        "rel_change_last": st["rel_change"], "eig_sweeps_last": st["eig_sweeps"],
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": {"kernel_class": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "peak_source": peak_note, "traffic": None,
+                     "avg_launch_us": avg_ms * 1e3, "launches": prof["launches"],
+                     "measured": "CUDA events around each launch of the class, second timed pass of K eager sweeps",
+                     "class_ms_2sweeps": {c: round(v["ms"], 4) for c, v in per_class.items()}},
+        "e2e": {"value": e2e_sweeps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "step": f"set_data + set_factors from host, {e2e_sweeps} sweeps, X back to host"},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def oracle_setup(name):
+    from oracle import fctn_oracle as O
+    truth, Y, mask, init, R = synth.workload_inputs(name, O.fctn_full)
+    N = Y.ndim
+    prob = O.Problem(dims=Y.shape, R=R, lam=(synth.LAMBDA,) * N, delta=(synth.DELTA,) * N, rho=synth.RHO)
+    return O, O.init_state(Y, mask, init), prob
+
+
+def cpu_baseline(name, budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample."""
+    O, st, prob = oracle_setup(name)
+    O.pam_sweep(st, prob)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.pam_sweep(st, prob)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full sweeps of workload {name} after one warm-up sweep ({el:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    O, st, prob = oracle_setup(args.workload)
+    for _ in range(args.warmup):
+        O.pam_sweep(st, prob)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.pam_sweep(st, prob)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    w = synth.WORKLOADS[args.workload]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {DESC[args.workload]}", "dims": list(w["dims"]), "rank": w["r"],
+                   "sampling": w["p"], "precision": "fp64 (CPU oracle)", "reuse": True,
+                   "order_policy": "alternate"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{args.steps} full sweeps of workload {args.workload}, one per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(DESC))
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * libfctn — GB300 (sm_103a) trace-regularized FCTN completion, PAM sweep.
+ *
+ * C ABI.  Every entry point returns an int status (FCTN_OK = 0 on success);
+ * no C++ exception crosses this boundary.  After a failure,
+ * fctn_last_error() returns a message for the calling thread.
+ *
+ * The method (arXiv 2510.22506): an N-th order tensor X (I_1 x ... x I_N) is
+ * modelled as FCTN({A_k}) with factors
+ *     A_k : R_{1,k} x ... x R_{k-1,k} x I_k x R_{k,k+1} x ... x R_{k,N}
+ * (FCTN format, Sec. 1; Definitions 1-3 and Property 1, Sec. 2.2), and
+ *     min 1/2 ||X - FCTN(A)||_F^2 + sum_k lambda_k/2 tr(A_k(k)^T L_k A_k(k))
+ *     s.t. P_Omega(X - Y) = 0                                    (Eq. 1/2)
+ * is solved by proximal alternating minimisation (scheme 3): each factor is
+ * the solution of the Sylvester system of Eq. 5, solved through the
+ * eigenbases of L_k and of the Gram M_k M_k^T (Eqs. 7-9), then X is updated
+ * in closed form (Eq. 10).  Algorithm 2 adds intermediate-tensor reuse and a
+ * permuted update order (Sec. 3.3).
+ *
+ * Layout: all tensors are dense row-major (C order).  X and Y have shape
+ * (I_1, ..., I_N).  Factor k has the shape above (A_k's own mode at position
+ * k).  The observation mask is one byte per element of X (non-zero =
+ * observed).  Element type is double for FCTN_FP64 and float otherwise.
+ *
+ * Pointers: each data-passing call takes a `where` argument:
+ * FCTN_HOST (pageable or pinned host memory) or FCTN_DEVICE (device memory
+ * on the handle's device).  The caller owns every buffer it passes; the
+ * library copies inputs into its own device-resident state (factors, X,
+ * mask, intermediate tensors, workspaces), which it owns until
+ * fctn_destroy().  Results are written to caller-owned buffers.
+ *
+ * Concurrency: a handle is not thread-safe.  Distinct handles may be used
+ * concurrently from different threads and streams.  All work of a handle is
+ * ordered on the stream given at creation (NULL = the legacy default stream).
+ */
+#ifndef FCTN_H
+#define FCTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FCTN_MAX_ORDER 8
+
+/* status codes */
+enum {
+  FCTN_OK = 0,
+  FCTN_E_ARG = 1,        /* invalid argument (sizes, ranks, pointers, flags)            */
+  FCTN_E_OOM = 2,        /* device allocation failed                                    */
+  FCTN_E_SINGULAR = 3,   /* min_ij T_ij <= 0: Eq. 5 has no unique solution this way     */
+  FCTN_E_NONFINITE = 4,  /* NaN/Inf appeared in the stop-test reductions                */
+  FCTN_E_TIMEOUT = 5,    /* a bounded device-side wait or iteration limit ran out       */
+  FCTN_E_CUDA = 6,       /* a CUDA runtime call failed                                  */
+  FCTN_E_STATE = 7,      /* call out of order (e.g. sweep before data was set)          */
+  FCTN_E_UNSUPPORTED = 8 /* valid request that this build does not implement            */
+};
+
+/* arithmetic of the contractions (merged tensors, Gram, right-hand side, X update) */
+enum {
+  FCTN_FP64 = 0,  /* everything in double: the parity path                             */
+  FCTN_FP32 = 1,  /* plain single precision on the CUDA cores                          */
+  FCTN_TF32 = 2,  /* tcgen05 TF32 contractions, FP32 accumulation                      */
+  FCTN_BF16 = 3   /* tcgen05 BF16 contractions, FP32 accumulation                      */
+};
+
+/* update-order policy of Algorithm 2 ("unordered permutation" of the factors) */
+enum {
+  FCTN_ORDER_PLAIN = 0,     /* (1, ..., N) every sweep (Algorithm 1's order)                */
+  FCTN_ORDER_ALTERNATE = 1  /* N = 4: odd sweeps (1,2,3,4), even sweeps (3,4,1,2); else plain */
+};
+
+/* sign of the periodically modified negative Laplacian L_k (Sec. 3.1) */
+enum {
+  FCTN_LAPLACIAN_PSD = 0,     /* diagonal 2+delta, cyclic neighbours -1 (positive definite) */
+  FCTN_LAPLACIAN_PRINTED = 1  /* diagonal -2-delta, cyclic neighbours +1 (as printed)       */
+};
+
+enum { FCTN_HOST = 0, FCTN_DEVICE = 1 };
+
+typedef struct fctn_params {
+  int32_t order;                                  /* N, 2 <= N <= FCTN_MAX_ORDER       */
+  int32_t precision;                              /* FCTN_FP64 / FP32 / TF32 / BF16    */
+  int32_t reuse;                                  /* 1 = Algorithm 2 reuse, 0 = Alg. 1 */
+  int32_t order_policy;                           /* FCTN_ORDER_*                      */
+  int32_t laplacian_sign;                         /* FCTN_LAPLACIAN_*                  */
+  int32_t refine_steps;                           /* Sylvester refinement steps (>= 0) */
+  int64_t dims[FCTN_MAX_ORDER];                   /* I_1 .. I_N                        */
+  int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  /* R_{a,b}; only a < b is read       */
+  double lambda[FCTN_MAX_ORDER];                  /* lambda_k > 0 (Eq. 1)              */
+  double delta[FCTN_MAX_ORDER];                   /* delta_k > 0 (L_k)                 */
+  double rho;                                     /* proximal weight rho > 0 (Eq. 3)   */
+} fctn_params;
+
+typedef struct fctn_stats {
+  int64_t t;          /* completed sweeps since fctn_set_data / fctn_set_factors              */
+  double rel_change;  /* ||X^{t} - X^{t-1}||_F / ||X^{t-1}||_F of the last sweep               */
+  double objective;   /* Eq. 2 value after the last sweep (indicator term is 0 on D)          */
+  double data_term;   /* 1/2 ||X - FCTN(A)||_F^2 after the last sweep                         */
+  int32_t converged;  /* fctn_complete: 1 if rel_change <= tol was reached                    */
+  int32_t status;     /* FCTN_OK or the error that stopped the run                             */
+  int32_t eig_sweeps; /* Jacobi sweeps of the Gram eigensolver, max over the last sweep's k    */
+  int32_t reserved;
+} fctn_stats;
+
+typedef struct fctn_handle fctn_handle;
+
+/* Message of the calling thread's last failure (always NUL-terminated, may be
+ * truncated to n bytes).  Returns the full message length. */
+size_t fctn_last_error(char* buf, size_t n);
+
+/* Library version string (static storage). */
+const char* fctn_version(void);
+
+/* Device bytes a handle with these parameters allocates (admission control).
+ * Pure host arithmetic, no GPU needed. */
+int fctn_footprint_bytes(const fctn_params* p, size_t* out_bytes);
+
+/* Validate p, allocate the device state on the current device, build the
+ * L_k eigenbases (Eq. 7, closed form of a symmetric circulant) and bind the
+ * handle to `cuda_stream` (a cudaStream_t; NULL = legacy default stream). */
+int fctn_create(const fctn_params* p, void* cuda_stream, fctn_handle** out);
+
+/* Copy in the observed tensor Y and the mask Omega and set X^(1) = P_Omega(Y)
+ * (Algorithms 1/2, Initialize).  Resets t, the reuse cache and the order
+ * schedule.  Y: prod(dims) elements; mask: prod(dims) bytes. */
+int fctn_set_data(fctn_handle* h, const void* Y, const uint8_t* mask, int where);
+
+/* Copy in the factors A_k (array of N pointers, factor k in its FCTN shape).
+ * Resets t, the reuse cache and the order schedule. */
+int fctn_set_factors(fctn_handle* h, const void* const* factors, int where);
+
+/* FCTN({A_k}) of the current factors into `out` (prod(dims) elements);
+ * the contraction of the FCTN format (Sec. 1) from scratch. */
+int fctn_contract(fctn_handle* h, void* out, int where);
+
+/* Run `nsweeps` PAM sweeps (each: every factor update of Eqs. 4-9 in the
+ * current order, then the X update of Eq. 10).  `stats` (may be NULL)
+ * receives the state after the last sweep; this synchronises the stream. */
+int fctn_pam_sweep(fctn_handle* h, int nsweeps, fctn_stats* stats);
+
+/* Sweep until rel_change <= tol (after at least one sweep) or until the
+ * handle has done max_sweeps sweeps in total; then copy X into out_X (may be
+ * NULL).  tol <= 0 runs exactly up to max_sweeps. */
+int fctn_complete(fctn_handle* h, double tol, int max_sweeps, void* out_X, int where, fctn_stats* stats);
+
+/* Copy factor k (FCTN shape) / the completed tensor X out. */
+int fctn_get_factor(fctn_handle* h, int k, void* out, int where);
+int fctn_get_X(fctn_handle* h, void* out, int where);
+
+/* Synchronise the handle's stream. */
+int fctn_sync(fctn_handle* h);
+
+/* Count of kernel launches the handle has issued so far (instrumentation). */
+int fctn_launch_count(fctn_handle* h, int64_t* out);
+
+/* Capture each distinct sweep as a CUDA graph and replay it (default: on).
+ * With graphs off every kernel is launched individually. */
+int fctn_set_graphs(fctn_handle* h, int enable);
+
+/* Kernel classes for profiling. */
+enum {
+  FCTN_KC_MERGED = 0,   /* pair intermediates / merged tensors M_k (contractions)      */
+  FCTN_KC_GRAM = 1,     /* Gram + right-hand side, split over the columns of M_k        */
+  FCTN_KC_REDUCE = 2,   /* fixed-order reduction of the split partials                  */
+  FCTN_KC_EIG = 3,      /* Gram eigendecomposition                                      */
+  FCTN_KC_SOLVE = 4,    /* Eq. 8 solve and its FP64 refinement                          */
+  FCTN_KC_XUPDATE = 5,  /* X update of Eq. 10 fused with F = A_k(k) M_k and the sums    */
+  FCTN_KC_MISC = 6,     /* trace terms, finalisation, staging                           */
+  FCTN_KC_COUNT = 7
+};
+
+/* Time every launch of one kernel class with CUDA events recorded on the
+ * handle's stream (kernel_class = -1 turns it off).  Resets the counters.
+ * While profiling is on, sweeps run without graphs. */
+int fctn_profile(fctn_handle* h, int kernel_class);
+
+/* Synchronise and report, since fctn_profile(): launches of the class, their
+ * summed event time, and their algorithmic bytes and flops (what the method
+ * must move / compute for those launches, not hardware counters). */
+int fctn_profile_read(fctn_handle* h, int64_t* launches, double* ms, double* alg_bytes, double* alg_flops);
+
+int fctn_destroy(fctn_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCTN_H */

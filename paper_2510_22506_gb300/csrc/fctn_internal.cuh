@@ -1,0 +1,123 @@
+// Internal declarations shared by the libfctn translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "fctn.h"
+
+#define FCTN_MAXD 16  // digits of a contraction plan's output index
+#define FCTN_MAXC 8   // digits of its contracted index
+#define FCTN_CON_TABLE 4096  // contracted-index offsets kept in shared memory
+
+// Index plan of one tensor contraction (Definition 3): the output is dense
+// row-major over `out_ext`; each output digit walks operand A with `a_str`
+// and operand B with `b_str` (0 = not present); the contracted digits walk
+// A with `ca_str` and B with `cb_str`.  B == nullptr turns the kernel into a
+// permute (generalized transposition, Definition 1).
+struct ContractPlan {
+  int nout, ncon;
+  int64_t out_ext[FCTN_MAXD];
+  int64_t a_str[FCTN_MAXD], b_str[FCTN_MAXD];
+  int64_t con_ext[FCTN_MAXC];
+  int64_t ca_str[FCTN_MAXC], cb_str[FCTN_MAXC];
+  int64_t out_size, con_size;
+};
+
+// View of X_(k) as (pre, I_k, post): element (i, j) with j = a*post + b sits at
+// a*I_k*post + i*post + b.
+struct ModeView {
+  int64_t pre, I, post;
+};
+
+// Split-K contraction D = M [M ; X_(k)]^T (Gram block then RHS block).
+struct GramPlan {
+  int64_t s, I, Pk;     // M: s x Pk row-major; X_(k): I x Pk through `xv`
+  ModeView xv;
+  int64_t ncols;        // s + I
+  int tiles_r, tiles_c; // 64 x 64 output tiles
+  int ksplit;           // number of K chunks
+  int64_t kchunk;       // columns of M per chunk (multiple of 32)
+};
+
+// Pair form of a merged tensor (see kernels_fused.cu):
+//   M[sigma, j] = sum_kappa L[loff(j) + lo[sigma] + lk[kappa]] * R[roff(j) + ro[sigma] + rk[kappa]]
+// j is decoded row-major over `ext` (the modes t != k, ascending); each digit
+// adds `lstr` (`rstr`) elements to loff (roff).  tab = {lo[s], ro[s], lk[K], rk[K]}.
+struct PairPlan {
+  int nd;
+  int64_t ext[FCTN_MAX_ORDER];
+  int64_t lstr[FCTN_MAX_ORDER], rstr[FCTN_MAX_ORDER];
+  int Ljs, Rjs;  // row lengths of L and R (elements staged per column)
+  int K;         // contracted length
+  const int* tab;
+};
+
+// ---- kernels_fused.cu -------------------------------------------------------
+void launch_gram_fused_f32(const PairPlan& p, const float* L, const float* R, const float* X, float* part,
+                           const GramPlan& g, float* Mout, cudaStream_t st);
+void launch_gram_fused_f64(const PairPlan& p, const double* L, const double* R, const double* X, double* part,
+                           const GramPlan& g, double* Mout, cudaStream_t st);
+void launch_xupdate_fused_f32(const PairPlan& p, const float* L, const float* R, const float* Ak, float* X,
+                              const uint32_t* bits, double rho, const GramPlan& g, double* red, cudaStream_t st);
+void launch_xupdate_fused_f64(const PairPlan& p, const double* L, const double* R, const double* Ak, double* X,
+                              const uint32_t* bits, double rho, const GramPlan& g, double* red, cudaStream_t st);
+size_t gram_fused_smem(const PairPlan& p, int s, int bk, int elem);
+int gram_fused_bk(const PairPlan& p, int s, int elem);
+size_t xupdate_fused_smem(const PairPlan& p, int s, int cb, int elem);
+int xupdate_fused_cb(const PairPlan& p, int s, int elem);
+
+// ---- kernels_contract.cu ---------------------------------------------------
+void launch_contract_f32(const float* A, const float* B, float* out, const ContractPlan& p, cudaStream_t s);
+void launch_contract_f64(const double* A, const double* B, double* out, const ContractPlan& p, cudaStream_t s);
+void launch_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* Lam, cudaStream_t s);
+void launch_init_x_mask_f32(const float* Y, const uint8_t* mask, float* X, uint32_t* bits, int64_t n, cudaStream_t s);
+void launch_init_x_mask_f64(const double* Y, const uint8_t* mask, double* X, uint32_t* bits, int64_t n, cudaStream_t s);
+void launch_convert_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+void launch_convert_f32_to_f64(const float* in, double* out, int64_t n, cudaStream_t s);
+
+// ---- kernels_gram.cu -------------------------------------------------------
+// Sum the ksplit partials in a fixed order; write G (s x s), Y = Yraw + rho*A_old
+// (I x s) in double and, if Gs/Ys are non-null, single-precision copies.
+void launch_reduce_gram_rhs_f32(const float* partials, const GramPlan& g, const double* A_old, double rho,
+                                double* Gd, double* Yd, float* Gs, float* Ys, cudaStream_t s);
+void launch_reduce_gram_rhs_f64(const double* partials, const GramPlan& g, const double* A_old, double rho,
+                                double* Gd, double* Yd, cudaStream_t s);
+// X update of Eq. 10 fused with F = A_(k) M (reuse path): writes X in place and
+// per-block FP64 partial sums {||dX||^2, ||X_old||^2, ||X_new - F||^2}.
+int xupdate_blocks(const GramPlan& g);
+void launch_xupdate_f32(const float* Ak, const float* M, float* X, const uint32_t* bits, double rho,
+                        const GramPlan& g, double* red, cudaStream_t s);
+void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint32_t* bits, double rho,
+                        const GramPlan& g, double* red, cudaStream_t s);
+
+// ---- kernels_solve.cu ------------------------------------------------------
+// Symmetric eigendecomposition of the Gram by one-sided Jacobi (one CTA).
+// C (s x s, column j = eigenvector j) is read as the warm start when warm != 0
+// and overwritten with the result; Phi gets the eigenvalues.  work: 3 s^2.
+// *status: FCTN_E_SINGULAR if min Phi + tmin <= 0, FCTN_E_TIMEOUT if the
+// sweep limit ran out; *used: sweeps taken.
+void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
+                    double tmin, int* status, int* used, cudaStream_t st);
+void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
+                    double tmin, int* status, int* used, cudaStream_t st);
+// Eq. 8 by row blocks: Z = ((Q^T R) C) / T ; A = (Q Z) C^T into A64 (= or +=) and Ac.
+void launch_solve_a_f32(const float* Q, const float* R, const float* C, const double* LamL, const float* Phi,
+                        double lam, double rho, int I, int s, float* Z, cudaStream_t st);
+void launch_solve_a_f64(const double* Q, const double* R, const double* C, const double* LamL, const double* Phi,
+                        double lam, double rho, int I, int s, double* Z, cudaStream_t st);
+void launch_solve_b_f32(const float* Q, const float* Z, const float* C, int I, int s, int accumulate, double* A64,
+                        float* Ac, cudaStream_t st);
+void launch_solve_b_f64(const double* Q, const double* Z, const double* C, int I, int s, int accumulate, double* A64,
+                        double* Ac, cudaStream_t st);
+// FP64 residual of Eq. 5: R = Y - lam L A - rho A - A G (one CTA per row)
+void launch_resid_f32(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
+                      double c0, double c1, float* R, cudaStream_t st);
+void launch_resid_f64(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
+                      double c0, double c1, double* R, cudaStream_t st);
+// trace term lam/2 tr(A^T L A) for one factor (A: I x s double) -> out[0]
+void launch_trace_term(const double* A, int64_t I, int64_t s, double c0, double c1, double lam, double* out,
+                       cudaStream_t st);
+// finalize: stats[0]=rel, [1]=objective, [2]=data term, [3]=nonfinite flag
+void launch_finalize(const double* red, int nblocks, const double* traces, int N, double* stats, cudaStream_t st);

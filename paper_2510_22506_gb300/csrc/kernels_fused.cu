@@ -1,0 +1,325 @@
+// Merged tensor formed on chip, fused into its two consumers (CUDA-core path).
+//
+// Every merged tensor the sweep needs is the contraction of two operands,
+// M_k[sigma, j] = sum_kappa L[row_L(j), lo(sigma) + lk(kappa)] * R[row_R(j), ro(sigma) + rk(kappa)]
+// (Property 1; N = 3: L = A_a, R = A_b; N = 4 with reuse: L = A_b, R = the
+// cached pair intermediate T_cd of Algorithm 2; N = 2: R is the constant 1).
+// A chunk of columns j is formed into shared memory and consumed at once:
+//   gram_fused:    D = M_k [M_k ; X_(k)]^T partials (Gram and right-hand side
+//                  of Eq. 5), optionally writing M_k out (the merged tensor
+//                  of the factor updated last, reused by the X update).
+//   xupdate_fused: F = A_k(k) M_k and the masked proximal update of Eq. 10.
+#include "fctn_internal.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ void decode_col(const PairPlan& p, int64_t j, int64_t& lo, int64_t& ro) {
+  lo = 0;
+  ro = 0;
+  for (int d = p.nd - 1; d >= 0; --d) {
+    int64_t e = p.ext[d];
+    int64_t dig = j % e;
+    j /= e;
+    lo += dig * p.lstr[d];
+    ro += dig * p.rstr[d];
+  }
+}
+
+__device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j) {
+  uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
+  uint32_t a = jj / post, b = jj - a * post;
+  return ((int64_t)a * v.I + i) * v.post + b;
+}
+
+// Form Ms[jj * ldm + sigma] for jj in [0, nb) of columns starting at j0.
+// Slabs: Ls[jj * Ljs ...], Rs[jj * Rjs ...].  Tables in shared memory.
+template <typename T>
+__device__ __forceinline__ void form_tile(const PairPlan& p, const T* __restrict__ L, const T* __restrict__ R,
+                                          int64_t j0, int nb, int64_t Pk, T* Ls, T* Rs, int64_t* cl, int64_t* cr,
+                                          const int* lo, const int* ro, const int* lk, const int* rk, int s,
+                                          T* Ms, int ldm) {
+  const int tid = threadIdx.x;
+  for (int jj = tid; jj < nb; jj += NT) {
+    int64_t a = 0, b = 0;
+    if (j0 + jj < Pk) decode_col(p, j0 + jj, a, b);
+    cl[jj] = a;
+    cr[jj] = b;
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * p.Ljs; e += NT) {
+    int jj = e / p.Ljs, c = e - jj * p.Ljs;
+    Ls[e] = (j0 + jj < Pk) ? L[cl[jj] + c] : (T)0;
+  }
+  for (int e = tid; e < nb * p.Rjs; e += NT) {
+    int jj = e / p.Rjs, c = e - jj * p.Rjs;
+    Rs[e] = (j0 + jj < Pk) ? R[cr[jj] + c] : (T)0;
+  }
+  __syncthreads();
+  for (int e = tid; e < nb * s; e += NT) {
+    int jj = e / s, sg = e - jj * s;
+    const T* l = Ls + jj * p.Ljs + lo[sg];
+    const T* r = Rs + jj * p.Rjs + ro[sg];
+    T acc = 0;
+    for (int q = 0; q < p.K; ++q) acc = fma(l[lk[q]], r[rk[q]], acc);
+    Ms[jj * ldm + sg] = acc;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restrict__ L, const T* __restrict__ R,
+                                                   const T* __restrict__ X, T* __restrict__ part, GramPlan g, int BK,
+                                                   T* __restrict__ Mout) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int s = (int)g.s;
+  const int ldm = s + 1;
+  int* lo = (int*)sm;
+  int* ro = lo + s;
+  int* lk = ro + s;
+  int* rk = lk + p.K;
+  int64_t* cl = (int64_t*)(((uintptr_t)(rk + p.K) + 15) & ~(uintptr_t)15);
+  int64_t* cr = cl + BK;
+  T* Ls = (T*)(cr + BK);
+  T* Rs = Ls + (size_t)BK * p.Ljs;
+  T* Ms = Rs + (size_t)BK * p.Rjs;     // BK x ldm, Ms[kk*ldm + sigma]
+  T* Xs = Ms + (size_t)BK * ldm;       // BK x 64
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int e = tid; e < s; e += NT) {
+    lo[e] = p.tab[e];
+    ro[e] = p.tab[s + e];
+  }
+  for (int e = tid; e < p.K; e += NT) {
+    lk[e] = p.tab[2 * s + e];
+    rk[e] = p.tab[2 * s + p.K + e];
+  }
+  const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+  const int64_t kb = (int64_t)blockIdx.z * g.kchunk;
+  const int64_t ke = min(kb + g.kchunk, g.Pk);
+  const bool write_m = Mout != nullptr && blockIdx.x == 0 && blockIdx.y == 0;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  __syncthreads();
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    const int nb = (int)min((int64_t)BK, ke - k0);
+    form_tile<T>(p, L, R, k0, BK, ke, Ls, Rs, cl, cr, lo, ro, lk, rk, s, Ms, ldm);
+    if (write_m) {
+      for (int e = tid; e < s * nb; e += NT) {
+        int sg = e / nb, jj = e - sg * nb;
+        Mout[(int64_t)sg * g.Pk + k0 + jj] = Ms[jj * ldm + sg];
+      }
+    }
+    // X rows of this tile: X_(k)[c - s][j]
+    if (c0 + 64 > g.s) {
+      if (g.xv.post == 1) {
+        for (int e = tid; e < 64 * BK; e += NT) {
+          int c = e % 64, kk = e / 64;
+          int64_t col = c0 + c, j = k0 + kk;
+          Xs[kk * 64 + c] = (col >= g.s && col < g.ncols && kk < nb) ? X[j * g.xv.I + (col - g.s)] : (T)0;
+        }
+      } else {
+        for (int e = tid; e < 64 * BK; e += NT) {
+          int c = e / BK, kk = e % BK;
+          int64_t col = c0 + c, j = k0 + kk;
+          Xs[kk * 64 + c] = (col >= g.s && col < g.ncols && kk < nb) ? X[xaddr(g.xv, col - g.s, j)] : (T)0;
+        }
+      }
+    }
+    __syncthreads();
+    for (int kk = 0; kk < nb; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        int64_t row = r0 + ty * 4 + a;
+        av[a] = row < g.s ? Ms[kk * ldm + row] : (T)0;
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int64_t col = c0 + tx * 4 + b;
+        bv[b] = col < g.s ? Ms[kk * ldm + col] : Xs[kk * 64 + tx * 4 + b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  T* P = part + (int64_t)blockIdx.z * g.s * g.ncols;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t row = r0 + ty * 4 + a;
+    if (row >= g.s) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t col = c0 + tx * 4 + b;
+      if (col < g.ncols) P[row * g.ncols + col] = acc[a][b];
+    }
+  }
+}
+
+// F = A_(k) M_k over a 64 (rows i) x 64 (columns j) tile, M_k formed on chip
+// in column sub-chunks of CB, then Eq. 10 and the stop-test partial sums.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_xupdate_fused(PairPlan p, const T* __restrict__ L, const T* __restrict__ R,
+                                                      const T* __restrict__ Ak, T* __restrict__ X,
+                                                      const uint32_t* __restrict__ bits, double rho, GramPlan g,
+                                                      int CB, double* __restrict__ red) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int s = (int)g.s;
+  const int ldm = s + 1;
+  int* lo = (int*)sm;
+  int* ro = lo + s;
+  int* lk = ro + s;
+  int* rk = lk + p.K;
+  int64_t* cl = (int64_t*)(((uintptr_t)(rk + p.K) + 15) & ~(uintptr_t)15);
+  int64_t* cr = cl + CB;
+  T* Ls = (T*)(cr + CB);
+  T* Rs = Ls + (size_t)CB * p.Ljs;
+  T* Ms = Rs + (size_t)CB * p.Rjs;     // 64 x ldm (column jj, row sigma)
+  T* As = Ms + (size_t)64 * ldm;       // 64 x s  (row i, sigma)
+  __shared__ double sred[3][NT / 32];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int e = tid; e < s; e += NT) {
+    lo[e] = p.tab[e];
+    ro[e] = p.tab[s + e];
+  }
+  for (int e = tid; e < p.K; e += NT) {
+    lk[e] = p.tab[2 * s + e];
+    rk[e] = p.tab[2 * s + p.K + e];
+  }
+  const int64_t i0 = (int64_t)blockIdx.y * 64, j0 = (int64_t)blockIdx.x * 64;
+  for (int e = tid; e < 64 * s; e += NT) {
+    int r = e / s, sg = e - r * s;
+    As[e] = (i0 + r < g.I) ? Ak[(i0 + r) * g.s + sg] : (T)0;
+  }
+  __syncthreads();
+  for (int c = 0; c < 64; c += CB) form_tile<T>(p, L, R, j0 + c, CB, g.Pk, Ls, Rs, cl, cr, lo, ro, lk, rk, s,
+                                                Ms + (size_t)c * ldm, ldm);
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int sg = 0; sg < s; ++sg) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[(ty * 4 + a) * s + sg];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Ms[(tx * 4 + b) * ldm + sg];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+  const T r = (T)rho, inv = (T)(1.0 / (1.0 + rho));
+  T d2 = 0, x2 = 0, r2 = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t i = i0 + ty * 4 + a;
+    if (i >= g.I) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t j = j0 + tx * 4 + b;
+      if (j >= g.Pk) continue;
+      int64_t e = xaddr(g.xv, i, j);
+      T xo = X[e];
+      bool obs = (bits[e >> 5] >> (e & 31)) & 1u;
+      T f = acc[a][b];
+      T xn = obs ? xo : (f + r * xo) * inv;
+      X[e] = xn;
+      T d = xn - xo, q = xn - f;
+      d2 = fma(d, d, d2);
+      x2 = fma(xo, xo, x2);
+      r2 = fma(q, q, r2);
+    }
+  }
+  double v[3] = {(double)d2, (double)x2, (double)r2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double t = v[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((tid & 31) == 0) sred[q][tid >> 5] = t;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sred[tid][w];
+    int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    red[blk * 3 + tid] = t;
+  }
+}
+
+size_t head_bytes(const PairPlan& p, int s, int nb) {
+  size_t b = (size_t)(2 * s + 2 * p.K) * 4;
+  b = (b + 15) & ~(size_t)15;
+  return b + 2 * (size_t)nb * 8;
+}
+
+}  // namespace
+
+int gram_fused_bk(const PairPlan& p, int s, int elem) {
+  // columns per chunk: slabs + formed tile + X rows within ~100 KB
+  for (int bk = 32; bk >= 4; bk /= 2) {
+    size_t b = head_bytes(p, s, bk) + (size_t)bk * (p.Ljs + p.Rjs + s + 1 + 64) * elem;
+    if (b <= 100 * 1024) return bk;
+  }
+  return 4;
+}
+
+size_t gram_fused_smem(const PairPlan& p, int s, int bk, int elem) {
+  return head_bytes(p, s, bk) + (size_t)bk * (p.Ljs + p.Rjs + s + 1 + 64) * elem;
+}
+
+int xupdate_fused_cb(const PairPlan& p, int s, int elem) {
+  for (int cb = 32; cb >= 1; cb /= 2) {
+    size_t b = head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * (size_t)(s + 1) + 64 * (size_t)s) * elem;
+    if (b <= 200 * 1024) return cb;
+  }
+  return 1;
+}
+
+size_t xupdate_fused_smem(const PairPlan& p, int s, int cb, int elem) {
+  return head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * (size_t)(s + 1) + 64 * (size_t)s) * elem;
+}
+
+template <typename T>
+static void gram_fused(const PairPlan& p, const T* L, const T* R, const T* X, T* part, const GramPlan& g, T* Mout,
+                       cudaStream_t st) {
+  const int bk = gram_fused_bk(p, (int)g.s, sizeof(T));
+  const size_t sb = gram_fused_smem(p, (int)g.s, bk, sizeof(T));
+  cudaFuncSetAttribute(k_gram_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  dim3 grid(g.tiles_c, g.tiles_r, g.ksplit);
+  k_gram_fused<T><<<grid, NT, sb, st>>>(p, L, R, X, part, g, bk, Mout);
+}
+
+template <typename T>
+static void xupdate_fused(const PairPlan& p, const T* L, const T* R, const T* Ak, T* X, const uint32_t* bits,
+                          double rho, const GramPlan& g, double* red, cudaStream_t st) {
+  const int cb = xupdate_fused_cb(p, (int)g.s, sizeof(T));
+  const size_t sb = xupdate_fused_smem(p, (int)g.s, cb, sizeof(T));
+  cudaFuncSetAttribute(k_xupdate_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  dim3 grid((unsigned)((g.Pk + 63) / 64), (unsigned)((g.I + 63) / 64));
+  k_xupdate_fused<T><<<grid, NT, sb, st>>>(p, L, R, Ak, X, bits, rho, g, cb, red);
+}
+
+void launch_gram_fused_f32(const PairPlan& p, const float* L, const float* R, const float* X, float* part,
+                           const GramPlan& g, float* Mout, cudaStream_t st) {
+  gram_fused<float>(p, L, R, X, part, g, Mout, st);
+}
+void launch_gram_fused_f64(const PairPlan& p, const double* L, const double* R, const double* X, double* part,
+                           const GramPlan& g, double* Mout, cudaStream_t st) {
+  gram_fused<double>(p, L, R, X, part, g, Mout, st);
+}
+void launch_xupdate_fused_f32(const PairPlan& p, const float* L, const float* R, const float* Ak, float* X,
+                              const uint32_t* bits, double rho, const GramPlan& g, double* red, cudaStream_t st) {
+  xupdate_fused<float>(p, L, R, Ak, X, bits, rho, g, red, st);
+}
+void launch_xupdate_fused_f64(const PairPlan& p, const double* L, const double* R, const double* Ak, double* X,
+                              const uint32_t* bits, double rho, const GramPlan& g, double* red, cudaStream_t st) {
+  xupdate_fused<double>(p, L, R, Ak, X, bits, rho, g, red, st);
+}

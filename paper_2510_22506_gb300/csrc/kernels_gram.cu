@@ -1,0 +1,161 @@
+// Reduction of the split-K Gram / right-hand-side partials of Eq. 5, and the
+// X update of Eq. 10 from a materialised merged tensor (CUDA-core path).
+//
+// reduce:   every chunk of columns of M_k wrote its own partial of
+//           D = M_k [M_k ; X_(k)]^T; they are summed in a fixed order
+//           (deterministic: a rerun gives identical bytes).
+// xupdate:  F = A_k(k) M_k (the reuse path of Algorithm 2, where M_k is the
+//           merged tensor of the factor updated last, kept from its update)
+//           fused with the masked proximal update of Eq. 10 and the
+//           stop-test reductions.
+#include "fctn_internal.cuh"
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 32, NT = 256;
+
+__device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j) {
+  // j < 2^32 always (P_k = P / I_k with P < 2^40 and I_k >= 1 is checked on the host)
+  uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
+  uint32_t a = jj / post, b = jj - a * post;
+  return ((int64_t)a * v.I + i) * v.post + b;
+}
+
+template <typename T>
+__global__ void k_reduce_gram_rhs(const T* __restrict__ part, GramPlan g, const double* __restrict__ A_old,
+                                  double rho, double* __restrict__ Gd, double* __restrict__ Yd,
+                                  float* __restrict__ Gs, float* __restrict__ Ys) {
+  const int64_t total = g.s * g.ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    // fixed-order compensated (Kahan) sum in the partials' precision
+    T sum = 0, comp = 0;
+    for (int z = 0; z < g.ksplit; ++z) {
+      T y = part[(int64_t)z * total + e] - comp;
+      T t = sum + y;
+      comp = (t - sum) - y;
+      sum = t;
+    }
+    double acc = (double)sum;
+    int64_t row = e / g.ncols, col = e % g.ncols;
+    if (col < g.s) {
+      Gd[row * g.s + col] = acc;
+      if (Gs) Gs[row * g.s + col] = (float)acc;
+    } else {
+      int64_t i = col - g.s;
+      double y = acc + rho * A_old[i * g.s + row];
+      Yd[i * g.s + row] = y;
+      if (Ys) Ys[i * g.s + row] = (float)y;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_xupdate(const T* __restrict__ Ak, const T* __restrict__ M,
+                                                T* __restrict__ X, const uint32_t* __restrict__ bits, double rho,
+                                                GramPlan g, double* __restrict__ red) {
+  __shared__ T As[TK][TM + 4];
+  __shared__ T Bs[TK][TN + 4];
+  __shared__ double sred[3][NT / 32];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t i0 = (int64_t)blockIdx.y * TM;
+  const int64_t j0 = (int64_t)blockIdx.x * TN;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int64_t k0 = 0; k0 < g.s; k0 += TK) {
+    for (int e = tid; e < TM * TK; e += NT) {
+      int r = e / TK, kk = e % TK;
+      int64_t i = i0 + r, sg = k0 + kk;
+      As[kk][r] = (i < g.I && sg < g.s) ? Ak[i * g.s + sg] : (T)0;
+    }
+    for (int e = tid; e < TN * TK; e += NT) {
+      int c = e % TN, kk = e / TN;
+      int64_t j = j0 + c, sg = k0 + kk;
+      Bs[kk][c] = (j < g.Pk && sg < g.s) ? M[sg * g.Pk + j] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  const T r = (T)rho, inv = (T)(1.0 / (1.0 + rho));
+  T d2 = 0, x2 = 0, r2 = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int64_t i = i0 + ty * 4 + a;
+    if (i >= g.I) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t j = j0 + tx * 4 + b;
+      if (j >= g.Pk) continue;
+      int64_t e = xaddr(g.xv, i, j);
+      T xo = X[e];
+      bool obs = (bits[e >> 5] >> (e & 31)) & 1u;
+      T f = acc[a][b];
+      T xn = obs ? xo : (f + r * xo) * inv;
+      X[e] = xn;
+      T d = xn - xo, q = xn - f;
+      d2 = fma(d, d, d2);
+      x2 = fma(xo, xo, x2);
+      r2 = fma(q, q, r2);
+    }
+  }
+  double v[3] = {(double)d2, (double)x2, (double)r2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double t = v[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((tid & 31) == 0) sred[q][tid >> 5] = t;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sred[tid][w];
+    int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    red[blk * 3 + tid] = t;
+  }
+}
+
+unsigned rgrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 4) b = 152 * 4;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+void launch_reduce_gram_rhs_f32(const float* partials, const GramPlan& g, const double* A_old, double rho,
+                                double* Gd, double* Yd, float* Gs, float* Ys, cudaStream_t s) {
+  k_reduce_gram_rhs<float><<<rgrid(g.s * g.ncols), 256, 0, s>>>(partials, g, A_old, rho, Gd, Yd, Gs, Ys);
+}
+void launch_reduce_gram_rhs_f64(const double* partials, const GramPlan& g, const double* A_old, double rho,
+                                double* Gd, double* Yd, cudaStream_t s) {
+  k_reduce_gram_rhs<double><<<rgrid(g.s * g.ncols), 256, 0, s>>>(partials, g, A_old, rho, Gd, Yd, nullptr, nullptr);
+}
+int xupdate_blocks(const GramPlan& g) {
+  return (int)(((g.Pk + TN - 1) / TN) * ((g.I + TM - 1) / TM));
+}
+void launch_xupdate_f32(const float* Ak, const float* M, float* X, const uint32_t* bits, double rho,
+                        const GramPlan& g, double* red, cudaStream_t s) {
+  dim3 grid((unsigned)((g.Pk + TN - 1) / TN), (unsigned)((g.I + TM - 1) / TM));
+  k_xupdate<float><<<grid, NT, 0, s>>>(Ak, M, X, bits, rho, g, red);
+}
+void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint32_t* bits, double rho,
+                        const GramPlan& g, double* red, cudaStream_t s) {
+  dim3 grid((unsigned)((g.Pk + TN - 1) / TN), (unsigned)((g.I + TM - 1) / TM));
+  k_xupdate<double><<<grid, NT, 0, s>>>(Ak, M, X, bits, rho, g, red);
+}

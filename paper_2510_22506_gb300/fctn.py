@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libfctn.so (names follow the C ABI in include/fctn.h).
+
+Only argument marshalling lives here: every step of the completion runs in
+the library's CUDA kernels.  Arrays are accepted as NumPy arrays (host
+memory, passed as FCTN_HOST) or as CUDA torch tensors (device memory, passed
+as FCTN_DEVICE through ``data_ptr()``).  Importing this module raises if the
+library has not been built; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIBPATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfctn.so")
+if not os.path.exists(_LIBPATH):
+    raise ImportError(f"{_LIBPATH} is missing: build it with `python -m paper_2510_22506_gb300.build`")
+lib = ctypes.CDLL(_LIBPATH)
+
+MAX_ORDER = 8
+FCTN_OK, FCTN_E_ARG, FCTN_E_OOM, FCTN_E_SINGULAR, FCTN_E_NONFINITE, FCTN_E_TIMEOUT, FCTN_E_CUDA, \
+    FCTN_E_STATE, FCTN_E_UNSUPPORTED = range(9)
+FCTN_FP64, FCTN_FP32, FCTN_TF32, FCTN_BF16 = range(4)
+FCTN_ORDER_PLAIN, FCTN_ORDER_ALTERNATE = 0, 1
+FCTN_LAPLACIAN_PSD, FCTN_LAPLACIAN_PRINTED = 0, 1
+FCTN_HOST, FCTN_DEVICE = 0, 1
+
+PRECISIONS = {"fp64": FCTN_FP64, "fp32": FCTN_FP32, "tf32": FCTN_TF32, "bf16": FCTN_BF16}
+
+
+class fctn_params(ctypes.Structure):
+    _fields_ = [
+        ("order", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reuse", ctypes.c_int32),
+        ("order_policy", ctypes.c_int32),
+        ("laplacian_sign", ctypes.c_int32),
+        ("refine_steps", ctypes.c_int32),
+        ("dims", ctypes.c_int64 * MAX_ORDER),
+        ("ranks", (ctypes.c_int32 * MAX_ORDER) * MAX_ORDER),
+        ("lambda_", ctypes.c_double * MAX_ORDER),
+        ("delta", ctypes.c_double * MAX_ORDER),
+        ("rho", ctypes.c_double),
+    ]
+
+
+class fctn_stats(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_int64),
+        ("rel_change", ctypes.c_double),
+        ("objective", ctypes.c_double),
+        ("data_term", ctypes.c_double),
+        ("converged", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("eig_sweeps", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp, _i, _i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+lib.fctn_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+lib.fctn_last_error.restype = ctypes.c_size_t
+lib.fctn_version.restype = ctypes.c_char_p
+lib.fctn_footprint_bytes.argtypes = [ctypes.POINTER(fctn_params), ctypes.POINTER(ctypes.c_size_t)]
+lib.fctn_create.argtypes = [ctypes.POINTER(fctn_params), _vp, ctypes.POINTER(_vp)]
+lib.fctn_set_data.argtypes = [_vp, _vp, _vp, _i]
+lib.fctn_set_factors.argtypes = [_vp, ctypes.POINTER(_vp), _i]
+lib.fctn_contract.argtypes = [_vp, _vp, _i]
+lib.fctn_pam_sweep.argtypes = [_vp, _i, ctypes.POINTER(fctn_stats)]
+lib.fctn_complete.argtypes = [_vp, ctypes.c_double, _i, _vp, _i, ctypes.POINTER(fctn_stats)]
+lib.fctn_get_factor.argtypes = [_vp, _i, _vp, _i]
+lib.fctn_get_X.argtypes = [_vp, _vp, _i]
+lib.fctn_sync.argtypes = [_vp]
+lib.fctn_launch_count.argtypes = [_vp, _i64p]
+lib.fctn_destroy.argtypes = [_vp]
+lib.fctn_set_graphs.argtypes = [_vp, _i]
+lib.fctn_profile.argtypes = [_vp, _i]
+_dp = ctypes.POINTER(ctypes.c_double)
+lib.fctn_profile_read.argtypes = [_vp, _i64p, _dp, _dp, _dp]
+for _f in ("fctn_footprint_bytes", "fctn_create", "fctn_set_data", "fctn_set_factors", "fctn_contract",
+           "fctn_pam_sweep", "fctn_complete", "fctn_get_factor", "fctn_get_X", "fctn_sync", "fctn_launch_count",
+           "fctn_destroy", "fctn_set_graphs", "fctn_profile", "fctn_profile_read"):
+    getattr(lib, _f).restype = ctypes.c_int
+
+EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_create", "fctn_set_data",
+            "fctn_set_factors", "fctn_contract", "fctn_pam_sweep", "fctn_complete", "fctn_get_factor",
+            "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
+            "fctn_profile_read")
+KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
+
+
+class FctnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfctn error {code}: {msg}")
+        self.code = code
+
+
+def fctn_last_error():
+    buf = ctypes.create_string_buffer(1024)
+    lib.fctn_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc):
+    if rc != FCTN_OK:
+        raise FctnError(rc, fctn_last_error())
+
+
+def fctn_version():
+    return lib.fctn_version().decode()
+
+
+def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
+                laplacian_sign="psd", refine_steps=None):
+    """fctn_params from Python values; R is an N x N symmetric rank matrix."""
+    N = len(dims)
+    p = fctn_params()
+    p.order = N
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.reuse = int(bool(reuse))
+    p.order_policy = {"plain": 0, "alternate": 1}[order_policy] if isinstance(order_policy, str) else int(order_policy)
+    p.laplacian_sign = {"psd": 0, "printed": 1}[laplacian_sign] if isinstance(laplacian_sign, str) else int(laplacian_sign)
+    if refine_steps is None:
+        refine_steps = 0 if p.precision == FCTN_FP64 else 1
+    p.refine_steps = int(refine_steps)
+    lams = list(lam) if np.ndim(lam) else [lam] * N
+    dels = list(delta) if np.ndim(delta) else [delta] * N
+    for k in range(N):
+        p.dims[k] = int(dims[k])
+        p.lambda_[k] = float(lams[k])
+        p.delta[k] = float(dels[k])
+        for t in range(N):
+            if t != k:
+                p.ranks[min(k, t)][max(k, t)] = int(R[min(k, t)][max(k, t)])
+    p.rho = float(rho)
+    return p
+
+
+def elem_dtype(p):
+    return np.float64 if p.precision == FCTN_FP64 else np.float32
+
+
+def _ptr(a, dtype=None):
+    """(pointer, where) of a NumPy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(ctypes.c_void_p), FCTN_HOST
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), (FCTN_DEVICE if a.is_cuda else FCTN_HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def fctn_footprint_bytes(params):
+    out = ctypes.c_size_t(0)
+    _check(lib.fctn_footprint_bytes(ctypes.byref(params), ctypes.byref(out)))
+    return out.value
+
+
+def fctn_create(params, stream=None):
+    """Create a handle; ``stream`` is a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    h = ctypes.c_void_p()
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.fctn_create(ctypes.byref(params), sp, ctypes.byref(h)))
+    return h
+
+
+def fctn_set_data(h, Y, mask):
+    py, wy = _ptr(Y)
+    pm, wm = _ptr(mask)
+    if wy != wm:
+        raise ValueError("Y and mask must both be on the host or both on the device")
+    _check(lib.fctn_set_data(h, py, pm, wy))
+
+
+def fctn_set_factors(h, factors):
+    ptrs, where = [], None
+    for a in factors:
+        p, w = _ptr(a)
+        if where is not None and w != where:
+            raise ValueError("all factors must live in the same memory")
+        where = w
+        ptrs.append(p)
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    _check(lib.fctn_set_factors(h, arr, where))
+
+
+def fctn_contract(h, out):
+    p, w = _ptr(out)
+    _check(lib.fctn_contract(h, p, w))
+    return out
+
+
+def fctn_pam_sweep(h, nsweeps=1, want_stats=True):
+    st = fctn_stats()
+    _check(lib.fctn_pam_sweep(h, int(nsweeps), ctypes.byref(st) if want_stats else None))
+    return st.as_dict() if want_stats else None
+
+
+def fctn_complete(h, tol, max_sweeps, out_X=None):
+    st = fctn_stats()
+    if out_X is None:
+        rc = lib.fctn_complete(h, float(tol), int(max_sweeps), None, FCTN_HOST, ctypes.byref(st))
+    else:
+        p, w = _ptr(out_X)
+        rc = lib.fctn_complete(h, float(tol), int(max_sweeps), p, w, ctypes.byref(st))
+    _check(rc)
+    return st.as_dict()
+
+
+def fctn_get_factor(h, k, out):
+    p, w = _ptr(out)
+    _check(lib.fctn_get_factor(h, int(k), p, w))
+    return out
+
+
+def fctn_get_X(h, out):
+    p, w = _ptr(out)
+    _check(lib.fctn_get_X(h, p, w))
+    return out
+
+
+def fctn_sync(h):
+    _check(lib.fctn_sync(h))
+
+
+def fctn_launch_count(h):
+    out = ctypes.c_int64(0)
+    _check(lib.fctn_launch_count(h, ctypes.byref(out)))
+    return out.value
+
+
+def fctn_set_graphs(h, enable):
+    _check(lib.fctn_set_graphs(h, int(bool(enable))))
+
+
+def fctn_profile(h, kernel_class):
+    """Start timing every launch of one kernel class (name or number; -1/None = off)."""
+    kc = -1 if kernel_class is None else (KC[kernel_class] if isinstance(kernel_class, str) else int(kernel_class))
+    _check(lib.fctn_profile(h, kc))
+
+
+def fctn_profile_read(h):
+    n = ctypes.c_int64(0)
+    ms, b, f = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib.fctn_profile_read(h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b), ctypes.byref(f)))
+    return {"launches": n.value, "ms": ms.value, "bytes": b.value, "flops": f.value}
+
+
+def fctn_destroy(h):
+    _check(lib.fctn_destroy(h))
+
+
+def factor_shapes(params):
+    N = params.order
+    out = []
+    for k in range(N):
+        out.append(tuple(int(params.dims[k]) if t == k else int(params.ranks[min(k, t)][max(k, t)]) for t in range(N)))
+    return out
