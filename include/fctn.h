@@ -184,6 +184,37 @@ int fctn_profile_read(fctn_handle* h, int64_t* launches, double* ms, double* alg
 
 int fctn_destroy(fctn_handle* h);
 
+/* ---- FCTN contraction without device allocation --------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory: code whose GPU memory is entirely owned by
+ * another allocator (for example a framework's caching allocator that has
+ * reserved the device), and latency-critical loops where cudaMalloc/cudaFree
+ * would synchronise the device.  It computes the same FCTN({A_k}) as
+ * fctn_contract, but without a handle and without allocating: the
+ * intermediates of the contraction chain live in one static device array of
+ * FCTN_NOALLOC_SCRATCH_BYTES (each intermediate may use half of it), which
+ * every GPU that loads this library holds until the process exits.
+ *
+ * order, dims[order]: N and I_1..I_N.  ranks: N*N row-major, ranks[a*N+b]
+ * read for a < b.  precision: FCTN_FP64 or FCTN_FP32 (element type double /
+ * float).  factors: N device pointers, factor k in its FCTN shape (mode k at
+ * position k, row-major).  out: device buffer of prod(dims) elements.  All
+ * work is queued on cuda_stream (NULL = legacy default stream); the call
+ * returns without synchronising.
+ *
+ * Errors: FCTN_E_ARG for bad arguments or when an intermediate would exceed
+ * half the scratch (nothing is launched then); FCTN_E_CUDA if a launch fails.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one scratch
+ * array and it keeps the last call's contents (every element a call reads is
+ * written by that call first, so nothing needs clearing); calls that overlap
+ * on the GPU (different streams, or host threads) race on it and must be
+ * serialised by the caller. */
+#define FCTN_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int fctn_contract_noalloc(int order, const int64_t* dims, const int32_t* ranks, int precision,
+                          const void* const* factors, void* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

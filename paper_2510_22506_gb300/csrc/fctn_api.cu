@@ -949,6 +949,8 @@ int read_stats(fctn_handle* h, fctn_stats* out) {
 
 }  // namespace
 
+int fctn_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 size_t fctn_last_error(char* buf, size_t n) {

@@ -68,6 +68,10 @@ int gram_fused_bk(const PairPlan& p, int s, int elem);
 size_t xupdate_fused_smem(const PairPlan& p, int s, int cb, int elem);
 int xupdate_fused_cb(const PairPlan& p, int s, int elem);
 
+// ---- fctn_api.cu -------------------------------------------------------------
+// Record `msg` as the calling thread's last error (fctn_last_error) and return code.
+int fctn_internal_fail(int code, const char* msg);
+
 // ---- kernels_contract.cu ---------------------------------------------------
 void launch_contract_f32(const float* A, const float* B, float* out, const ContractPlan& p, cudaStream_t s);
 void launch_contract_f64(const double* A, const double* B, double* out, const ContractPlan& p, cudaStream_t s);

@@ -81,6 +81,8 @@ lib.fctn_set_graphs.argtypes = [_vp, _i]
 lib.fctn_profile.argtypes = [_vp, _i]
 _dp = ctypes.POINTER(ctypes.c_double)
 lib.fctn_profile_read.argtypes = [_vp, _i64p, _dp, _dp, _dp]
+lib.fctn_contract_noalloc.argtypes = [_i, _i64p, ctypes.POINTER(ctypes.c_int32), _i, ctypes.POINTER(_vp), _vp, _vp]
+lib.fctn_contract_noalloc.restype = ctypes.c_int
 for _f in ("fctn_footprint_bytes", "fctn_create", "fctn_set_data", "fctn_set_factors", "fctn_contract",
            "fctn_pam_sweep", "fctn_complete", "fctn_get_factor", "fctn_get_X", "fctn_sync", "fctn_launch_count",
            "fctn_destroy", "fctn_set_graphs", "fctn_profile", "fctn_profile_read"):
@@ -89,7 +91,7 @@ for _f in ("fctn_footprint_bytes", "fctn_create", "fctn_set_data", "fctn_set_fac
 EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_create", "fctn_set_data",
             "fctn_set_factors", "fctn_contract", "fctn_pam_sweep", "fctn_complete", "fctn_get_factor",
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
-            "fctn_profile_read")
+            "fctn_profile_read", "fctn_contract_noalloc")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
 
 
@@ -255,6 +257,33 @@ def fctn_profile_read(h):
     ms, b, f = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
     _check(lib.fctn_profile_read(h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b), ctypes.byref(f)))
     return {"launches": n.value, "ms": ms.value, "bytes": b.value, "flops": f.value}
+
+
+def fctn_contract_noalloc(dims, R, precision, factors, out, stream=None):
+    """FCTN contraction of device factors into device `out` without any device allocation.
+
+    For callers that cannot allocate device memory (see include/fctn.h); the
+    chain intermediates use the library's static scratch array.
+    """
+    N = len(dims)
+    d = (ctypes.c_int64 * N)(*[int(x) for x in dims])
+    r = (ctypes.c_int32 * (N * N))(*[int(R[a][b]) if a != b else 0 for a in range(N) for b in range(N)])
+    ptrs = []
+    for a in factors:
+        pa, w = _ptr(a)
+        if w != FCTN_DEVICE:
+            raise ValueError("fctn_contract_noalloc takes device factors")
+        ptrs.append(pa)
+    po, w = _ptr(out)
+    if w != FCTN_DEVICE:
+        raise ValueError("fctn_contract_noalloc writes a device buffer")
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    arr = (ctypes.c_void_p * N)(*ptrs)
+    _check(lib.fctn_contract_noalloc(N, d, r, prec, arr, po, sp))
+    return out
 
 
 def fctn_destroy(h):
