@@ -184,6 +184,45 @@ int fctn_profile_read(fctn_handle* h, int64_t* launches, double* ms, double* alg
 
 int fctn_destroy(fctn_handle* h);
 
+/* ---- serving: continuous batching of completion jobs ----------------------
+ * A server admits submitted jobs (any order, sizes, ranks, sampling rates)
+ * while a slot is free and the job's fctn_footprint_bytes fits the memory
+ * budget.  An admitted job keeps its factors, X and mask on the device; each
+ * of its sweeps is one CUDA-graph launch on the job's own stream, so sweeps
+ * of different jobs overlap on the GPU.  A job runs until rel_change <= tol
+ * or max_sweeps sweeps, then waits (X resident) until fctn_server_result.
+ * The caller drives the scheduler with fctn_server_step (non-blocking). */
+enum { FCTN_JOB_QUEUED = 0, FCTN_JOB_RUNNING = 1, FCTN_JOB_DONE = 2, FCTN_JOB_FAILED = 3 };
+
+typedef struct fctn_server_config {
+  int32_t max_jobs;         /* concurrent jobs (slots), 1..1024                          */
+  int32_t reserved;
+  size_t mem_budget_bytes;  /* device bytes for admitted jobs; 0 = 80 % of free memory  */
+} fctn_server_config;
+
+typedef struct fctn_job_info {
+  int32_t state;                      /* FCTN_JOB_*                                    */
+  int32_t status;                     /* FCTN_OK or the error that failed the job      */
+  int64_t sweeps;                     /* sweeps completed                              */
+  double rel_change, objective;       /* of the last completed sweep                   */
+  double t_submit, t_admit, t_done;   /* host steady-clock seconds                     */
+} fctn_job_info;
+
+typedef struct fctn_server fctn_server;
+
+int fctn_server_create(const fctn_server_config* cfg, fctn_server** out);
+/* Copy a job in (host buffers: Y, mask bytes, factors in their FCTN shape).
+ * Fails with FCTN_E_OOM if the job alone exceeds the memory budget. */
+int fctn_server_submit(fctn_server* s, const fctn_params* p, const void* Y, const uint8_t* mask,
+                       const void* const* factors, double tol, int max_sweeps, uint64_t* job_id);
+/* One scheduling pass: retire finished sweeps, launch next sweeps, admit jobs. */
+int fctn_server_step(fctn_server* s, int* running, int* queued);
+int fctn_server_poll(fctn_server* s, uint64_t job_id, fctn_job_info* info);
+/* Copy the finished job's X out (out_X may be NULL) and release the job. */
+int fctn_server_result(fctn_server* s, uint64_t job_id, void* out_X, int where);
+int fctn_server_stats(fctn_server* s, int64_t* sweeps_launched, size_t* bytes_in_use);
+int fctn_server_destroy(fctn_server* s);
+
 /* ---- FCTN contraction without device allocation --------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory: code whose GPU memory is entirely owned by

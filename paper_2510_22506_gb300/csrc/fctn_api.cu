@@ -951,6 +951,18 @@ int read_stats(fctn_handle* h, fctn_stats* out) {
 
 int fctn_internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+int fctn_internal_sweep_async(fctn_handle* h, double* pinned) {
+  if (!h->data_set || !h->factors_set) return fail(FCTN_E_STATE, "set data and factors before sweeping");
+  int rc = one_sweep(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(pinned, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(pinned + 4, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  pinned[5] = (double)h->t;
+  return FCTN_OK;
+}
+
+cudaStream_t fctn_internal_stream(fctn_handle* h) { return h->st; }
+
 extern "C" {
 
 size_t fctn_last_error(char* buf, size_t n) {

@@ -71,6 +71,11 @@ int xupdate_fused_cb(const PairPlan& p, int s, int elem);
 // ---- fctn_api.cu -------------------------------------------------------------
 // Record `msg` as the calling thread's last error (fctn_last_error) and return code.
 int fctn_internal_fail(int code, const char* msg);
+// Serving hooks: queue one sweep and an asynchronous copy of the stop-test
+// values {rel, objective, data term, nonfinite flag, status, t} into
+// `pinned` (host, 6 doubles); the handle's stream.
+int fctn_internal_sweep_async(fctn_handle* h, double* pinned);
+cudaStream_t fctn_internal_stream(fctn_handle* h);
 
 // ---- kernels_contract.cu ---------------------------------------------------
 void launch_contract_f32(const float* A, const float* B, float* out, const ContractPlan& p, cudaStream_t s);

@@ -68,6 +68,24 @@ __device__ __forceinline__ void form_tile(const PairPlan& p, const T* __restrict
   __syncthreads();
 }
 
+// Asynchronous global -> shared copy of one element (zero-filled when !valid).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Gram + right-hand side partials with M_k formed on chip.  Two-stage
+// pipeline over chunks of BK columns: the slabs of L and R rows and the X
+// rows of chunk c+1 are copied asynchronously while chunk c is formed and
+// consumed.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restrict__ L, const T* __restrict__ R,
                                                    const T* __restrict__ X, T* __restrict__ part, GramPlan g, int BK,
@@ -79,12 +97,12 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   int* ro = lo + s;
   int* lk = ro + s;
   int* rk = lk + p.K;
-  int64_t* cl = (int64_t*)(((uintptr_t)(rk + p.K) + 15) & ~(uintptr_t)15);
-  int64_t* cr = cl + BK;
-  T* Ls = (T*)(cr + BK);
-  T* Rs = Ls + (size_t)BK * p.Ljs;
-  T* Ms = Rs + (size_t)BK * p.Rjs;     // BK x ldm, Ms[kk*ldm + sigma]
-  T* Xs = Ms + (size_t)BK * ldm;       // BK x 64
+  int64_t* cl = (int64_t*)(((uintptr_t)(rk + p.K) + 15) & ~(uintptr_t)15);  // [2][BK]
+  int64_t* cr = cl + 2 * BK;                                                  // [2][BK]
+  T* Ls = (T*)(cr + 2 * BK);                    // [2][BK * Ljs]
+  T* Rs = Ls + (size_t)2 * BK * p.Ljs;          // [2][BK * Rjs]
+  T* Xs = Rs + (size_t)2 * BK * p.Rjs;          // [2][BK * 64]
+  T* Ms = Xs + (size_t)2 * BK * 64;             // BK x ldm, Ms[kk*ldm + sigma]
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < s; e += NT) {
     lo[e] = p.tab[e];
@@ -98,38 +116,91 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   const int64_t kb = (int64_t)blockIdx.z * g.kchunk;
   const int64_t ke = min(kb + g.kchunk, g.Pk);
   const bool write_m = Mout != nullptr && blockIdx.x == 0 && blockIdx.y == 0;
+  const bool has_x = c0 + 64 > g.s;
+  const int nchunk = (int)((ke - kb + BK - 1) / BK);
+
+  // decode the columns of chunk c into buffer b (then a barrier), and issue its copies
+  auto issue = [&](int c, int b) {
+    const int64_t k0 = kb + (int64_t)c * BK;
+    for (int jj = tid; jj < BK; jj += NT) {
+      int64_t a = 0, bb = 0;
+      if (k0 + jj < ke) decode_col(p, k0 + jj, a, bb);
+      cl[b * BK + jj] = a;
+      cr[b * BK + jj] = bb;
+    }
+    __syncthreads();
+    T* ls = Ls + (size_t)b * BK * p.Ljs;
+    T* rs = Rs + (size_t)b * BK * p.Rjs;
+    for (int e = tid; e < BK * p.Ljs; e += NT) {
+      int jj = e / p.Ljs, c_ = e - jj * p.Ljs;
+      bool v = k0 + jj < ke;
+      cp_async_elem(ls + e, v ? L + cl[b * BK + jj] + c_ : L, v);
+    }
+    for (int e = tid; e < BK * p.Rjs; e += NT) {
+      int jj = e / p.Rjs, c_ = e - jj * p.Rjs;
+      bool v = k0 + jj < ke;
+      cp_async_elem(rs + e, v ? R + cr[b * BK + jj] + c_ : R, v);
+    }
+    if (has_x) {
+      T* xs = Xs + (size_t)b * BK * 64;
+      if (g.xv.post == 1) {
+        for (int e = tid; e < 64 * BK; e += NT) {
+          int cc = e % 64, kk = e / 64;
+          int64_t col = c0 + cc, j = k0 + kk;
+          bool v = col >= g.s && col < g.ncols && j < ke;
+          cp_async_elem(xs + kk * 64 + cc, v ? X + j * g.xv.I + (col - g.s) : X, v);
+        }
+      } else {
+        for (int e = tid; e < 64 * BK; e += NT) {
+          int cc = e / BK, kk = e % BK;
+          int64_t col = c0 + cc, j = k0 + kk;
+          bool v = col >= g.s && col < g.ncols && j < ke;
+          cp_async_elem(xs + kk * 64 + cc, v ? X + xaddr(g.xv, col - g.s, j) : X, v);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   __syncthreads();
-  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+  if (nchunk > 0) issue(0, 0);
+  for (int c = 0; c < nchunk; ++c) {
+    const int b = c & 1;
+    const int64_t k0 = kb + (int64_t)c * BK;
     const int nb = (int)min((int64_t)BK, ke - k0);
-    form_tile<T>(p, L, R, k0, BK, ke, Ls, Rs, cl, cr, lo, ro, lk, rk, s, Ms, ldm);
+    if (c + 1 < nchunk) {
+      issue(c + 1, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    // form the M_k tile of this chunk
+    {
+      const T* ls = Ls + (size_t)b * BK * p.Ljs;
+      const T* rs = Rs + (size_t)b * BK * p.Rjs;
+      for (int e = tid; e < BK * s; e += NT) {
+        int jj = e / s, sg = e - jj * s;
+        const T* l = ls + jj * p.Ljs + lo[sg];
+        const T* r = rs + jj * p.Rjs + ro[sg];
+        T a = 0;
+        for (int q = 0; q < p.K; ++q) a = fma(l[lk[q]], r[rk[q]], a);
+        Ms[jj * ldm + sg] = a;
+      }
+    }
+    __syncthreads();
     if (write_m) {
       for (int e = tid; e < s * nb; e += NT) {
         int sg = e / nb, jj = e - sg * nb;
         Mout[(int64_t)sg * g.Pk + k0 + jj] = Ms[jj * ldm + sg];
       }
     }
-    // X rows of this tile: X_(k)[c - s][j]
-    if (c0 + 64 > g.s) {
-      if (g.xv.post == 1) {
-        for (int e = tid; e < 64 * BK; e += NT) {
-          int c = e % 64, kk = e / 64;
-          int64_t col = c0 + c, j = k0 + kk;
-          Xs[kk * 64 + c] = (col >= g.s && col < g.ncols && kk < nb) ? X[j * g.xv.I + (col - g.s)] : (T)0;
-        }
-      } else {
-        for (int e = tid; e < 64 * BK; e += NT) {
-          int c = e / BK, kk = e % BK;
-          int64_t col = c0 + c, j = k0 + kk;
-          Xs[kk * 64 + c] = (col >= g.s && col < g.ncols && kk < nb) ? X[xaddr(g.xv, col - g.s, j)] : (T)0;
-        }
-      }
-    }
-    __syncthreads();
+    const T* xs = Xs + (size_t)b * BK * 64;
     for (int kk = 0; kk < nb; ++kk) {
       T av[4], bv[4];
 #pragma unroll
@@ -138,14 +209,14 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
         av[a] = row < g.s ? Ms[kk * ldm + row] : (T)0;
       }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        int64_t col = c0 + tx * 4 + b;
-        bv[b] = col < g.s ? Ms[kk * ldm + col] : Xs[kk * 64 + tx * 4 + b];
+      for (int b2 = 0; b2 < 4; ++b2) {
+        int64_t col = c0 + tx * 4 + b2;
+        bv[b2] = col < g.s ? Ms[kk * ldm + col] : xs[kk * 64 + tx * 4 + b2];
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fma(av[a], bv[b2], acc[a][b2]);
     }
     __syncthreads();
   }
@@ -155,9 +226,9 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
     int64_t row = r0 + ty * 4 + a;
     if (row >= g.s) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int64_t col = c0 + tx * 4 + b;
-      if (col < g.ncols) P[row * g.ncols + col] = acc[a][b];
+    for (int b2 = 0; b2 < 4; ++b2) {
+      int64_t col = c0 + tx * 4 + b2;
+      if (col < g.ncols) P[row * g.ncols + col] = acc[a][b2];
     }
   }
 }
@@ -262,17 +333,15 @@ size_t head_bytes(const PairPlan& p, int s, int nb) {
 
 }  // namespace
 
-int gram_fused_bk(const PairPlan& p, int s, int elem) {
-  // columns per chunk: slabs + formed tile + X rows within ~100 KB
-  for (int bk = 32; bk >= 4; bk /= 2) {
-    size_t b = head_bytes(p, s, bk) + (size_t)bk * (p.Ljs + p.Rjs + s + 1 + 64) * elem;
-    if (b <= 100 * 1024) return bk;
-  }
-  return 4;
+size_t gram_fused_smem(const PairPlan& p, int s, int bk, int elem) {
+  // tables, 2 x column offsets, 2 x (L slab, R slab, X rows), formed tile
+  return head_bytes(p, s, 2 * bk) + (size_t)bk * (2 * (p.Ljs + p.Rjs + 64) + s + 1) * elem;
 }
 
-size_t gram_fused_smem(const PairPlan& p, int s, int bk, int elem) {
-  return head_bytes(p, s, bk) + (size_t)bk * (p.Ljs + p.Rjs + s + 1 + 64) * elem;
+int gram_fused_bk(const PairPlan& p, int s, int elem) {
+  for (int bk = 32; bk >= 4; bk /= 2)
+    if (gram_fused_smem(p, s, bk, elem) <= 110 * 1024) return bk;
+  return 4;
 }
 
 int xupdate_fused_cb(const PairPlan& p, int s, int elem) {

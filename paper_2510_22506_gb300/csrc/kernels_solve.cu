@@ -31,16 +31,36 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Warm start: V0 (the previous sweep's C for the same factor) is first
 // re-orthonormalised by one Newton-Schulz step V0 (3I - V0^T V0)/2.
 // Also checks min_j Phi_j + tmin > 0 (T of Eq. 8 positive) -> FCTN_E_SINGULAR.
-constexpr int EG = 8;  // lanes per pair
+constexpr int EG = 16;  // lanes per pair
 
-// Sum over the 8 lanes of one group.  The mask names only this group's lanes:
+// Sum over the EG lanes of one group.  The mask names only this group's lanes:
 // other groups of the same warp may be skipping a pair or have left the loop.
 template <typename T>
 __device__ __forceinline__ T group_sum(T v) {
-  const unsigned mask = ((1u << EG) - 1u) << (EG * ((threadIdx.x & 31) / EG));
+  const unsigned mask = (EG == 32) ? 0xffffffffu : (((1u << EG) - 1u) << (EG * ((threadIdx.x & 31) / EG)));
 #pragma unroll
   for (int o = EG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
+}
+
+// Rotation (cos, sin) that zeroes a_p . a_q: t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// zeta = (|a_q|^2 - |a_p|^2) / (2 a_p . a_q).  In FP32 the angle uses fast
+// approximations (an inexact angle only leaves the pair slightly less
+// orthogonal), while c = 1/sqrt(1 + t^2) is correctly rounded so that the
+// rotation stays orthogonal to working precision.
+__device__ __forceinline__ void rot_cs(float al, float be, float ga, float& cs, float& sn) {
+  float zeta = __fdividef(be - al, 2.f * ga);
+  float w = fmaf(zeta, zeta, 1.f);
+  float sq = w * rsqrtf(w);
+  float t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sq);
+  cs = __frsqrt_rn(fmaf(t, t, 1.f));
+  sn = cs * t;
+}
+__device__ __forceinline__ void rot_cs(double al, double be, double ga, double& cs, double& sn) {
+  double zeta = (be - al) / (2.0 * ga);
+  double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  cs = 1.0 / sqrt(1.0 + t * t);
+  sn = cs * t;
 }
 
 // A_SM / V_SM: A^T / V^T live in shared memory (compile-time, so that the
@@ -69,10 +89,10 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
       At[(int64_t)j * s + r] = Cio[e];
     }
     __syncthreads();
-    for (int64_t e = tid; e < ss; e += nt) {             // S = V0^T V0
+    for (int64_t e = tid; e < ss; e += nt) {             // S = V0^T V0 (from V0 in global: no bank conflicts)
       int a = (int)(e / s), b = (int)(e % s);
       T acc = 0;
-      for (int r = 0; r < s; ++r) acc = fma(At[(int64_t)a * s + r], At[(int64_t)b * s + r], acc);
+      for (int r = 0; r < s; ++r) acc = fma(Cio[(int64_t)r * s + a], Cio[(int64_t)r * s + b], acc);
       S[e] = acc;
     }
     __syncthreads();
@@ -105,10 +125,14 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
   __syncthreads();
   const T eps = Eps<T>::v();
   const T tol = sqrt((T)(s > 1 ? s : 1)) * eps;
+  // float4 rows: FP32, s a multiple of 4, rows 16-byte aligned (shared or
+  // cudaMalloc'ed work, row stride s * 4 bytes)
+  const bool vec4 = (sizeof(T) == 4) && (s % 4 == 0);
+  const int s4 = s / 4;
   const T floor_abs = eps * eps * red[0] / (T)(s > 0 ? s : 1);
   int sweep = 0;
   bool converged = (s <= 1);
-  __shared__ float mu_max;  // largest |a_p.a_q| / (|a_p||a_q|) rotated in this sweep
+  __shared__ float mu_max;  // largest (a_p.a_q)^2 / (|a_p|^2 |a_q|^2) rotated in this sweep
   for (; sweep < max_sweeps && !converged; ++sweep) {
     if (tid == 0) {
       rotated = 0;
@@ -126,31 +150,57 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
         if (q >= s) continue;
         T* ap = At + (int64_t)p * s;
         T* aq = At + (int64_t)q * s;
+        T* vp = Vt + (int64_t)p * s;
+        T* vq = Vt + (int64_t)q * s;
         T al = 0, be = 0, ga = 0;
-        for (int c = gl; c < s; c += EG) {
-          T x = ap[c], y = aq[c];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+        if (vec4) {
+          const float4* p4 = (const float4*)ap;
+          const float4* q4 = (const float4*)aq;
+          for (int c = gl; c < s4; c += EG) {
+            float4 x = p4[c], y = q4[c];
+            al = fma(x.x, x.x, fma(x.y, x.y, fma(x.z, x.z, fma(x.w, x.w, al))));
+            be = fma(y.x, y.x, fma(y.y, y.y, fma(y.z, y.z, fma(y.w, y.w, be))));
+            ga = fma(x.x, y.x, fma(x.y, y.y, fma(x.z, y.z, fma(x.w, y.w, ga))));
+          }
+        } else {
+          for (int c = gl; c < s; c += EG) {
+            T x = ap[c], y = aq[c];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
         }
         al = group_sum(al);
         be = group_sum(be);
         ga = group_sum(ga);
-        if (!(fabs(ga) > tol * sqrt(al * be) + floor_abs)) continue;
+        // rotate iff |ga| > tol sqrt(al be) + floor  (squared form, no sqrt)
+        const T thr = tol * sqrt(al * be) + floor_abs;
+        if (!(ga * ga > thr * thr)) continue;
         any = 1;
-        mu_mine = fmaxf(mu_mine, (float)(fabs(ga) / sqrt(al * be)));
-        T zeta = (be - al) / (2 * ga);
-        T t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-        T cs = rsqrt((T)1 + t * t), sn = cs * t;
-        T* vp = Vt + (int64_t)p * s;
-        T* vq = Vt + (int64_t)q * s;
-        for (int c = gl; c < s; c += EG) {
-          T x = ap[c], y = aq[c];
-          ap[c] = cs * x - sn * y;
-          aq[c] = sn * x + cs * y;
-          T u = vp[c], w = vq[c];
-          vp[c] = cs * u - sn * w;
-          vq[c] = sn * u + cs * w;
+        mu_mine = fmaxf(mu_mine, (float)(ga * ga / (al * be)));  // squared ratio
+        T cs, sn;
+        rot_cs(al, be, ga, cs, sn);
+        if (vec4) {
+          float4* p4 = (float4*)ap;
+          float4* q4 = (float4*)aq;
+          float4* u4 = (float4*)vp;
+          float4* w4 = (float4*)vq;
+          for (int c = gl; c < s4; c += EG) {
+            float4 x = p4[c], y = q4[c], u = u4[c], w = w4[c];
+            p4[c] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w);
+            q4[c] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w);
+            u4[c] = make_float4(cs * u.x - sn * w.x, cs * u.y - sn * w.y, cs * u.z - sn * w.z, cs * u.w - sn * w.w);
+            w4[c] = make_float4(sn * u.x + cs * w.x, sn * u.y + cs * w.y, sn * u.z + cs * w.z, sn * u.w + cs * w.w);
+          }
+        } else {
+          for (int c = gl; c < s; c += EG) {
+            T x = ap[c], y = aq[c];
+            ap[c] = cs * x - sn * y;
+            aq[c] = sn * x + cs * y;
+            T u = vp[c], w = vq[c];
+            vp[c] = cs * u - sn * w;
+            vq[c] = sn * u + cs * w;
+          }
         }
       }
       __syncthreads();
@@ -163,7 +213,7 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
     // cyclic Jacobi converges quadratically: after a sweep whose largest
     // rotated off-term was below sqrt(tol), the next sweep would rotate
     // nothing above tol
-    converged = (rotated == 0) || (mu_max < (float)sqrt(tol));
+    converged = (rotated == 0) || (mu_max < (float)tol);  // mu^2 < tol  <=>  mu < sqrt(tol)
     __syncthreads();
   }
   // Phi_j = v_j . a_j ; C[r][j] = Vt[j][r]

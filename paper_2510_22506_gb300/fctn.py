@@ -91,8 +91,37 @@ for _f in ("fctn_footprint_bytes", "fctn_create", "fctn_set_data", "fctn_set_fac
 EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_create", "fctn_set_data",
             "fctn_set_factors", "fctn_contract", "fctn_pam_sweep", "fctn_complete", "fctn_get_factor",
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
-            "fctn_profile_read", "fctn_contract_noalloc")
+            "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
+            "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
+
+
+class fctn_server_config(ctypes.Structure):
+    _fields_ = [("max_jobs", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class fctn_job_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("sweeps", ctypes.c_int64),
+                ("rel_change", ctypes.c_double), ("objective", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+FCTN_JOB_QUEUED, FCTN_JOB_RUNNING, FCTN_JOB_DONE, FCTN_JOB_FAILED = range(4)
+lib.fctn_server_create.argtypes = [ctypes.POINTER(fctn_server_config), ctypes.POINTER(ctypes.c_void_p)]
+lib.fctn_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(fctn_params), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p), ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+lib.fctn_server_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+lib.fctn_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(fctn_job_info)]
+lib.fctn_server_result.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
+lib.fctn_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)]
+lib.fctn_server_destroy.argtypes = [ctypes.c_void_p]
+for _f in ("fctn_server_create", "fctn_server_submit", "fctn_server_step", "fctn_server_poll", "fctn_server_result",
+           "fctn_server_stats", "fctn_server_destroy"):
+    getattr(lib, _f).restype = ctypes.c_int
 
 
 class FctnError(RuntimeError):
@@ -296,3 +325,55 @@ def factor_shapes(params):
     for k in range(N):
         out.append(tuple(int(params.dims[k]) if t == k else int(params.ranks[min(k, t)][max(k, t)]) for t in range(N)))
     return out
+
+
+def fctn_server_create(max_jobs=32, mem_budget_bytes=0):
+    cfg = fctn_server_config(max_jobs=int(max_jobs), reserved=0, mem_budget_bytes=int(mem_budget_bytes))
+    out = ctypes.c_void_p()
+    _check(lib.fctn_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def fctn_server_submit(srv, params, Y, mask, factors, tol, max_sweeps):
+    """Submit a job from host arrays; returns its id."""
+    dt = elem_dtype(params)
+    Y = np.ascontiguousarray(Y, dtype=dt)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    fs = [np.ascontiguousarray(a, dtype=dt) for a in factors]
+    arr = (ctypes.c_void_p * len(fs))(*[a.ctypes.data_as(ctypes.c_void_p) for a in fs])
+    jid = ctypes.c_uint64(0)
+    _check(lib.fctn_server_submit(srv, ctypes.byref(params), Y.ctypes.data_as(ctypes.c_void_p),
+                                  mask.ctypes.data_as(ctypes.c_void_p), arr, float(tol), int(max_sweeps),
+                                  ctypes.byref(jid)))
+    return jid.value
+
+
+def fctn_server_step(srv):
+    r, q = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.fctn_server_step(srv, ctypes.byref(r), ctypes.byref(q)))
+    return r.value, q.value
+
+
+def fctn_server_poll(srv, job_id):
+    info = fctn_job_info()
+    _check(lib.fctn_server_poll(srv, ctypes.c_uint64(job_id), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def fctn_server_result(srv, job_id, out=None):
+    if out is None:
+        _check(lib.fctn_server_result(srv, ctypes.c_uint64(job_id), None, FCTN_HOST))
+        return None
+    p, w = _ptr(out)
+    _check(lib.fctn_server_result(srv, ctypes.c_uint64(job_id), p, w))
+    return out
+
+
+def fctn_server_stats(srv):
+    n, b = ctypes.c_int64(0), ctypes.c_size_t(0)
+    _check(lib.fctn_server_stats(srv, ctypes.byref(n), ctypes.byref(b)))
+    return {"sweeps_launched": n.value, "bytes_in_use": b.value}
+
+
+def fctn_server_destroy(srv):
+    _check(lib.fctn_server_destroy(srv))

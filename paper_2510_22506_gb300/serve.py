@@ -1,0 +1,148 @@
+"""Serving driver: Poisson arrivals of completion jobs into the libfctn server.
+
+The scheduling itself (admission by device footprint, one CUDA-graph sweep
+per job per pass on the job's own stream, retirement on the stop test) lives
+in the library (fctn_server_*).  This module builds a job mix, submits jobs at
+their arrival times while stepping the server, and reports throughput and
+latency percentiles; `run_sequential` runs the same jobs one after another
+through fctn_complete for comparison.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import fctn as F
+from . import synth
+
+MIX_SHAPES = [(64, 64, 16), (128, 128, 31), (144, 176, 3, 20), (256, 256, 31)]
+MIX_RANKS = [3, 4, 6]
+MIX_RATES = [0.05, 0.1, 0.2]
+
+
+def library_contract(dims, R):
+    """FCTN contraction of host factors through the library (FP64)."""
+    def contract(fs):
+        p = F.make_params(dims, R, precision="fp64", reuse=False)
+        h = F.fctn_create(p)
+        try:
+            F.fctn_set_factors(h, [np.ascontiguousarray(a) for a in fs])
+            out = np.empty(dims, dtype=np.float64)
+            F.fctn_contract(h, out)
+        finally:
+            F.fctn_destroy(h)
+        return out
+    return contract
+
+
+def mix_jobs(n_jobs, seed=5000, rate=20.0, shapes=MIX_SHAPES, contract=None):
+    """Job specs of the serving mix: shape, ranks, sampling rate, Poisson arrival time."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    jobs = []
+    for i in range(n_jobs):
+        dims = tuple(shapes[rng.integers(len(shapes))])
+        r = int(MIX_RANKS[rng.integers(len(MIX_RANKS))])
+        pr = float(MIX_RATES[rng.integers(len(MIX_RATES))])
+        cap = (3, 3) if 3 in dims else None
+        R = synth.rank_matrix(dims, r, cap)
+        c = contract(dims, R) if contract else library_contract(dims, R)
+        truth, Y, mask, init, _ = synth.workload_inputs(None, c, dims=dims, r=r, p=pr, idx=100 + i, noise=0.0,
+                                                        cap=cap)
+        jobs.append(dict(i=i, dims=dims, r=r, p=pr, R=R, Y=Y, mask=mask, init=init, truth=truth,
+                         arrival=float(arrivals[i])))
+    return jobs
+
+
+def job_params(job, precision):
+    return F.make_params(job["dims"], job["R"], lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO,
+                         precision=precision, reuse=True, order_policy="alternate")
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if xs else None
+
+
+def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_budget_bytes=0,
+            keep_results=False, poll_sleep=2e-5, arrivals=True):
+    """Submit jobs at their arrival times, step the server until all finish."""
+    srv = F.fctn_server_create(max_jobs=max_jobs, mem_budget_bytes=mem_budget_bytes)
+    pending = sorted(jobs, key=lambda j: j["arrival"]) if arrivals else list(jobs)
+    ids, t_arr, results, infos = {}, {}, {}, {}
+    try:
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(pending) or ids:
+            now = time.perf_counter() - t0
+            while nxt < len(pending) and (not arrivals or pending[nxt]["arrival"] <= now):
+                j = pending[nxt]
+                p = job_params(j, precision)
+                dt = F.elem_dtype(p)
+                jid = F.fctn_server_submit(srv, p, j["Y"].astype(dt), j["mask"], [a.astype(dt) for a in j["init"]],
+                                           tol, max_sweeps)
+                ids[jid] = j["i"]
+                t_arr[j["i"]] = t0 + (j["arrival"] if arrivals else 0.0)
+                nxt += 1
+            F.fctn_server_step(srv)
+            done = []
+            for jid, i in ids.items():
+                info = F.fctn_server_poll(srv, jid)
+                if info["state"] in (F.FCTN_JOB_DONE, F.FCTN_JOB_FAILED):
+                    info["t_wall_done"] = time.perf_counter()
+                    infos[i] = info
+                    done.append(jid)
+            for jid in done:
+                i = ids.pop(jid)
+                if infos[i]["state"] == F.FCTN_JOB_DONE:
+                    out = None
+                    if keep_results:
+                        j = jobs[i] if jobs[i]["i"] == i else next(x for x in jobs if x["i"] == i)
+                        out = np.empty(j["dims"], dtype=F.elem_dtype(job_params(j, precision)))
+                    F.fctn_server_result(srv, jid, out)
+                    if keep_results:
+                        results[i] = out
+            if not done and poll_sleep:
+                time.sleep(poll_sleep)
+        t_end = time.perf_counter()
+        stats = F.fctn_server_stats(srv)
+    finally:
+        F.fctn_server_destroy(srv)
+    lat = [infos[i]["t_wall_done"] - t_arr[i] for i in infos]
+    ttt = [infos[i]["t_done"] - infos[i]["t_admit"] for i in infos if infos[i]["state"] == F.FCTN_JOB_DONE]
+    sweeps = sum(infos[i]["sweeps"] for i in infos)
+    first = min(t_arr.values())
+    return {"jobs": len(infos), "failed": sum(1 for i in infos if infos[i]["state"] != F.FCTN_JOB_DONE),
+            "wall_s": t_end - first, "jobs_per_s": len(infos) / (t_end - first), "sweeps": int(sweeps),
+            "sweeps_per_s": sweeps / (t_end - first), "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+            "ttt_p50_s": _pct(ttt, 50), "ttt_p99_s": _pct(ttt, 99), "sweeps_launched": stats["sweeps_launched"],
+            "infos": infos, "results": results}
+
+
+def run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500, keep_results=False):
+    """The same jobs one at a time through fctn_complete (no concurrency)."""
+    infos, results = {}, {}
+    t0 = time.perf_counter()
+    sweeps = 0
+    for j in jobs:
+        p = job_params(j, precision)
+        dt = F.elem_dtype(p)
+        h = F.fctn_create(p)
+        try:
+            ts = time.perf_counter()
+            F.fctn_set_data(h, np.ascontiguousarray(j["Y"].astype(dt)), j["mask"].astype(np.uint8))
+            F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(dt)) for a in j["init"]])
+            out = np.empty(j["dims"], dtype=dt)
+            st = F.fctn_complete(h, tol, max_sweeps, out)
+            infos[j["i"]] = dict(st, wall=time.perf_counter() - ts)
+            sweeps += st["t"]
+            if keep_results:
+                results[j["i"]] = out
+        finally:
+            F.fctn_destroy(h)
+    wall = time.perf_counter() - t0
+    ttt = [v["wall"] for v in infos.values()]
+    return {"jobs": len(jobs), "wall_s": wall, "jobs_per_s": len(jobs) / wall, "sweeps": int(sweeps),
+            "sweeps_per_s": sweeps / wall, "ttt_p50_s": _pct(ttt, 50), "ttt_p99_s": _pct(ttt, 99),
+            "infos": infos, "results": results}
