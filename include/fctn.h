@@ -63,7 +63,8 @@ enum {
   FCTN_FP64 = 0,  /* everything in double: the parity path                             */
   FCTN_FP32 = 1,  /* plain single precision on the CUDA cores                          */
   FCTN_TF32 = 2,  /* tcgen05 TF32 contractions, FP32 accumulation                      */
-  FCTN_BF16 = 3   /* tcgen05 BF16 contractions, FP32 accumulation                      */
+  FCTN_BF16 = 3   /* tcgen05 BF16 contractions on split operands (v = hi + lo, three
+                     MMAs per product: hi.hi + hi.lo + lo.hi), FP32 accumulation     */
 };
 
 /* update-order policy of Algorithm 2 ("unordered permutation" of the factors) */
@@ -220,6 +221,9 @@ int fctn_server_step(fctn_server* s, int* running, int* queued);
 int fctn_server_poll(fctn_server* s, uint64_t job_id, fctn_job_info* info);
 /* Copy the finished job's X out (out_X may be NULL) and release the job. */
 int fctn_server_result(fctn_server* s, uint64_t job_id, void* out_X, int where);
+/* Ids of jobs that finished (DONE or FAILED) since the last call, up to cap;
+ * *n gets the count. */
+int fctn_server_finished(fctn_server* s, uint64_t* ids, int cap, int* n);
 int fctn_server_stats(fctn_server* s, int64_t* sweeps_launched, size_t* bytes_in_use);
 int fctn_server_destroy(fctn_server* s);
 

@@ -91,6 +91,8 @@ struct fctn_handle {
   void* M = nullptr;              // merged tensor of the factor updated last (Algorithm 2 reuse)
   bool mat[FCTN_MAX_ORDER] = {};  // M_k is small enough to keep for the X update
   PairPlan pp[FCTN_MAX_ORDER];    // pair form of every M_k
+  TcPlan tp[FCTN_MAX_ORDER];      // tensor-core Gram plan (TF32 / BF16)
+  bool tc = false;
   int* tabs = nullptr;            // device index tables of the pair forms
   void* ones = nullptr;           // the constant 1 (second operand when N = 2)
   void* Lbuf = nullptr;           // chain intermediate (no pair cache, N >= 4)
@@ -166,16 +168,6 @@ View factor_d1_view(const fctn_handle* h, int t) {
     ext[u] = (u == t) ? h->I[t] : rank_of(h, t, u);
   }
   return dense_view(h->N, labs, ext);
-}
-
-// Canonical M_k order: open bonds (k,t) then modes t, t != k ascending.
-void merged_order(const fctn_handle* h, int k, Lab* out, int* n) {
-  int c = 0;
-  for (int t = 0; t < h->N; ++t)
-    if (t != k) out[c++] = bond_lab(k, t);
-  for (int t = 0; t < h->N; ++t)
-    if (t != k) out[c++] = mode_lab(t);
-  *n = c;
 }
 
 int make_plan(const View& A, const View* B, const Lab* out, int nout, ContractPlan* p, View* outv) {
@@ -584,8 +576,12 @@ GramPlan gram_plan(const fctn_handle* h, int k) {
   g.ncols = g.s + g.I;
   g.tiles_r = (int)((g.s + 63) / 64);
   g.tiles_c = (int)((g.ncols + 63) / 64);
-  int64_t target = (2 * 152 + g.tiles_r * g.tiles_c - 1) / (g.tiles_r * g.tiles_c);
-  int64_t maxsplit = (g.Pk + 31) / 32;
+  int64_t ctas_per_split = g.tiles_r * g.tiles_c;
+  if (h->tc) ctas_per_split = h->tp[k].n_groups > 0 ? h->tp[k].n_groups : 1;
+  int64_t target = (2 * 152 + ctas_per_split - 1) / ctas_per_split;
+  // tensor-core path: at least four 32-column chunks per CTA, so the per-split
+  // partial (s x (s + I) floats) stays small against the columns it consumes
+  int64_t maxsplit = h->tc ? (g.Pk + 127) / 128 : (g.Pk + 31) / 32;
   int64_t ks = target < maxsplit ? target : maxsplit;
   if (ks < 1) ks = 1;
   int64_t chunk = (g.Pk + ks - 1) / ks;
@@ -599,8 +595,6 @@ int check_params(const fctn_params* p) {
   if (!p) return fail(FCTN_E_ARG, "params is NULL");
   if (p->order < 2 || p->order > FCTN_MAX_ORDER) return fail(FCTN_E_ARG, "order %d outside [2, %d]", p->order, FCTN_MAX_ORDER);
   if (p->precision < FCTN_FP64 || p->precision > FCTN_BF16) return fail(FCTN_E_ARG, "unknown precision %d", p->precision);
-  if (p->precision == FCTN_TF32 || p->precision == FCTN_BF16)
-    return fail(FCTN_E_UNSUPPORTED, "tensor-core precisions are not built in this library version");
   if (p->order_policy != FCTN_ORDER_PLAIN && p->order_policy != FCTN_ORDER_ALTERNATE)
     return fail(FCTN_E_ARG, "unknown order policy %d", p->order_policy);
   if (p->laplacian_sign != FCTN_LAPLACIAN_PSD && p->laplacian_sign != FCTN_LAPLACIAN_PRINTED)
@@ -635,6 +629,7 @@ void fill_shapes(fctn_handle* h, const fctn_params* p) {
   }
   h->f64 = (p->precision == FCTN_FP64);
   h->esz = h->f64 ? 8 : 4;
+  h->tc = (p->precision == FCTN_TF32 || p->precision == FCTN_BF16);
 }
 
 struct Sizes {
@@ -658,6 +653,28 @@ int64_t lbuf_need(const fctn_handle* h) {
     if (sz > need) need = sz;
   }
   return need;
+}
+
+// Host-only planning of every factor's pair form (and its index tables) and,
+// for the tensor-core precisions, of the tcgen05 Gram kernel.
+int plan_all(fctn_handle* h, std::vector<int>* all, size_t* offs) {
+  for (int k = 0; k < h->N; ++k) {
+    View L, R;
+    pair_operands(h, k, &L, &R);
+    std::vector<int> tab;
+    int rc = plan_pair(h, k, L, R, &h->pp[k], &tab);
+    if (rc) return rc;
+    if (offs) offs[k] = all->size();
+    all->insert(all->end(), tab.begin(), tab.end());
+    h->mat[k] = h->p.reuse && materialise_ok(h, k);
+    if (h->tc) {
+      h->tp[k].n_groups = 0;
+      GramPlan g = gram_plan(h, k);
+      rc = tc_plan(h->pp[k], g, h->p.precision, &h->tp[k]);
+      if (rc) return fail(rc, "tensor-core Gram kernel does not cover factor %d (s_k = %lld)", k, (long long)h->s[k]);
+    }
+  }
+  return FCTN_OK;
 }
 
 Sizes sizes_of(const fctn_handle* h) {
@@ -779,9 +796,15 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     }
   } else {
     float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
-    LAUNCH(FCTN_KC_GRAM, gram_bytes, gram_flops,
-           launch_gram_fused_f32(h->pp[k], (const float*)L, (const float*)R, (const float*)h->X, (float*)h->part,
-                                 g, (float*)Mout, h->st));
+    if (h->tc) {
+      LAUNCH(FCTN_KC_GRAM, gram_bytes, gram_flops,
+             launch_gram_tc(h->pp[k], (const float*)L, (const float*)R, (const float*)h->X, (float*)h->part, g,
+                            h->tp[k], h->p.precision, (float*)Mout, h->status, h->st));
+    } else {
+      LAUNCH(FCTN_KC_GRAM, gram_bytes, gram_flops,
+             launch_gram_fused_f32(h->pp[k], (const float*)L, (const float*)R, (const float*)h->X,
+                                   (float*)h->part, g, (float*)Mout, h->st));
+    }
     LAUNCH(FCTN_KC_REDUCE, red_bytes, part_elems,
            launch_reduce_gram_rhs_f32((const float*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, (float*)h->Gs,
                                       (float*)h->Ys, h->st));
@@ -982,7 +1005,9 @@ int fctn_footprint_bytes(const fctn_params* p, size_t* out) {
   if (!out) return fail(FCTN_E_ARG, "out is NULL");
   fctn_handle tmp;
   fill_shapes(&tmp, p);
-  *out = footprint(&tmp);
+  std::vector<int> tabs;
+  if ((rc = plan_all(&tmp, &tabs, nullptr))) return rc;
+  *out = footprint(&tmp) + tabs.size() * sizeof(int);
   return FCTN_OK;
 }
 
@@ -1002,6 +1027,13 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
       return fail(FCTN_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(se));
     }
     h->own_stream = true;
+  }
+  std::vector<int> all_tabs;
+  size_t tab_offs[FCTN_MAX_ORDER];
+  if ((rc = plan_all(h, &all_tabs, tab_offs))) {
+    if (h->own_stream) cudaStreamDestroy(h->st);
+    delete h;
+    return rc;
   }
   Sizes z = sizes_of(h);
   const size_t e = h->esz, se = h->f64 ? 8 : 4;
@@ -1051,23 +1083,9 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
   A_(h->stage, h->stage_bytes);
   A_(h->stage_mask, h->P);
   {
-    // pair forms of every merged tensor and their index tables
-    std::vector<int> all;
-    size_t offs[FCTN_MAX_ORDER];
-    for (int k = 0; k < h->N; ++k) {
-      View L, R;
-      pair_operands(h, k, &L, &R);
-      std::vector<int> tab;
-      if ((rc = plan_pair(h, k, L, R, &h->pp[k], &tab))) {
-        free_all(h);
-        if (h->own_stream) cudaStreamDestroy(h->st);
-        delete h;
-        return rc;
-      }
-      offs[k] = all.size();
-      all.insert(all.end(), tab.begin(), tab.end());
-      h->mat[k] = h->p.reuse && materialise_ok(h, k);
-    }
+    // index tables of the pair forms
+    std::vector<int>& all = all_tabs;
+    size_t* offs = tab_offs;
     A_(h->tabs, all.size() * sizeof(int));
     for (int k = 0; k < h->N; ++k) h->pp[k].tab = h->tabs + offs[k];
     cudaError_t ce = cudaMemcpy(h->tabs, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);

@@ -54,6 +54,24 @@ struct PairPlan {
   const int* tab;
 };
 
+// ---- kernels_tc.cu ------------------------------------------------------------
+// Column groups of the tensor-core Gram kernel: each CTA computes, for all
+// 128-row blocks of M_k, the Gram columns [0, mw) (if mw > 0) and the
+// right-hand-side columns of X rows [xi0, xi0 + xw), within 512 TMEM columns.
+#define TC_MAX_GROUPS 8
+struct TcGroup {
+  int mw, xi0, xw, width;
+};
+struct TcPlan {
+  int n_mb, n_groups, BK, tmem_cols;
+  uint32_t a_bytes, x_bytes;
+  size_t smem;
+  TcGroup groups[TC_MAX_GROUPS];
+};
+int tc_plan(const PairPlan& p, const GramPlan& g, int precision, TcPlan* tp);
+void launch_gram_tc(const PairPlan& p, const float* L, const float* R, const float* X, float* part,
+                    const GramPlan& g, const TcPlan& tp, int precision, float* Mout, int* status, cudaStream_t st);
+
 // ---- kernels_fused.cu -------------------------------------------------------
 void launch_gram_fused_f32(const PairPlan& p, const float* L, const float* R, const float* X, float* part,
                            const GramPlan& g, float* Mout, cudaStream_t st);
@@ -105,8 +123,8 @@ void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint
 // Symmetric eigendecomposition of the Gram by one-sided Jacobi (one CTA).
 // C (s x s, column j = eigenvector j) is read as the warm start when warm != 0
 // and overwritten with the result; Phi gets the eigenvalues.  work: 3 s^2.
-// *status: FCTN_E_SINGULAR if min Phi + tmin <= 0, FCTN_E_TIMEOUT if the
-// sweep limit ran out; *used: sweeps taken.
+// *status: FCTN_E_SINGULAR if min Phi + tmin <= 0; *used: sweeps taken
+// (max_sweeps if the sweep limit ran out, which is not an error).
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,

@@ -10,22 +10,11 @@
 //                  of the factor updated last, reused by the X update).
 //   xupdate_fused: F = A_k(k) M_k and the masked proximal update of Eq. 10.
 #include "fctn_internal.cuh"
+#include "fctn_tile.cuh"
 
 namespace {
 
 constexpr int NT = 256;
-
-__device__ __forceinline__ void decode_col(const PairPlan& p, int64_t j, int64_t& lo, int64_t& ro) {
-  lo = 0;
-  ro = 0;
-  for (int d = p.nd - 1; d >= 0; --d) {
-    int64_t e = p.ext[d];
-    int64_t dig = j % e;
-    j /= e;
-    lo += dig * p.lstr[d];
-    ro += dig * p.rstr[d];
-  }
-}
 
 __device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j) {
   uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
@@ -33,36 +22,35 @@ __device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j
   return ((int64_t)a * v.I + i) * v.post + b;
 }
 
-// Form Ms[jj * ldm + sigma] for jj in [0, nb) of columns starting at j0.
-// Slabs: Ls[jj * Ljs ...], Rs[jj * Rjs ...].  Tables in shared memory.
+// Form Ms[jj * ldm + sigma] for jj in [0, nb) of columns starting at j0
+// (nb <= 32; columns at or beyond Pk are zero).  The distinct L / R rows of
+// the columns are staged once each (Ls, Rs), with the per-column slots and row
+// offsets in lsl/rsl and cl/cr.  Tables lo, ro, lk, rk in shared memory.
 template <typename T>
 __device__ __forceinline__ void form_tile(const PairPlan& p, const T* __restrict__ L, const T* __restrict__ R,
                                           int64_t j0, int nb, int64_t Pk, T* Ls, T* Rs, int64_t* cl, int64_t* cr,
-                                          const int* lo, const int* ro, const int* lk, const int* rk, int s,
-                                          T* Ms, int ldm) {
+                                          int* lsl, int* rsl, int* cnt, const int* lo, const int* ro, const int* lk,
+                                          const int* rk, int s, T* Ms, int ldm) {
   const int tid = threadIdx.x;
-  for (int jj = tid; jj < nb; jj += NT) {
-    int64_t a = 0, b = 0;
-    if (j0 + jj < Pk) decode_col(p, j0 + jj, a, b);
-    cl[jj] = a;
-    cr[jj] = b;
-  }
+  if (tid < 32) fctn_tile::chunk_slots(p, j0, nb, Pk, lsl, rsl, cl, cr, cnt);
   __syncthreads();
-  for (int e = tid; e < nb * p.Ljs; e += NT) {
-    int jj = e / p.Ljs, c = e - jj * p.Ljs;
-    Ls[e] = (j0 + jj < Pk) ? L[cl[jj] + c] : (T)0;
+  for (int e = tid; e < cnt[0] * p.Ljs; e += NT) {
+    int q = e / p.Ljs, c = e - q * p.Ljs;
+    Ls[e] = L[cl[q] + c];
   }
-  for (int e = tid; e < nb * p.Rjs; e += NT) {
-    int jj = e / p.Rjs, c = e - jj * p.Rjs;
-    Rs[e] = (j0 + jj < Pk) ? R[cr[jj] + c] : (T)0;
+  for (int e = tid; e < cnt[1] * p.Rjs; e += NT) {
+    int q = e / p.Rjs, c = e - q * p.Rjs;
+    Rs[e] = R[cr[q] + c];
   }
   __syncthreads();
   for (int e = tid; e < nb * s; e += NT) {
     int jj = e / s, sg = e - jj * s;
-    const T* l = Ls + jj * p.Ljs + lo[sg];
-    const T* r = Rs + jj * p.Rjs + ro[sg];
     T acc = 0;
-    for (int q = 0; q < p.K; ++q) acc = fma(l[lk[q]], r[rk[q]], acc);
+    if (j0 + jj < Pk) {
+      const T* l = Ls + lsl[jj] * p.Ljs + lo[sg];
+      const T* r = Rs + rsl[jj] * p.Rjs + ro[sg];
+      for (int q = 0; q < p.K; ++q) acc = fma(l[lk[q]], r[rk[q]], acc);
+    }
     Ms[jj * ldm + sg] = acc;
   }
   __syncthreads();
@@ -103,6 +91,7 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   T* Rs = Ls + (size_t)2 * BK * p.Ljs;          // [2][BK * Rjs]
   T* Xs = Rs + (size_t)2 * BK * p.Rjs;          // [2][BK * 64]
   T* Ms = Xs + (size_t)2 * BK * 64;             // BK x ldm, Ms[kk*ldm + sigma]
+  __shared__ int lsl[2][32], rsl[2][32], cnt[2][2];  // per stage: row slots of the columns, distinct-row counts
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < s; e += NT) {
     lo[e] = p.tab[e];
@@ -122,24 +111,17 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   // decode the columns of chunk c into buffer b (then a barrier), and issue its copies
   auto issue = [&](int c, int b) {
     const int64_t k0 = kb + (int64_t)c * BK;
-    for (int jj = tid; jj < BK; jj += NT) {
-      int64_t a = 0, bb = 0;
-      if (k0 + jj < ke) decode_col(p, k0 + jj, a, bb);
-      cl[b * BK + jj] = a;
-      cr[b * BK + jj] = bb;
-    }
+    if (tid < 32) fctn_tile::chunk_slots(p, k0, BK, ke, lsl[b], rsl[b], cl + b * BK, cr + b * BK, cnt[b]);
     __syncthreads();
     T* ls = Ls + (size_t)b * BK * p.Ljs;
     T* rs = Rs + (size_t)b * BK * p.Rjs;
-    for (int e = tid; e < BK * p.Ljs; e += NT) {
-      int jj = e / p.Ljs, c_ = e - jj * p.Ljs;
-      bool v = k0 + jj < ke;
-      cp_async_elem(ls + e, v ? L + cl[b * BK + jj] + c_ : L, v);
+    for (int e = tid; e < cnt[b][0] * p.Ljs; e += NT) {
+      int q = e / p.Ljs, c_ = e - q * p.Ljs;
+      cp_async_elem(ls + e, L + cl[b * BK + q] + c_, true);
     }
-    for (int e = tid; e < BK * p.Rjs; e += NT) {
-      int jj = e / p.Rjs, c_ = e - jj * p.Rjs;
-      bool v = k0 + jj < ke;
-      cp_async_elem(rs + e, v ? R + cr[b * BK + jj] + c_ : R, v);
+    for (int e = tid; e < cnt[b][1] * p.Rjs; e += NT) {
+      int q = e / p.Rjs, c_ = e - q * p.Rjs;
+      cp_async_elem(rs + e, R + cr[b * BK + q] + c_, true);
     }
     if (has_x) {
       T* xs = Xs + (size_t)b * BK * 64;
@@ -186,10 +168,12 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
       const T* rs = Rs + (size_t)b * BK * p.Rjs;
       for (int e = tid; e < BK * s; e += NT) {
         int jj = e / s, sg = e - jj * s;
-        const T* l = ls + jj * p.Ljs + lo[sg];
-        const T* r = rs + jj * p.Rjs + ro[sg];
         T a = 0;
-        for (int q = 0; q < p.K; ++q) a = fma(l[lk[q]], r[rk[q]], a);
+        if (k0 + jj < ke) {
+          const T* l = ls + lsl[b][jj] * p.Ljs + lo[sg];
+          const T* r = rs + rsl[b][jj] * p.Rjs + ro[sg];
+          for (int q = 0; q < p.K; ++q) a = fma(l[lk[q]], r[rk[q]], a);
+        }
         Ms[jj * ldm + sg] = a;
       }
     }
@@ -269,8 +253,10 @@ __global__ void __launch_bounds__(NT) k_xupdate_fused(PairPlan p, const T* __res
     As[e] = (i0 + r < g.I) ? Ak[(i0 + r) * g.s + sg] : (T)0;
   }
   __syncthreads();
-  for (int c = 0; c < 64; c += CB) form_tile<T>(p, L, R, j0 + c, CB, g.Pk, Ls, Rs, cl, cr, lo, ro, lk, rk, s,
-                                                Ms + (size_t)c * ldm, ldm);
+  __shared__ int lsl[32], rsl[32], cnt[2];
+  for (int c = 0; c < 64; c += CB)
+    form_tile<T>(p, L, R, j0 + c, CB, g.Pk, Ls, Rs, cl, cr, lsl, rsl, cnt, lo, ro, lk, rk, s, Ms + (size_t)c * ldm,
+                 ldm);
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)

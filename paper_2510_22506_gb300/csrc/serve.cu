@@ -57,6 +57,7 @@ struct fctn_server {
   size_t used = 0;
   int active = 0;
   int64_t sweeps_launched = 0;
+  std::vector<uint64_t> finished;  // jobs that reached DONE / FAILED, not yet reported
 };
 
 namespace {
@@ -81,6 +82,7 @@ void release(fctn_server* S, Job& j) {
 }
 
 void finish(fctn_server* S, Job& j, int state, int status, const char* msg) {
+  S->finished.push_back(j.id);
   j.state = state;
   j.status = status;
   j.t_done = now_s();
@@ -265,6 +267,16 @@ int fctn_server_result(fctn_server* S, uint64_t job_id, void* out_X, int where) 
   release(S, j);
   S->jobs.erase(it);
   return rc;
+}
+
+int fctn_server_finished(fctn_server* S, uint64_t* ids, int cap, int* n) {
+  if (!S || !n || (cap > 0 && !ids)) return svr_fail(FCTN_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(S->mu);
+  int c = (int)S->finished.size() < cap ? (int)S->finished.size() : cap;
+  for (int i = 0; i < c; ++i) ids[i] = S->finished[i];
+  S->finished.erase(S->finished.begin(), S->finished.begin() + c);
+  *n = c;
+  return FCTN_OK;
 }
 
 int fctn_server_stats(fctn_server* S, int64_t* sweeps_launched, size_t* bytes_in_use) {

@@ -92,7 +92,8 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_set_factors", "fctn_contract", "fctn_pam_sweep", "fctn_complete", "fctn_get_factor",
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
-            "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy")
+            "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
+            "fctn_server_finished")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
 
 
@@ -119,8 +120,10 @@ lib.fctn_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTE
 lib.fctn_server_result.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
 lib.fctn_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)]
 lib.fctn_server_destroy.argtypes = [ctypes.c_void_p]
+lib.fctn_server_finished.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]
 for _f in ("fctn_server_create", "fctn_server_submit", "fctn_server_step", "fctn_server_poll", "fctn_server_result",
-           "fctn_server_stats", "fctn_server_destroy"):
+           "fctn_server_stats", "fctn_server_destroy", "fctn_server_finished"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -367,6 +370,13 @@ def fctn_server_result(srv, job_id, out=None):
     p, w = _ptr(out)
     _check(lib.fctn_server_result(srv, ctypes.c_uint64(job_id), p, w))
     return out
+
+
+def fctn_server_finished(srv, cap=1024):
+    ids = (ctypes.c_uint64 * cap)()
+    n = ctypes.c_int(0)
+    _check(lib.fctn_server_finished(srv, ids, cap, ctypes.byref(n)))
+    return [ids[i] for i in range(n.value)]
 
 
 def fctn_server_stats(srv):

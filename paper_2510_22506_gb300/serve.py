@@ -86,13 +86,12 @@ def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_b
                 t_arr[j["i"]] = t0 + (j["arrival"] if arrivals else 0.0)
                 nxt += 1
             F.fctn_server_step(srv)
-            done = []
-            for jid, i in ids.items():
+            done = F.fctn_server_finished(srv)
+            tnow = time.perf_counter()
+            for jid in done:
                 info = F.fctn_server_poll(srv, jid)
-                if info["state"] in (F.FCTN_JOB_DONE, F.FCTN_JOB_FAILED):
-                    info["t_wall_done"] = time.perf_counter()
-                    infos[i] = info
-                    done.append(jid)
+                info["t_wall_done"] = tnow
+                infos[ids[jid]] = info
             for jid in done:
                 i = ids.pop(jid)
                 if infos[i]["state"] == F.FCTN_JOB_DONE:
