@@ -234,7 +234,22 @@ def run_ours(args):
     value = args.steps * ws / (total_ms / 1e3)
     peaks, peak_src = load_peaks()
     avg_ms = prof["ms"] / max(prof["launches"], 1)
-    if dom in ("gram", "merged", "solve", "eig") and prof["flops"] > 0:
+    svals = [int(np.prod([R[min(k, t), max(k, t)] for t in range(N) if t != k])) for k in range(N)]
+    if dom == "eig":
+        # one CTA by construction: the roof is one SM's FP32 FMA rate.  Algorithmic
+        # flops of one-sided Jacobi: warm start 6 s^3 + 9 s^2 (s-1) per sweep.
+        sw = max(int(st["eig_sweeps"]), 1)
+        flops = float(np.mean([6 * sv ** 3 + 9 * sw * sv * sv * (sv - 1) for sv in svals]))
+        bound, unit = "alu", "TFLOP/s"
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        peak = 128 * 2 * 2.07e9 / 1e12
+        peak_note = "derived: one SM, 128 FP32 lanes x 2 x 2.07 GHz (single-CTA kernel)"
+    elif dom == "gram" and precision in ("tf32", "bf16"):
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = prof["flops"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
+        peak_note = (f"{peak_src} dense BF16" + (" x nominal TF32/BF16 ratio 0.5" if precision == "tf32" else ""))
+    elif dom in ("gram", "merged", "solve") and prof["flops"] > 0:
         bound, unit = "alu", "TFLOP/s"
         achieved = prof["flops"] / max(prof["launches"], 1) / (avg_ms / 1e3) / 1e12
         peak = FP32_PEAK_TFLOPS if dt == np.float32 else 1.25
@@ -265,11 +280,58 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(d2h),
                 "step": f"set_data + set_factors from host, {e2e_sweeps} sweeps, X back to host"},
     }
+    if ws == 1 and not args.no_extras:
+        line["precision_modes"] = precision_modes(F, name, Y, mask, init, R, args.steps)
+        line["serving"] = serving_mix(args.serve_jobs)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def precision_modes(F, name, Y, mask, init, R, steps):
+    """Sweeps/s of the same workload in every precision (graphs, L2 flushed between sweeps)."""
+    import torch
+    out = {}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for prec in ("fp32", "tf32", "bf16"):
+        p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=prec)
+        st = torch.cuda.Stream()
+        h = F.fctn_create(p, st)
+        try:
+            F.fctn_set_data(h, np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8))
+            F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(np.float32)) for a in init])
+            tot = 0.0
+            with torch.cuda.stream(st):
+                for i in range(steps + 3):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    F.fctn_pam_sweep(h, 1, want_stats=False)
+                    b.record(st)
+                    flush.zero_()
+                    b.synchronize()
+                    if i >= 3:
+                        tot += a.elapsed_time(b)
+            out[prec] = steps / (tot / 1e3)
+        finally:
+            F.fctn_destroy(h)
+    return {"unit": UNIT, "sweeps_per_s": out, "workload": name}
+
+
+def serving_mix(n_jobs):
+    """Serving mix (Poisson 20 jobs/s; shapes 64x64x16, 128x128x31, 144x176x3x20,
+    256x256x31; ranks {3,4,6}; SR {0.05,0.1,0.2}; to rel < 1e-4, cap 500):
+    served concurrently in TF32 vs the same jobs one by one in plain FP32."""
+    from paper_2510_22506_gb300 import serve as S
+    jobs = S.mix_jobs(n_jobs, seed=5000, rate=20.0)
+    served = S.run_mix(jobs, precision="tf32", tol=1e-4, max_sweeps=500, max_jobs=32)
+    seq = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500)
+    keys = ("jobs", "failed", "wall_s", "jobs_per_s", "sweeps", "sweeps_per_s", "latency_p50_s", "latency_p99_s",
+            "ttt_p50_s", "ttt_p99_s")
+    return {"served_tf32": {k: served.get(k) for k in keys},
+            "sequential_fp32": {k: seq.get(k) for k in keys if k in seq},
+            "jobs_per_s_ratio": served["jobs_per_s"] / seq["jobs_per_s"]}
 
 
 def oracle_setup(name):
@@ -332,6 +394,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision and serving comparisons")
+    ap.add_argument("--serve-jobs", type=int, default=48)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -783,16 +783,16 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_a_f64(h->Q64[k], h->Yd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->st));
+           launch_solve_a_f64(h->Q64[k], h->Yd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 0, h->A64[k], (double*)h->Ac[k], h->st));
+           launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 0, h->A64[k], (double*)h->Ac[k], h->status, h->st));
     for (int r = 0; r < h->p.refine_steps; ++r) {
       LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
              launch_resid_f64(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, h->Rd, h->st));
       LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_a_f64(h->Q64[k], h->Rd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->st));
+             launch_solve_a_f64(h->Q64[k], h->Rd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
       LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 1, h->A64[k], (double*)h->Ac[k], h->st));
+             launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 1, h->A64[k], (double*)h->Ac[k], h->status, h->st));
     }
   } else {
     float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
@@ -812,16 +812,16 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
                           h->eig_used + k, h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_a_f32(h->Q32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->st));
+           launch_solve_a_f32(h->Q32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 0, h->A64[k], (float*)h->Ac[k], h->st));
+           launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 0, h->A64[k], (float*)h->Ac[k], h->status, h->st));
     for (int r = 0; r < h->p.refine_steps; ++r) {
       LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
              launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
       LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_a_f32(h->Q32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->st));
+             launch_solve_a_f32(h->Q32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
       LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 1, h->A64[k], (float*)h->Ac[k], h->st));
+             launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 1, h->A64[k], (float*)h->Ac[k], h->status, h->st));
     }
   }
   h->cvalid[k] = true;

@@ -131,13 +131,13 @@ void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s
                     double tmin, int* status, int* used, cudaStream_t st);
 // Eq. 8 by row blocks: Z = ((Q^T R) C) / T ; A = (Q Z) C^T into A64 (= or +=) and Ac.
 void launch_solve_a_f32(const float* Q, const float* R, const float* C, const double* LamL, const float* Phi,
-                        double lam, double rho, int I, int s, float* Z, cudaStream_t st);
+                        double lam, double rho, int I, int s, float* Z, int* status, cudaStream_t st);
 void launch_solve_a_f64(const double* Q, const double* R, const double* C, const double* LamL, const double* Phi,
-                        double lam, double rho, int I, int s, double* Z, cudaStream_t st);
+                        double lam, double rho, int I, int s, double* Z, int* status, cudaStream_t st);
 void launch_solve_b_f32(const float* Q, const float* Z, const float* C, int I, int s, int accumulate, double* A64,
-                        float* Ac, cudaStream_t st);
+                        float* Ac, int* status, cudaStream_t st);
 void launch_solve_b_f64(const double* Q, const double* Z, const double* C, int I, int s, int accumulate, double* A64,
-                        double* Ac, cudaStream_t st);
+                        double* Ac, int* status, cudaStream_t st);
 // FP64 residual of Eq. 5: R = Y - lam L A - rho A - A G (one CTA per row)
 void launch_resid_f32(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
                       double c0, double c1, float* R, cudaStream_t st);

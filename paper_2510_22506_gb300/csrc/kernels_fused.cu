@@ -16,6 +16,10 @@ namespace {
 
 constexpr int NT = 256;
 
+// Leading dimension of the formed tile: all 64-row output tiles, plus 4
+// (a multiple of 4, so rows start 16-byte aligned).
+__host__ __device__ __forceinline__ int gram_ldm(const GramPlan& g) { return g.tiles_r * 64 + 4; }
+
 __device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j) {
   uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
   uint32_t a = jj / post, b = jj - a * post;
@@ -56,6 +60,15 @@ __device__ __forceinline__ void form_tile(const PairPlan& p, const T* __restrict
   __syncthreads();
 }
 
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  float4 t = *(const float4*)p;
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* v) {
+  double2 t0 = *(const double2*)p, t1 = *(const double2*)(p + 2);
+  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
 // Asynchronous global -> shared copy of one element (zero-filled when !valid).
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
@@ -80,17 +93,17 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
                                                    T* __restrict__ Mout) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int s = (int)g.s;
-  const int ldm = s + 1;
+  const int ldm = gram_ldm(g);  // rows of the formed tile, padded to the 64-row tiles (zero beyond s)
   int* lo = (int*)sm;
   int* ro = lo + s;
   int* lk = ro + s;
   int* rk = lk + p.K;
   int64_t* cl = (int64_t*)(((uintptr_t)(rk + p.K) + 15) & ~(uintptr_t)15);  // [2][BK]
   int64_t* cr = cl + 2 * BK;                                                  // [2][BK]
-  T* Ls = (T*)(cr + 2 * BK);                    // [2][BK * Ljs]
+  T* Ms = (T*)(cr + 2 * BK);                    // BK x ldm, Ms[kk*ldm + sigma] (16-byte aligned)
+  T* Xs = Ms + (size_t)BK * ldm;                // [2][BK * 64]
+  T* Ls = Xs + (size_t)2 * BK * 64;             // [2][BK * Ljs]
   T* Rs = Ls + (size_t)2 * BK * p.Ljs;          // [2][BK * Rjs]
-  T* Xs = Rs + (size_t)2 * BK * p.Rjs;          // [2][BK * 64]
-  T* Ms = Xs + (size_t)2 * BK * 64;             // BK x ldm, Ms[kk*ldm + sigma]
   __shared__ int lsl[2][32], rsl[2][32], cnt[2][2];  // per stage: row slots of the columns, distinct-row counts
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < s; e += NT) {
@@ -107,6 +120,9 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   const bool write_m = Mout != nullptr && blockIdx.x == 0 && blockIdx.y == 0;
   const bool has_x = c0 + 64 > g.s;
   const int nchunk = (int)((ke - kb + BK - 1) / BK);
+  // steps of (row, column) when a flat index advances by NT
+  const int dqL = NT / p.Ljs, dcL = NT % p.Ljs, dqR = NT / p.Rjs, dcR = NT % p.Rjs;
+  const int dqS = NT / s, dcS = NT % s;
 
   // decode the columns of chunk c into buffer b (then a barrier), and issue its copies
   auto issue = [&](int c, int b) {
@@ -115,13 +131,23 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
     __syncthreads();
     T* ls = Ls + (size_t)b * BK * p.Ljs;
     T* rs = Rs + (size_t)b * BK * p.Rjs;
-    for (int e = tid; e < cnt[b][0] * p.Ljs; e += NT) {
-      int q = e / p.Ljs, c_ = e - q * p.Ljs;
-      cp_async_elem(ls + e, L + cl[b * BK + q] + c_, true);
+    {
+      int q = tid / p.Ljs, c_ = tid - q * p.Ljs;
+      for (int e = tid; e < cnt[b][0] * p.Ljs; e += NT) {
+        cp_async_elem(ls + e, L + cl[b * BK + q] + c_, true);
+        q += dqL;
+        c_ += dcL;
+        if (c_ >= p.Ljs) { c_ -= p.Ljs; ++q; }
+      }
     }
-    for (int e = tid; e < cnt[b][1] * p.Rjs; e += NT) {
-      int q = e / p.Rjs, c_ = e - q * p.Rjs;
-      cp_async_elem(rs + e, R + cr[b * BK + q] + c_, true);
+    {
+      int q = tid / p.Rjs, c_ = tid - q * p.Rjs;
+      for (int e = tid; e < cnt[b][1] * p.Rjs; e += NT) {
+        cp_async_elem(rs + e, R + cr[b * BK + q] + c_, true);
+        q += dqR;
+        c_ += dcR;
+        if (c_ >= p.Rjs) { c_ -= p.Rjs; ++q; }
+      }
     }
     if (has_x) {
       T* xs = Xs + (size_t)b * BK * 64;
@@ -149,6 +175,7 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int e = tid; e < BK * ldm; e += NT) Ms[e] = 0;  // rows >= s stay zero
   __syncthreads();
   if (nchunk > 0) issue(0, 0);
   for (int c = 0; c < nchunk; ++c) {
@@ -166,8 +193,8 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
     {
       const T* ls = Ls + (size_t)b * BK * p.Ljs;
       const T* rs = Rs + (size_t)b * BK * p.Rjs;
+      int jj = tid / s, sg = tid - jj * s;
       for (int e = tid; e < BK * s; e += NT) {
-        int jj = e / s, sg = e - jj * s;
         T a = 0;
         if (k0 + jj < ke) {
           const T* l = ls + lsl[b][jj] * p.Ljs + lo[sg];
@@ -175,6 +202,9 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
           for (int q = 0; q < p.K; ++q) a = fma(l[lk[q]], r[rk[q]], a);
         }
         Ms[jj * ldm + sg] = a;
+        jj += dqS;
+        sg += dcS;
+        if (sg >= s) { sg -= s; ++jj; }
       }
     }
     __syncthreads();
@@ -185,22 +215,35 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
       }
     }
     const T* xs = Xs + (size_t)b * BK * 64;
-    for (int kk = 0; kk < nb; ++kk) {
-      T av[4], bv[4];
+    const T* ap = Ms + r0 + ty * 4;  // rows >= s are zero in Ms
+    if (c0 + 64 <= g.s || c0 >= g.s) {
+      // the 64 columns of this tile are all Gram columns (from Ms) or all X rows (from xs)
+      const T* bp = (c0 + 64 <= g.s) ? Ms + c0 + tx * 4 : xs + tx * 4;
+      const int bstr = (c0 + 64 <= g.s) ? ldm : 64;
+#pragma unroll 4
+      for (int kk = 0; kk < nb; ++kk) {
+        T av[4], bv[4];
+        load4(ap + kk * ldm, av);
+        load4(bp + kk * bstr, bv);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        int64_t row = r0 + ty * 4 + a;
-        av[a] = row < g.s ? Ms[kk * ldm + row] : (T)0;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fma(av[a], bv[b2], acc[a][b2]);
       }
+    } else {
+      for (int kk = 0; kk < nb; ++kk) {
+        T av[4], bv[4];
+        load4(ap + kk * ldm, av);
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) {
-        int64_t col = c0 + tx * 4 + b2;
-        bv[b2] = col < g.s ? Ms[kk * ldm + col] : xs[kk * 64 + tx * 4 + b2];
+        for (int b2 = 0; b2 < 4; ++b2) {
+          int64_t col = c0 + tx * 4 + b2;
+          bv[b2] = col < g.s ? Ms[kk * ldm + col] : xs[kk * 64 + tx * 4 + b2];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fma(av[a], bv[b2], acc[a][b2]);
       }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fma(av[a], bv[b2], acc[a][b2]);
     }
     __syncthreads();
   }
@@ -320,8 +363,9 @@ size_t head_bytes(const PairPlan& p, int s, int nb) {
 }  // namespace
 
 size_t gram_fused_smem(const PairPlan& p, int s, int bk, int elem) {
-  // tables, 2 x column offsets, 2 x (L slab, R slab, X rows), formed tile
-  return head_bytes(p, s, 2 * bk) + (size_t)bk * (2 * (p.Ljs + p.Rjs + 64) + s + 1) * elem;
+  // tables, 2 x column offsets, formed tile, 2 x (X rows, L slab, R slab)
+  const int ldm = ((s + 63) / 64) * 64 + 4;
+  return head_bytes(p, s, 2 * bk) + (size_t)bk * (2 * (p.Ljs + p.Rjs + 64) + ldm) * elem;
 }
 
 int gram_fused_bk(const PairPlan& p, int s, int elem) {

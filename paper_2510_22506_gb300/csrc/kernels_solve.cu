@@ -27,7 +27,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // (m/2 disjoint pairs per round, m-1 rounds per sweep); a group of 8 lanes
 // owns one pair; a pair only touches its own two rows of A^T and V^T, so one
 // barrier per round suffices.  A pair is skipped once
-// |a_p . a_q| <= sqrt(s) eps |a_p| |a_q| + floor, floor = eps^2 ||G||_F^2 / s.
+// (a_p . a_q)^2 <= tol^2 |a_p|^2 |a_q|^2 + floor^2 with tol = sqrt(s) eps and
+// floor = eps^2 ||G||_F^2 / s.
 // Warm start: V0 (the previous sweep's C for the same factor) is first
 // re-orthonormalised by one Newton-Schulz step V0 (3I - V0^T V0)/2.
 // Also checks min_j Phi_j + tmin > 0 (T of Eq. 8 positive) -> FCTN_E_SINGULAR.
@@ -47,14 +48,16 @@ __device__ __forceinline__ T group_sum(T v) {
 // Rotation (cos, sin) that zeroes a_p . a_q: t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // zeta = (|a_q|^2 - |a_p|^2) / (2 a_p . a_q).  In FP32 the angle uses fast
 // approximations (an inexact angle only leaves the pair slightly less
-// orthogonal), while c = 1/sqrt(1 + t^2) is correctly rounded so that the
+// orthogonal), while c = 1/sqrt(1 + t^2) gets a Newton step so that the
 // rotation stays orthogonal to working precision.
 __device__ __forceinline__ void rot_cs(float al, float be, float ga, float& cs, float& sn) {
   float zeta = __fdividef(be - al, 2.f * ga);
   float w = fmaf(zeta, zeta, 1.f);
   float sq = w * rsqrtf(w);
   float t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sq);
-  cs = __frsqrt_rn(fmaf(t, t, 1.f));
+  float x = fmaf(t, t, 1.f);
+  float y = rsqrtf(x);
+  cs = y * fmaf(-0.5f * x * y, y, 1.5f);  // one Newton step: c^2 (1 + t^2) = 1 to about an ulp
   sn = cs * t;
 }
 __device__ __forceinline__ void rot_cs(double al, double be, double ga, double& cs, double& sn) {
@@ -128,9 +131,10 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
   const T tol = sqrt((T)(s > 1 ? s : 1)) * eps;
   // float4 rows: FP32, s a multiple of 4, rows 16-byte aligned (shared or
   // cudaMalloc'ed work, row stride s * 4 bytes)
-  const bool vec4 = (sizeof(T) == 4) && (s % 4 == 0);
+  const bool vec4 = (sizeof(T) == 4) && (s % 4 == 0) && (s <= 16 * EG);  // at most 4 float4 per lane per row
   const int s4 = s / 4;
   const T floor_abs = eps * eps * red[0] / (T)(s > 0 ? s : 1);
+  const T tol2 = tol * tol, floor2 = floor_abs * floor_abs;
   int sweep = 0;
   bool converged = (s <= 1);
   __shared__ float mu_max;  // largest (a_p.a_q)^2 / (|a_p|^2 |a_q|^2) rotated in this sweep
@@ -154,14 +158,22 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
         T* vp = Vt + (int64_t)p * s;
         T* vq = Vt + (int64_t)q * s;
         T al = 0, be = 0, ga = 0;
+        // rows of A kept in registers between the dot products and the rotation
+        float4 xr[4], yr[4];
         if (vec4) {
           const float4* p4 = (const float4*)ap;
           const float4* q4 = (const float4*)aq;
-          for (int c = gl; c < s4; c += EG) {
-            float4 x = p4[c], y = q4[c];
-            al = fma(x.x, x.x, fma(x.y, x.y, fma(x.z, x.z, fma(x.w, x.w, al))));
-            be = fma(y.x, y.x, fma(y.y, y.y, fma(y.z, y.z, fma(y.w, y.w, be))));
-            ga = fma(x.x, y.x, fma(x.y, y.y, fma(x.z, y.z, fma(x.w, y.w, ga))));
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = gl + u * EG;
+            if (c < s4) {
+              float4 x = p4[c], y = q4[c];
+              xr[u] = x;
+              yr[u] = y;
+              al = fma(x.x, x.x, fma(x.y, x.y, fma(x.z, x.z, fma(x.w, x.w, al))));
+              be = fma(y.x, y.x, fma(y.y, y.y, fma(y.z, y.z, fma(y.w, y.w, be))));
+              ga = fma(x.x, y.x, fma(x.y, y.y, fma(x.z, y.z, fma(x.w, y.w, ga))));
+            }
           }
         } else {
           for (int c = gl; c < s; c += EG) {
@@ -174,11 +186,11 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
         al = group_sum(al);
         be = group_sum(be);
         ga = group_sum(ga);
-        // rotate iff |ga| > tol sqrt(al be) + floor  (squared form, no sqrt)
-        const T thr = tol * sqrt(al * be) + floor_abs;
-        if (!(ga * ga > thr * thr)) continue;
+        // rotate iff ga^2 > tol^2 al be + floor^2 (products only)
+        const T ab = al * be, g2 = ga * ga;
+        if (!(g2 > tol2 * ab + floor2)) continue;
         any = 1;
-        mu_mine = fmaxf(mu_mine, (float)(ga * ga / (al * be)));  // squared ratio
+        mu_mine = fmaxf(mu_mine, (float)g2 * __frcp_rn((float)ab));  // squared ratio (ab > 0 here)
         T cs, sn;
         rot_cs(al, be, ga, cs, sn);
         if (vec4) {
@@ -186,8 +198,11 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
           float4* q4 = (float4*)aq;
           float4* u4 = (float4*)vp;
           float4* w4 = (float4*)vq;
-          for (int c = gl; c < s4; c += EG) {
-            float4 x = p4[c], y = q4[c], u = u4[c], w = w4[c];
+#pragma unroll
+          for (int uu = 0; uu < 4; ++uu) {
+            const int c = gl + uu * EG;
+            if (c >= s4) continue;
+            float4 x = xr[uu], y = yr[uu], u = u4[c], w = w4[c];
             p4[c] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w);
             q4[c] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w);
             u4[c] = make_float4(cs * u.x - sn * w.x, cs * u.y - sn * w.y, cs * u.z - sn * w.z, cs * u.w - sn * w.w);
@@ -283,6 +298,40 @@ void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, dou
 //             to it, for a refinement pass) and to the compute copy.
 constexpr int SB = 8;  // rows per CTA
 
+// One bulk copy global -> shared by the TMA engine (cp.async.bulk), completed
+// on an mbarrier by transaction bytes; thread 0 issues, every thread waits
+// (bounded: on expiry *status gets FCTN_E_TIMEOUT and the caller's loop
+// continues with whatever landed).  Needs 16-byte aligned addresses and a
+// size that is a multiple of 16.
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar, unsigned phase,
+                                          int* status) {
+  if (threadIdx.x == 0) {
+    // order the block's earlier generic-proxy accesses of dst before the async-proxy write
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
+  }
+  bool ok = false;
+  for (long long it = 0; it < (1ll << 26) && !ok; ++it) {
+    unsigned r;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(su32(bar)), "r"(phase));
+    ok = r != 0;
+  }
+  if (!ok && threadIdx.x == 0) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
+}
+
+__device__ __forceinline__ bool aligned16(const void* p, size_t bytes) {
+  return ((uintptr_t)p % 16 == 0) && (bytes % 16 == 0);
+}
+
 // Copy n contiguous elements global -> shared with several loads in flight.
 template <typename T>
 __device__ __forceinline__ void stage(T* __restrict__ dst, const T* __restrict__ src, int n) {
@@ -305,18 +354,31 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_solve_a(const T* __restrict__ Q, const T* __restrict__ Rm,
                                                  const T* __restrict__ C, const double* __restrict__ LamL,
                                                  const T* __restrict__ Phi, double lam, double rho, int I, int s,
-                                                 int NC, T* __restrict__ Z) {
+                                                 int NC, T* __restrict__ Z, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
-  T* W = (T*)sm;                   // SB x s
-  T* Rs = W + (size_t)SB * s;      // NC x s
-  T* Qs = Rs + (size_t)NC * s;     // NC x SB  (Qs[n][r] = Q[n0 + n][i0 + r])
+  __shared__ __align__(8) uint64_t bar;
+  T* Rs = (T*)sm;                  // NC x s (first: 16-byte aligned for the bulk copy)
+  T* W = Rs + (size_t)NC * s;      // SB x s
+  T* Qs = W + (size_t)SB * s;      // NC x SB  (Qs[n][r] = Q[n0 + n][i0 + r])
   const int i0 = blockIdx.x * SB;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
   for (int e = tid; e < SB * s; e += nt) W[e] = 0;
+  unsigned phase = 0;
   for (int n0 = 0; n0 < I; n0 += NC) {
     const int nc = min(NC, I - n0);
     __syncthreads();
-    stage(Rs, Rm + (int64_t)n0 * s, nc * s);
+    const T* src = Rm + (int64_t)n0 * s;
+    const size_t bytes = (size_t)nc * s * sizeof(T);
+    if (aligned16(src, bytes)) {
+      bulk_copy(Rs, src, (unsigned)bytes, &bar, phase, status);
+      phase ^= 1u;
+    } else {
+      stage(Rs, src, nc * s);
+    }
     for (int e = tid; e < nc * SB; e += nt) {
       int n = e / SB, r = e % SB;
       Qs[e] = (i0 + r < I) ? Q[(int64_t)(n0 + n) * I + i0 + r] : (T)0;
@@ -354,18 +416,31 @@ __global__ void __launch_bounds__(256) k_solve_a(const T* __restrict__ Q, const 
 template <typename T, typename Tc>
 __global__ void __launch_bounds__(256) k_solve_b(const T* __restrict__ Q, const T* __restrict__ Z,
                                                  const T* __restrict__ C, int I, int s, int NC, int accumulate,
-                                                 double* __restrict__ A64, Tc* __restrict__ Ac) {
+                                                 double* __restrict__ A64, Tc* __restrict__ Ac, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
-  T* U = (T*)sm;                   // SB x s
-  T* Zs = U + (size_t)SB * s;      // NC x s
-  T* Qs = Zs + (size_t)NC * s;     // SB x NC (Qs[r][n] = Q[i0 + r][n0 + n])
+  __shared__ __align__(8) uint64_t bar;
+  T* Zs = (T*)sm;                  // NC x s (first: 16-byte aligned for the bulk copy)
+  T* U = Zs + (size_t)NC * s;      // SB x s
+  T* Qs = U + (size_t)SB * s;      // SB x NC (Qs[r][n] = Q[i0 + r][n0 + n])
   const int i0 = blockIdx.x * SB;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
   for (int e = tid; e < SB * s; e += nt) U[e] = 0;
+  unsigned phase = 0;
   for (int n0 = 0; n0 < I; n0 += NC) {
     const int nc = min(NC, I - n0);
     __syncthreads();
-    stage(Zs, Z + (int64_t)n0 * s, nc * s);
+    const T* src = Z + (int64_t)n0 * s;
+    const size_t bytes = (size_t)nc * s * sizeof(T);
+    if (aligned16(src, bytes)) {
+      bulk_copy(Zs, src, (unsigned)bytes, &bar, phase, status);
+      phase ^= 1u;
+    } else {
+      stage(Zs, src, nc * s);
+    }
     for (int e = tid; e < SB * nc; e += nt) {
       int r = e / nc, n = e % nc;
       Qs[r * NC + n] = (i0 + r < I) ? Q[(int64_t)(i0 + r) * I + n0 + n] : (T)0;
@@ -502,34 +577,34 @@ void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s
   eig<double>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
 }
 void launch_solve_a_f32(const float* Q, const float* R, const float* C, const double* LamL, const float* Phi,
-                        double lam, double rho, int I, int s, float* Z, cudaStream_t st) {
+                        double lam, double rho, int I, int s, float* Z, int* status, cudaStream_t st) {
   int nc = solve_chunk(I, s, sizeof(float));
   size_t sb = solve_smem(I, s, nc, sizeof(float));
   if (sb > 48 * 1024) cudaFuncSetAttribute(k_solve_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_a<float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z);
+  k_solve_a<float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z, status);
 }
 void launch_solve_a_f64(const double* Q, const double* R, const double* C, const double* LamL, const double* Phi,
-                        double lam, double rho, int I, int s, double* Z, cudaStream_t st) {
+                        double lam, double rho, int I, int s, double* Z, int* status, cudaStream_t st) {
   int nc = solve_chunk(I, s, sizeof(double));
   size_t sb = solve_smem(I, s, nc, sizeof(double));
   if (sb > 48 * 1024) cudaFuncSetAttribute(k_solve_a<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_a<double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z);
+  k_solve_a<double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z, status);
 }
 void launch_solve_b_f32(const float* Q, const float* Z, const float* C, int I, int s, int accumulate, double* A64,
-                        float* Ac, cudaStream_t st) {
+                        float* Ac, int* status, cudaStream_t st) {
   int nc = solve_chunk(I, s, sizeof(float));
   size_t sb = solve_smem(I, s, nc, sizeof(float));
   if (sb > 48 * 1024)
     cudaFuncSetAttribute(k_solve_b<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_b<float, float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac);
+  k_solve_b<float, float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac, status);
 }
 void launch_solve_b_f64(const double* Q, const double* Z, const double* C, int I, int s, int accumulate, double* A64,
-                        double* Ac, cudaStream_t st) {
+                        double* Ac, int* status, cudaStream_t st) {
   int nc = solve_chunk(I, s, sizeof(double));
   size_t sb = solve_smem(I, s, nc, sizeof(double));
   if (sb > 48 * 1024)
     cudaFuncSetAttribute(k_solve_b<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_b<double, double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac);
+  k_solve_b<double, double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac, status);
 }
 void launch_resid_f32(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
                       double c0, double c1, float* R, cudaStream_t st) {
