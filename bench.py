@@ -109,6 +109,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def max_over_ranks(total_ms, dist, device=None):
+    """Timed-region length of the slowest rank (every rank gets it)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, world_size, total_ms):
+    """Whole-job sweeps/s: every rank ran `steps` sweeps of its own replica."""
+    return steps * world_size / (total_ms / 1e3)
+
+
 def gpu_inputs(F, name):
     """Workload inputs; the ground-truth contraction runs on the library's own path."""
     w = synth.WORKLOADS[name]
@@ -182,9 +195,7 @@ def run_ours(args):
         step_ms = [a.elapsed_time(b) for a, b in ev]
         total_ms = float(sum(step_ms))
         if ws > 1:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, dist, dev)
             dist.barrier()
         clk = clocks.stop()
         st = F.fctn_pam_sweep(h, 0)
@@ -231,7 +242,7 @@ def run_ours(args):
         if ws > 1:
             dist.destroy_process_group()
         return
-    value = args.steps * ws / (total_ms / 1e3)
+    value = job_value(args.steps, ws, total_ms)
     peaks, peak_src = load_peaks()
     avg_ms = prof["ms"] / max(prof["launches"], 1)
     svals = [int(np.prod([R[min(k, t), max(k, t)] for t in range(N) if t != k])) for k in range(N)]

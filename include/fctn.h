@@ -93,6 +93,8 @@ typedef struct fctn_params {
   double lambda[FCTN_MAX_ORDER];                  /* lambda_k > 0 (Eq. 1)              */
   double delta[FCTN_MAX_ORDER];                   /* delta_k > 0 (L_k)                 */
   double rho;                                     /* proximal weight rho > 0 (Eq. 3)   */
+  double extrap_alpha;  /* asymmetric extrapolation (Sec. 4.3): after each factor update */
+  double extrap_beta;   /* A <- A + alpha (A - beta A^(t)); alpha = 0 turns it off       */
 } fctn_params;
 
 typedef struct fctn_stats {

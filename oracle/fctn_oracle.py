@@ -387,8 +387,17 @@ def _merged(state, prob, k, reuse):
     return merged_sequential(state.factors, k, state.counter)
 
 
-def pam_sweep(state, prob, reuse=True, policy=ORDER_ALTERNATE, trace_blocks=False):
+def extrapolate(A_new, A_old, alpha, beta):
+    """Asymmetric extrapolation (Sec. 4.3): A + alpha (A - beta A^(t))."""
+    return A_new + alpha * (A_new - beta * A_old)
+
+
+def pam_sweep(state, prob, reuse=True, policy=ORDER_ALTERNATE, trace_blocks=False, extrapolation=None):
     """One PAM sweep (scheme 3): every A_k in order, then X (Algorithms 1/2).
+
+    ``extrapolation = (alpha, beta)`` replaces every new factor by its
+    asymmetric extrapolation right after its update (the multi-temporal HSI
+    variant of Sec. 4.3); None is the plain method.
 
     With ``reuse`` the merged tensors come from cached pair intermediates
     (N = 4) and FCTN(A^{t+1}) for the X update is A_last(last) M'_last, where
@@ -414,6 +423,8 @@ def pam_sweep(state, prob, reuse=True, policy=ORDER_ALTERNATE, trace_blocks=Fals
         Ak_old = unfold_factor(state.factors[k], k)
         G, Y = gram_rhs(Xk, Mk, Ak_old, prob.rho, counter=state.counter)
         Ak_new = solve_factor(G, Y, Ls[k], prob.lam[k], prob.rho, counter=state.counter)
+        if extrapolation is not None:
+            Ak_new = extrapolate(Ak_new, Ak_old, extrapolation[0], extrapolation[1])
         state.factors[k] = fold_factor(Ak_new, dims, prob.R, k)
         state.versions[k] += 1
         last_M = (k, Mk)
@@ -447,7 +458,7 @@ def pam_sweep(state, prob, reuse=True, policy=ORDER_ALTERNATE, trace_blocks=Fals
 
 
 def complete(Y, mask, factors, prob, tol=1e-4, max_sweeps=500, reuse=True,
-             policy=ORDER_ALTERNATE, callback=None):
+             policy=ORDER_ALTERNATE, callback=None, extrapolation=None):
     """Run sweeps until rel <= tol or max_sweeps (do-while, Algorithms 1/2).
 
     ``tol <= 0`` runs exactly ``max_sweeps`` sweeps.
@@ -455,7 +466,7 @@ def complete(Y, mask, factors, prob, tol=1e-4, max_sweeps=500, reuse=True,
     st = init_state(Y, mask, factors)
     hist = []
     while True:
-        info = pam_sweep(st, prob, reuse=reuse, policy=policy)
+        info = pam_sweep(st, prob, reuse=reuse, policy=policy, extrapolation=extrapolation)
         hist.append(info)
         if callback is not None:
             callback(st, info)

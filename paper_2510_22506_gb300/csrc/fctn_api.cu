@@ -102,7 +102,7 @@ struct fctn_handle {
   bool Tvalid[2] = {false, false};
   void* chain[2] = {nullptr, nullptr};
   void* part = nullptr;
-  double *Gd = nullptr, *Yd = nullptr, *Rd = nullptr;
+  double *Gd = nullptr, *Yd = nullptr, *Rd = nullptr, *Aprev = nullptr;
   void *Gs = nullptr, *Ys = nullptr, *C = nullptr, *Phi = nullptr, *W1 = nullptr, *Z = nullptr, *W2 = nullptr,
        *Rs = nullptr, *gwork = nullptr;
   int* status = nullptr;
@@ -714,7 +714,7 @@ size_t footprint(const fctn_handle* h) {
     b += h->I[k] * h->s[k] * (8 + e);                     // factors (FP64 master + compute copy)
     b += h->I[k] * h->I[k] * 12 + h->I[k] * 8;            // L_k basis
   }
-  b += 3 * z.Is * 8 + z.ss * 8;                           // Gd, Yd, Rd
+  b += 4 * z.Is * 8 + z.ss * 8;                           // Gd, Yd, Rd, previous factor
   size_t se = h->f64 ? 8 : 4;
   b += (2 * z.ss + z.maxs + 5 * z.Is) * se + 3 * z.ss * se;  // solve buffers + eigensolver work
   for (int k = 0; k < h->N; ++k) b += h->s[k] * h->s[k] * se;  // warm-start eigenvectors
@@ -773,6 +773,9 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   const double red_bytes = part_elems * e + (double)g.s * g.ncols * 8.0 * 2;
   const double solve_flops = 2.0 * ((double)I * I * s + (double)I * s * s);
   const double resid_flops = 2.0 * (double)I * s * s;
+  const bool extrap = h->p.extrap_alpha != 0.0;
+  if (extrap && !h->dry)
+    CK(cudaMemcpyAsync(h->Aprev, h->A64[k], (size_t)I * s * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   if (h->f64) {
     double *Ck = (double*)h->Ck[k], *Phi = (double*)h->Phi, *Z = (double*)h->Z;
     LAUNCH(FCTN_KC_GRAM, gram_bytes, gram_flops,
@@ -823,6 +826,16 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
              launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 1, h->A64[k], (float*)h->Ac[k], h->status, h->st));
     }
+  }
+  if (extrap) {
+    if (h->f64)
+      LAUNCH(FCTN_KC_SOLVE, 0.0, 0.0,
+             launch_extrap_f64(h->A64[k], h->Aprev, h->p.extrap_alpha, h->p.extrap_beta, (double*)h->Ac[k],
+                               (int64_t)I * s, h->st));
+    else
+      LAUNCH(FCTN_KC_SOLVE, 0.0, 0.0,
+             launch_extrap_f32(h->A64[k], h->Aprev, h->p.extrap_alpha, h->p.extrap_beta, (float*)h->Ac[k],
+                               (int64_t)I * s, h->st));
   }
   h->cvalid[k] = true;
   h->ver[k]++;
@@ -1064,6 +1077,7 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
   A_(h->Gd, z.ss * 8);
   A_(h->Yd, z.Is * 8);
   A_(h->Rd, z.Is * 8);
+  A_(h->Aprev, z.Is * 8);
   A_(h->Gs, z.ss * se);
   A_(h->Ys, z.Is * se);
   A_(h->C, z.ss * se);

@@ -143,6 +143,11 @@ void launch_resid_f32(const double* Y, const double* A, const double* G, int I, 
                       double c0, double c1, float* R, cudaStream_t st);
 void launch_resid_f64(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
                       double c0, double c1, double* R, cudaStream_t st);
+// asymmetric extrapolation A <- A + alpha (A - beta A_old) of the FP64 master and its compute copy
+void launch_extrap_f32(double* A, const double* Aold, double alpha, double beta, float* Ac, int64_t n,
+                       cudaStream_t st);
+void launch_extrap_f64(double* A, const double* Aold, double alpha, double beta, double* Ac, int64_t n,
+                       cudaStream_t st);
 // trace term lam/2 tr(A^T L A) for one factor (A: I x s double) -> out[0]
 void launch_trace_term(const double* A, int64_t I, int64_t s, double c0, double c1, double lam, double* out,
                        cudaStream_t st);

@@ -514,6 +514,19 @@ __global__ void __launch_bounds__(128) k_resid(const double* __restrict__ Y, con
   }
 }
 
+// Asymmetric extrapolation (Sec. 4.3): A <- A + alpha (A - beta A_old), FP64
+// master and compute copy.
+template <typename Tc>
+__global__ void k_extrap(double* __restrict__ A, const double* __restrict__ Aold, double alpha, double beta,
+                         Tc* __restrict__ Ac, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double a = A[e];
+    a += alpha * (a - beta * Aold[e]);
+    A[e] = a;
+    Ac[e] = (Tc)a;
+  }
+}
+
 // lam/2 * tr(A^T L A) partial sums; L is the cyclic stencil (c0 on the
 // diagonal, c1 on both neighbours, coinciding entries summed).
 __global__ void k_trace(const double* __restrict__ A, int64_t I, int64_t s, double c0, double c1, double lam,
@@ -620,4 +633,15 @@ void launch_trace_term(const double* A, int64_t I, int64_t s, double c0, double 
 }
 void launch_finalize(const double* red, int nblocks, const double* traces, int N, double* stats, cudaStream_t st) {
   k_finalize<<<1, 256, 0, st>>>(red, nblocks, traces, N, stats);
+}
+
+void launch_extrap_f32(double* A, const double* Aold, double alpha, double beta, float* Ac, int64_t n,
+                       cudaStream_t st) {
+  k_extrap<float><<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(A, Aold, alpha, beta,
+                                                                                            Ac, n);
+}
+void launch_extrap_f64(double* A, const double* Aold, double alpha, double beta, double* Ac, int64_t n,
+                       cudaStream_t st) {
+  k_extrap<double><<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(A, Aold, alpha,
+                                                                                             beta, Ac, n);
 }

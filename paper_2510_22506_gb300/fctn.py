@@ -42,6 +42,8 @@ class fctn_params(ctypes.Structure):
         ("lambda_", ctypes.c_double * MAX_ORDER),
         ("delta", ctypes.c_double * MAX_ORDER),
         ("rho", ctypes.c_double),
+        ("extrap_alpha", ctypes.c_double),
+        ("extrap_beta", ctypes.c_double),
     ]
 
 
@@ -149,7 +151,7 @@ def fctn_version():
 
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
-                laplacian_sign="psd", refine_steps=None):
+                laplacian_sign="psd", refine_steps=None, extrapolation=None):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -171,6 +173,8 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
             if t != k:
                 p.ranks[min(k, t)][max(k, t)] = int(R[min(k, t)][max(k, t)])
     p.rho = float(rho)
+    if extrapolation is not None:
+        p.extrap_alpha, p.extrap_beta = float(extrapolation[0]), float(extrapolation[1])
     return p
 
 

@@ -189,3 +189,14 @@ def test_device_pointer_path_and_stream(F):
     finally:
         F.fctn_destroy(h)
     assert rel(X.cpu().numpy(), st.X) <= 1e-9
+
+
+@pytest.mark.parametrize("dims,r,cap", [((30, 30, 10), 3, None), ((13, 7, 3, 5), 3, (3, 2))])
+def test_fp64_asymmetric_extrapolation_matches_oracle(F, dims, r, cap):
+    """The multi-temporal variant (Sec. 4.3): alpha = beta = 0.5 after every factor update."""
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=46, noise=0.0, cap=cap)
+    st, _ = oracle_run(d, 15, extrapolation=(0.5, 0.5))
+    g = gpu_run(F, d, 15, precision="fp64", extrapolation=(0.5, 0.5))
+    assert rel(g["X"], st.X) <= 1e-9, rel(g["X"], st.X)
+    for a, b in zip(g["factors"], st.factors):
+        assert rel(a, b) <= 1e-9

@@ -365,3 +365,39 @@ def test_do_while_runs_at_least_one_sweep_and_caps():
     assert len(hist) == 1
     st, hist = O.complete(Y, mask, init, prob, tol=0, max_sweeps=7)
     assert len(hist) == 7 and st.t == 7
+
+
+# ------------------------------------------------ extrapolation (Sec. 4.3) --
+def test_extrapolation_alpha0_is_the_plain_method():
+    _, Y, mask, init, prob = _small_problem((8, 9, 5), 3)
+    a, _ = O.complete(Y, mask, init, prob, tol=0, max_sweeps=5, extrapolation=(0.0, 0.5))
+    b, _ = O.complete(Y, mask, init, prob, tol=0, max_sweeps=5)
+    np.testing.assert_array_equal(a.X, b.X)
+
+
+def test_extrapolation_step_is_alpha_times_the_proximal_gradient_step():
+    """With beta = 1 the extrapolation adds alpha (A^{t+1} - A^t), and by the
+    relative-error identity of Theorem 2 (condition 5) A^{t+1} - A^t equals
+    -(1/rho) grad_{A_k} f at the new block point: probed by central differences."""
+    dims, r = (6, 7, 4), 2
+    _, Y, mask, init, prob = _small_problem(dims, r)
+    st = O.init_state(Y, mask, init)
+    O.pam_sweep(st, prob)
+    Ls = [O.laplacian(dims[k], 0.5, "psd") for k in range(3)]
+    alpha, k = 0.5, 0
+    Mk = O.merged_matrix(O.merged_sequential(st.factors, k), dims, prob.R, k)
+    Aold = O.unfold_factor(st.factors[k], k)
+    G, Yr = O.gram_rhs(O.unfold_tensor(st.X, k), Mk, Aold, prob.rho)
+    Anew = O.solve_factor(G, Yr, Ls[k], prob.lam[k], prob.rho)
+    Aext = O.extrapolate(Anew, Aold, alpha, 1.0)
+    rng = np.random.default_rng(5)
+    fs = list(st.factors)
+    fs[k] = O.fold_factor(Anew, dims, prob.R, k)
+    for _ in range(3):
+        D = rng.standard_normal(Anew.shape)
+        h = 1e-3
+        fp = list(fs); fp[k] = O.fold_factor(Anew + h * D, dims, prob.R, k)
+        fm = list(fs); fm[k] = O.fold_factor(Anew - h * D, dims, prob.R, k)
+        grad_D = (O.objective(st.X, fp, Ls, prob.lam) - O.objective(st.X, fm, Ls, prob.lam)) / (2 * h)
+        step_D = float(np.sum((Aext - Anew) * D))
+        assert abs(step_D - (-alpha / prob.rho) * grad_D) <= 1e-6 * max(1.0, abs(step_D))

@@ -20,18 +20,20 @@ def inputs(name=None, dtype=np.float64, **over):
     return dict(truth=truth, Y=Yc, mask=mask, init=initc, R=R, dims=tuple(Y.shape))
 
 
-def oracle_run(d, sweeps, lam=0.01, delta=0.5, rho=0.1, reuse=True, policy="alternate", sign="psd"):
+def oracle_run(d, sweeps, lam=0.01, delta=0.5, rho=0.1, reuse=True, policy="alternate", sign="psd",
+               extrapolation=None):
     N = len(d["dims"])
     prob = O.Problem(dims=d["dims"], R=d["R"], lam=(lam,) * N, delta=(delta,) * N, rho=rho, sign=sign)
     st, hist = O.complete(d["Y"].astype(np.float64), d["mask"], [a.astype(np.float64) for a in d["init"]], prob,
-                          tol=0, max_sweeps=sweeps, reuse=reuse, policy=policy)
+                          tol=0, max_sweeps=sweeps, reuse=reuse, policy=policy, extrapolation=extrapolation)
     return st, hist
 
 
 def gpu_run(F, d, sweeps, precision="fp64", lam=0.01, delta=0.5, rho=0.1, reuse=True, policy="alternate",
-            sign="psd", refine_steps=None, stats_every=None):
+            sign="psd", refine_steps=None, stats_every=None, extrapolation=None):
     p = F.make_params(d["dims"], d["R"], lam=lam, delta=delta, rho=rho, precision=precision, reuse=reuse,
-                      order_policy=policy, laplacian_sign=sign, refine_steps=refine_steps)
+                      order_policy=policy, laplacian_sign=sign, refine_steps=refine_steps,
+                      extrapolation=extrapolation)
     dt = F.elem_dtype(p)
     h = F.fctn_create(p)
     try:
