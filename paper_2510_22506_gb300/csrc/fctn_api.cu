@@ -87,6 +87,8 @@ struct fctn_handle {
   void* Ac[FCTN_MAX_ORDER] = {};
   double* Q64[FCTN_MAX_ORDER] = {};
   float* Q32[FCTN_MAX_ORDER] = {};
+  double* QT64[FCTN_MAX_ORDER] = {};  // Q^T (rows = eigenvectors), for the forward solve
+  float* QT32[FCTN_MAX_ORDER] = {};
   double* Lam[FCTN_MAX_ORDER] = {};
   void* M = nullptr;              // merged tensor of the factor updated last (Algorithm 2 reuse)
   bool mat[FCTN_MAX_ORDER] = {};  // M_k is small enough to keep for the X update
@@ -712,7 +714,7 @@ size_t footprint(const fctn_handle* h) {
   b += z.part * e;                                        // split-K partials
   for (int k = 0; k < h->N; ++k) {
     b += h->I[k] * h->s[k] * (8 + e);                     // factors (FP64 master + compute copy)
-    b += h->I[k] * h->I[k] * 12 + h->I[k] * 8;            // L_k basis
+    b += h->I[k] * h->I[k] * 24 + h->I[k] * 8;            // L_k basis and its transpose
   }
   b += 4 * z.Is * 8 + z.ss * 8;                           // Gd, Yd, Rd, previous factor
   size_t se = h->f64 ? 8 : 4;
@@ -771,7 +773,8 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   const double gram_bytes = (double)h->P * e + part_elems * e + (Mout ? (double)g.s * g.Pk * e : 0.0);
   const double gram_flops = 2.0 * (double)g.s * (double)g.ncols * (double)g.Pk;
   const double red_bytes = part_elems * e + (double)g.s * g.ncols * 8.0 * 2;
-  const double solve_flops = 2.0 * ((double)I * I * s + (double)I * s * s);
+  const double fwd_flops = 2.0 * ((double)I * I * s + 2.0 * (double)I * s * s);  // Q^T R, then C and C^T
+  const double bwd_flops = 2.0 * (double)I * I * s;                              // Q W
   const double resid_flops = 2.0 * (double)I * s * s;
   const bool extrap = h->p.extrap_alpha != 0.0;
   if (extrap && !h->dry)
@@ -785,17 +788,23 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
            launch_reduce_gram_rhs_f64((const double*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, h->st));
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_a_f64(h->Q64[k], h->Yd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 0, h->A64[k], (double*)h->Ac[k], h->status, h->st));
-    for (int r = 0; r < h->p.refine_steps; ++r) {
-      LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
-             launch_resid_f64(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, h->Rd, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_a_f64(h->Q64[k], h->Rd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_b_f64(h->Q64[k], Z, Ck, I, s, 1, h->A64[k], (double*)h->Ac[k], h->status, h->st));
+    // Eq. 8, then refinement passes on the FP64 residual of Eq. 5 (the
+    // first residual is fused into the first backward pass)
+    const int nref = h->p.refine_steps;
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+           launch_solve_fwd_f64(h->QT64[k], h->Yd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
+           launch_solve_bwd_f64(h->Q64[k], Z, I, s, 0, h->A64[k], (double*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
+                                nref > 0 ? h->Rd : nullptr, h->status, h->st));
+    for (int r = 0; r < nref; ++r) {
+      if (r > 0)
+        LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
+               launch_resid_f64(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, h->Rd, h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+             launch_solve_fwd_f64(h->QT64[k], h->Rd, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
+             launch_solve_bwd_f64(h->Q64[k], Z, I, s, 1, h->A64[k], (double*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
+                                  c1, nullptr, h->status, h->st));
     }
   } else {
     float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
@@ -814,17 +823,23 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
                           h->eig_used + k, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_a_f32(h->Q32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-           launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 0, h->A64[k], (float*)h->Ac[k], h->status, h->st));
-    for (int r = 0; r < h->p.refine_steps; ++r) {
-      LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
-             launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_a_f32(h->Q32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, solve_flops,
-             launch_solve_b_f32(h->Q32[k], Z, Ck, I, s, 1, h->A64[k], (float*)h->Ac[k], h->status, h->st));
+    const int nref = h->p.refine_steps;
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+           launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
+                                h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
+           launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
+                                nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
+    for (int r = 0; r < nref; ++r) {
+      if (r > 0)
+        LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
+               launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+             launch_solve_fwd_f32(h->QT32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
+                                  h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
+             launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
+                                  c1, nullptr, h->status, h->st));
     }
   }
   if (extrap) {
@@ -1072,6 +1087,8 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     A_(h->Ac[k], h->I[k] * h->s[k] * e);
     A_(h->Q64[k], h->I[k] * h->I[k] * 8);
     A_(h->Q32[k], h->I[k] * h->I[k] * 4);
+    A_(h->QT64[k], h->I[k] * h->I[k] * 8);
+    A_(h->QT32[k], h->I[k] * h->I[k] * 4);
     A_(h->Lam[k], h->I[k] * 8);
   }
   A_(h->Gd, z.ss * 8);
@@ -1130,7 +1147,8 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
       if (v < mn) mn = v;
     }
     h->lam_min[k] = mn;
-    launch_laplacian_basis(h->I[k], p->delta[k], p->laplacian_sign, h->Q64[k], h->Q32[k], h->Lam[k], h->st);
+    launch_laplacian_basis(h->I[k], p->delta[k], p->laplacian_sign, h->Q64[k], h->Q32[k], h->QT64[k], h->QT32[k],
+                           h->Lam[k], h->st);
     h->launches++;
   }
   cudaError_t ce = cudaMemsetAsync(h->status, 0, 16, h->st);

@@ -98,7 +98,8 @@ cudaStream_t fctn_internal_stream(fctn_handle* h);
 // ---- kernels_contract.cu ---------------------------------------------------
 void launch_contract_f32(const float* A, const float* B, float* out, const ContractPlan& p, cudaStream_t s);
 void launch_contract_f64(const double* A, const double* B, double* out, const ContractPlan& p, cudaStream_t s);
-void launch_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* Lam, cudaStream_t s);
+void launch_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* QT, float* QTf, double* Lam,
+                            cudaStream_t s);
 void launch_init_x_mask_f32(const float* Y, const uint8_t* mask, float* X, uint32_t* bits, int64_t n, cudaStream_t s);
 void launch_init_x_mask_f64(const double* Y, const uint8_t* mask, double* X, uint32_t* bits, int64_t n, cudaStream_t s);
 void launch_convert_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
@@ -129,15 +130,19 @@ void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, in
                     double tmin, int* status, int* used, cudaStream_t st);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
-// Eq. 8 by row blocks: Z = ((Q^T R) C) / T ; A = (Q Z) C^T into A64 (= or +=) and Ac.
-void launch_solve_a_f32(const float* Q, const float* R, const float* C, const double* LamL, const float* Phi,
-                        double lam, double rho, int I, int s, float* Z, int* status, cudaStream_t st);
-void launch_solve_a_f64(const double* Q, const double* R, const double* C, const double* LamL, const double* Phi,
-                        double lam, double rho, int I, int s, double* Z, int* status, cudaStream_t st);
-void launch_solve_b_f32(const float* Q, const float* Z, const float* C, int I, int s, int accumulate, double* A64,
-                        float* Ac, int* status, cudaStream_t st);
-void launch_solve_b_f64(const double* Q, const double* Z, const double* C, int I, int s, int accumulate, double* A64,
-                        double* Ac, int* status, cudaStream_t st);
+// Eq. 8 by row blocks.  fwd: W = (((Q^T R) C) / T) C^T.  bwd: A = Q W into
+// A64 (= or +=) and Ac; with Rout != null (accumulate = 0 only) also the
+// FP64 residual of Eq. 5, Rout = Yd - lam L A - rho A - A Gd, for the new A.
+void launch_solve_fwd_f32(const float* QT, const float* R, const float* C, const double* LamL, const float* Phi,
+                          double lam, double rho, int I, int s, float* W, int* status, cudaStream_t st);
+void launch_solve_fwd_f64(const double* QT, const double* R, const double* C, const double* LamL, const double* Phi,
+                          double lam, double rho, int I, int s, double* W, int* status, cudaStream_t st);
+void launch_solve_bwd_f32(const float* Q, const float* W, int I, int s, int accumulate, double* A64, float* Ac,
+                          const double* Yd, const double* Gd, double lam, double rho, double c0, double c1, float* Rout,
+                          int* status, cudaStream_t st);
+void launch_solve_bwd_f64(const double* Q, const double* W, int I, int s, int accumulate, double* A64, double* Ac,
+                          const double* Yd, const double* Gd, double lam, double rho, double c0, double c1,
+                          double* Rout, int* status, cudaStream_t st);
 // FP64 residual of Eq. 5: R = Y - lam L A - rho A - A G (one CTA per row)
 void launch_resid_f32(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
                       double c0, double c1, float* R, cudaStream_t st);

@@ -115,7 +115,8 @@ void contract(const T* A, const T* B, T* out, const ContractPlan& p, cudaStream_
 // (2j-1, 2j): cos / sin of frequency j; for even I the last column is the
 // alternating vector.  Eigenvalue of frequency j: sgn*(2 + delta - 2cos(2 pi j/I)),
 // which also covers I <= 2 where the stencil entries add up.
-__global__ void k_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* Lam) {
+__global__ void k_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* QT, float* QTf,
+                                  double* Lam) {
   const double sgn = sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
   const int64_t total = I * I;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -133,6 +134,8 @@ __global__ void k_laplacian_basis(int64_t I, double delta, int sign, double* Q, 
     }
     Q[e] = v;
     if (Qf) Qf[e] = (float)v;
+    if (QT) QT[col * I + n] = v;
+    if (QTf) QTf[col * I + n] = (float)v;
     if (n == 0) {
       int64_t j = (col == 0) ? 0 : ((I % 2 == 0 && col == I - 1) ? I / 2 : (col + 1) / 2);
       Lam[col] = sgn * (2.0 + delta - 2.0 * cospi(2.0 * (double)j / (double)I));
@@ -181,8 +184,9 @@ void launch_contract_f32(const float* A, const float* B, float* out, const Contr
 void launch_contract_f64(const double* A, const double* B, double* out, const ContractPlan& p, cudaStream_t s) {
   contract<double>(A, B, out, p, s);
 }
-void launch_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* Lam, cudaStream_t s) {
-  k_laplacian_basis<<<grid_for(I * I), 256, 0, s>>>(I, delta, sign, Q, Qf, Lam);
+void launch_laplacian_basis(int64_t I, double delta, int sign, double* Q, float* Qf, double* QT, float* QTf, double* Lam,
+                            cudaStream_t s) {
+  k_laplacian_basis<<<grid_for(I * I), 256, 0, s>>>(I, delta, sign, Q, Qf, QT, QTf, Lam);
 }
 void launch_init_x_mask_f32(const float* Y, const uint8_t* mask, float* X, uint32_t* bits, int64_t n,
                             cudaStream_t s) {

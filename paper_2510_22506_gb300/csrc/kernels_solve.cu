@@ -3,6 +3,8 @@
 // reductions of the objective (Eq. 2) and the stop test.
 #include <float.h>
 
+#include <algorithm>
+
 #include "fctn_internal.cuh"
 
 namespace {
@@ -255,6 +257,325 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
   }
 }
 
+// ---------------------------------------- two-sided Jacobi, FP32, s <= 132 ----
+// The same decomposition G = C Phi C^T (Eq. 7) by the classical two-sided
+// cyclic Jacobi method on B = V^T G V (Jacobi 1846; parallel round-robin
+// order as in Golub & Van Loan, Sec. 8.5): each rotation J(p, q) zeroes
+// B_pq, B <- J^T B J, V <- V J; at convergence Phi = diag(B), C = V.
+// Warm start: V = V0 (3I - V0^T V0)/2 (one Newton-Schulz step on the previous
+// sweep's C), B = V^T (G V).
+// Layout, one CTA: the index set is padded to m = s rounded up to 4 (the
+// padding rows/columns of B are zero and never rotate).  A round is two
+// phases.  (A) every pair k of the round is (p_k, q_k) with rotation
+// (c_k, s_k); a thread owns the 2x2 blocks (rows of pair k, columns of pair
+// l), k <= l, and replaces them in place by J_k^T X J_l (both triangles), and
+// rotates rows p_k, q_k of V^T (float4 along r); blocks and rows of pairs
+// that do not rotate are left alone.  (B) one thread per pair of the next
+// round reads B_pp, B_qq, B_pq and sets its rotation.
+// Rotation test and stop test as in k_eig1, on B: rotate iff
+// B_pq^2 > tol^2 |B_pp B_qq| + floor^2 (tol = sqrt(s) eps, floor =
+// eps ||G||_F / sqrt(s)); stop after a sweep whose largest rotated
+// B_pq^2 / |B_pp B_qq| was below tol (quadratic convergence).
+constexpr int EIG2_MAX = 132;
+constexpr int EIG2_PT = 3;  // B blocks and V units per thread: 66 * 67 / 2 <= 3 * 1024
+
+struct __align__(16) PairRot {
+  int p, q;
+  float c, sn;
+};
+
+__device__ __forceinline__ void round_pair(int m, int round, int idx, int& p, int& q) {
+  if (idx == 0) {
+    p = m - 1;
+    q = round;
+  } else {
+    p = round + idx;
+    if (p >= m - 1) p -= m - 1;
+    q = round - idx;
+    if (q < 0) q += m - 1;
+  }
+  if (p > q) {
+    int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// out[i][j] = ca * sum_k op(X)[i][k] Y[k][j] (+ cb * Add[i][j]) for i, j < m,
+// op(X) = X or X^T; m % 4 == 0.  Each thread owns rows {ti, ti + m/2} x
+// columns {tj + u m/4}: the Y loads of a warp are consecutive words.
+template <bool TN>
+__device__ __forceinline__ void sm_mm(float* __restrict__ out, int so, const float* __restrict__ X, int sx,
+                                      const float* __restrict__ Y, int sy, int m, float ca,
+                                      const float* __restrict__ Add, int sa, float cb) {
+  const int mh = m / 2, mq = m / 4, ntile = mh * mq;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+    const int ti = t / mq, tj = t % mq;
+    float a00 = 0.f, a01 = 0.f, a02 = 0.f, a03 = 0.f, a10 = 0.f, a11 = 0.f, a12 = 0.f, a13 = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < m; ++k) {
+      float x0, x1;
+      if (TN) {
+        x0 = X[k * sx + ti];
+        x1 = X[k * sx + ti + mh];
+      } else {
+        x0 = X[ti * sx + k];
+        x1 = X[(ti + mh) * sx + k];
+      }
+      const float* yr = Y + k * sy + tj;
+      const float y0 = yr[0], y1 = yr[mq], y2 = yr[2 * mq], y3 = yr[3 * mq];
+      a00 = fmaf(x0, y0, a00);
+      a01 = fmaf(x0, y1, a01);
+      a02 = fmaf(x0, y2, a02);
+      a03 = fmaf(x0, y3, a03);
+      a10 = fmaf(x1, y0, a10);
+      a11 = fmaf(x1, y1, a11);
+      a12 = fmaf(x1, y2, a12);
+      a13 = fmaf(x1, y3, a13);
+    }
+    const float r0[4] = {a00, a01, a02, a03}, r1[4] = {a10, a11, a12, a13};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = tj + u * mq;
+      float v0 = ca * r0[u], v1 = ca * r1[u];
+      if (Add) {
+        v0 = fmaf(cb, Add[ti * sa + j], v0);
+        v1 = fmaf(cb, Add[(ti + mh) * sa + j], v1);
+      }
+      out[ti * so + j] = v0;
+      out[(ti + mh) * so + j] = v1;
+    }
+  }
+}
+
+// Rotation of pair (p, q) of round `round` from the current B.  Returns
+// B_pq^2 / |B_pp B_qq| if the pair rotates, else -1.
+__device__ __forceinline__ float set_rot(const float* __restrict__ B, int sb, int m, int round, int k, float tol2,
+                                         float floor2, PairRot* __restrict__ pt) {
+  int p, q;
+  round_pair(m, round, k, p, q);
+  const float bpp = B[p * sb + p], bqq = B[q * sb + q], bpq = B[p * sb + q];
+  const float ab = fabsf(bpp * bqq), g2 = bpq * bpq;
+  float c = 1.f, sn = 0.f, mu = -1.f;
+  if (g2 > tol2 * ab + floor2) {
+    rot_cs(bpp, bqq, bpq, c, sn);
+    mu = g2 / fmaxf(ab, FLT_MIN);
+  }
+  pt[k] = {p, q, c, sn};
+  return mu;
+}
+
+__global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, float* __restrict__ Cio,
+                                               float* __restrict__ Phi, int s, int warm, int max_sweeps, double tmin,
+                                               int* status, int* sweeps_used) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int m = (s + 3) & ~3, sp = m + 4, sb = m + 1, npair = m / 2, m4 = m / 4;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* X1 = (float*)sm;
+  float* X2 = X1 + m * sp;
+  float* X3 = X2 + m * sp;
+  PairRot* pt = (PairRot*)(X3 + m * sp);  // [npair]
+  __shared__ float red[32];
+  __shared__ unsigned wrot[3], wmu[3];  // per angle warp: rotations and largest ratio of a sweep
+  // ||G||_F
+  float fr = 0.f;
+  for (int e = tid; e < s * s; e += nt) fr = fmaf(G[e], G[e], fr);
+  fr = warp_sum(fr);
+  if ((tid & 31) == 0) red[tid >> 5] = fr;
+  // B in X1 (stride sb), V^T in X2 (stride sp)
+  if (warm) {
+    for (int e = tid; e < m * m; e += nt) {  // X1 <- V0 (row r, column j), zero padded
+      const int r = e / m, j = e % m;
+      X1[r * sp + j] = (r < s && j < s) ? Cio[r * s + j] : 0.f;
+    }
+    __syncthreads();
+    sm_mm<true>(X2, sp, X1, sp, X1, sp, m, 1.f, nullptr, 0, 0.f);  // S = V0^T V0
+    __syncthreads();
+    sm_mm<false>(X3, sp, X1, sp, X2, sp, m, -0.5f, X1, sp, 1.5f);  // V = 1.5 V0 - 0.5 V0 S
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {  // X1 <- G
+      const int r = e / m, j = e % m;
+      X1[r * sp + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
+    }
+    __syncthreads();
+    sm_mm<false>(X2, sp, X1, sp, X3, sp, m, 1.f, nullptr, 0, 0.f);  // W = G V
+    __syncthreads();
+    sm_mm<true>(X1, sb, X3, sp, X2, sp, m, 1.f, nullptr, 0, 0.f);  // B = V^T W
+    __syncthreads();
+    for (int e = tid; e < m * m; e += nt) {  // V^T
+      const int r = e / m, j = e % m;
+      X2[j * sp + r] = X3[r * sp + j];
+    }
+  } else {
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = e / m, j = e % m;
+      X1[r * sb + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
+      X2[r * sp + j] = (r == j) ? 1.f : 0.f;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += nt) {  // symmetrise B
+    const int r = e / m, j = e % m;
+    if (r < j) {
+      const float v = 0.5f * (X1[r * sb + j] + X1[j * sb + r]);
+      X1[r * sb + j] = v;
+      X1[j * sb + r] = v;
+    }
+  }
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nt / 32; ++w) t += red[w];
+    red[0] = sqrtf(t);
+  }
+  __syncthreads();
+  const float eps = FLT_EPSILON;
+  const float tol = sqrtf((float)(s > 1 ? s : 1)) * eps;
+  const float tol2 = tol * tol;
+  const float floor_abs = eps * red[0] * rsqrtf((float)(s > 0 ? s : 1));
+  const float floor2 = floor_abs * floor_abs;
+  float* B = X1;
+  float* Vt = X2;
+  // this thread's B blocks (k, l), k <= l, row-major over the upper triangle
+  // (a warp reads consecutive columns of the same rows), and V^T units
+  // (pair k, float4 column c4)
+  const int nblk = npair * (npair + 1) / 2, nvec = npair * m4;
+  int kl[EIG2_PT], vu[EIG2_PT];
+#pragma unroll
+  for (int i = 0; i < EIG2_PT; ++i) {
+    int b = tid + i * nt, k = 0;
+    if (b < nblk) {
+      while (b >= npair - k) {
+        b -= npair - k;
+        ++k;
+      }
+      kl[i] = k | ((k + b) << 16);
+    } else {
+      kl[i] = -1;
+    }
+    const int u = tid + i * nt;
+    vu[i] = u < nvec ? ((u / m4) | ((u % m4) << 16)) : -1;
+  }
+  // rotation count and largest ratio of the current and of the next sweep,
+  // per angle thread (tid < npair <= 66: at most three warps)
+  const int nw = (npair + 31) / 32;
+  unsigned c_cnt = 0, n_cnt = 0;
+  float c_mu = 0.f, n_mu = 0.f;
+  if (tid < npair) {
+    const float mu = set_rot(B, sb, m, 0, tid, tol2, floor2, pt);
+    if (mu >= 0.f) {
+      ++c_cnt;
+      c_mu = mu;
+    }
+  }
+  __syncthreads();
+  int sweep = 0;
+  bool converged = (s <= 1);
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    for (int round = 0; round < m - 1; ++round) {
+      // (A) rotate the blocks and V^T rows of this round's rotating pairs
+#pragma unroll
+      for (int i = 0; i < EIG2_PT; ++i) {
+        if (kl[i] < 0) break;
+        const int k = kl[i] & 0xffff, l = kl[i] >> 16;
+        const PairRot rk = pt[k];
+        if (k == l) {
+          if (rk.sn == 0.f) continue;
+          const float a = B[rk.p * sb + rk.p], bq = B[rk.q * sb + rk.q], g = B[rk.p * sb + rk.q];
+          const float t = rk.sn / rk.c;
+          B[rk.p * sb + rk.p] = fmaf(-t, g, a);
+          B[rk.q * sb + rk.q] = fmaf(t, g, bq);
+          B[rk.p * sb + rk.q] = 0.f;
+          B[rk.q * sb + rk.p] = 0.f;
+        } else {
+          const PairRot rl = pt[l];
+          if (rk.sn == 0.f && rl.sn == 0.f) continue;
+          const float x00 = B[rk.p * sb + rl.p], x01 = B[rk.p * sb + rl.q];
+          const float x10 = B[rk.q * sb + rl.p], x11 = B[rk.q * sb + rl.q];
+          const float y00 = rk.c * x00 - rk.sn * x10, y01 = rk.c * x01 - rk.sn * x11;
+          const float y10 = rk.sn * x00 + rk.c * x10, y11 = rk.sn * x01 + rk.c * x11;
+          const float z00 = rl.c * y00 - rl.sn * y01, z01 = rl.sn * y00 + rl.c * y01;
+          const float z10 = rl.c * y10 - rl.sn * y11, z11 = rl.sn * y10 + rl.c * y11;
+          B[rk.p * sb + rl.p] = z00;
+          B[rk.p * sb + rl.q] = z01;
+          B[rk.q * sb + rl.p] = z10;
+          B[rk.q * sb + rl.q] = z11;
+          B[rl.p * sb + rk.p] = z00;
+          B[rl.q * sb + rk.p] = z01;
+          B[rl.p * sb + rk.q] = z10;
+          B[rl.q * sb + rk.q] = z11;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < EIG2_PT; ++i) {
+        if (vu[i] < 0) break;
+        const PairRot rk = pt[vu[i] & 0xffff];
+        if (rk.sn == 0.f) continue;
+        float4* vp = (float4*)(Vt + rk.p * sp) + (vu[i] >> 16);
+        float4* vq = (float4*)(Vt + rk.q * sp) + (vu[i] >> 16);
+        const float4 x = *vp, y = *vq;
+        *vp = make_float4(rk.c * x.x - rk.sn * y.x, rk.c * x.y - rk.sn * y.y, rk.c * x.z - rk.sn * y.z,
+                          rk.c * x.w - rk.sn * y.w);
+        *vq = make_float4(rk.sn * x.x + rk.c * y.x, rk.sn * x.y + rk.c * y.y, rk.sn * x.z + rk.c * y.z,
+                          rk.sn * x.w + rk.c * y.w);
+      }
+      __syncthreads();
+      // (B) rotations of the next round (round 0 of the next sweep after the
+      // last round, counted for that sweep)
+      const bool last = (round == m - 2);
+      if (tid < npair) {
+        const float mu = set_rot(B, sb, m, last ? 0 : round + 1, tid, tol2, floor2, pt);
+        if (mu >= 0.f) {
+          if (last) {
+            ++n_cnt;
+            n_mu = fmaxf(n_mu, mu);
+          } else {
+            ++c_cnt;
+            c_mu = fmaxf(c_mu, mu);
+          }
+        }
+      }
+      if (last && tid < 32 * nw) {  // whole warps: this sweep's totals per warp
+        const unsigned cn = __reduce_add_sync(0xffffffffu, c_cnt);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(c_mu));  // mu >= 0
+        if ((tid & 31) == 0) {
+          wrot[tid >> 5] = cn;
+          wmu[tid >> 5] = mx;
+        }
+        c_cnt = n_cnt;
+        c_mu = n_mu;
+        n_cnt = 0;
+        n_mu = 0.f;
+      }
+      __syncthreads();
+    }
+    // cyclic Jacobi converges quadratically: after a sweep whose largest
+    // rotated ratio was below sqrt(tol), the next would rotate nothing above tol
+    unsigned cn = 0, mx = 0;
+    for (int w = 0; w < nw; ++w) {
+      cn += wrot[w];
+      mx = max(mx, wmu[w]);
+    }
+    converged = (cn == 0) || (__int_as_float((int)mx) < tol);
+  }
+  for (int j = tid; j < s; j += nt) Phi[j] = B[j * sb + j];
+  for (int e = tid; e < s * s; e += nt) {
+    const int r = e / s, j = e % s;
+    Cio[e] = Vt[j * sp + r];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float mn = Phi[0];
+    for (int j = 1; j < s; ++j) mn = fminf(mn, Phi[j]);
+    if (!((double)mn + tmin > 0.0)) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
+    if (sweeps_used) *sweeps_used = converged ? sweep : max_sweeps;
+  }
+}
+
+size_t eig2_smem(int s) {
+  const int m = (s + 3) & ~3, sp = m + 4, npair = m / 2;
+  return (size_t)3 * m * sp * sizeof(float) + (size_t)npair * sizeof(PairRot);
+}
+
 struct EigCfg {
   int a_smem, v_smem;
   size_t bytes;
@@ -271,6 +592,21 @@ EigCfg eig_cfg(int s, int elem) {
 template <typename T>
 void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, double tmin, int* status, int* used,
          cudaStream_t st) {
+  if (sizeof(T) == 4 && s <= EIG2_MAX) {
+    const int m = (s + 3) & ~3, npair = m / 2;
+    const int nblk = npair * (npair + 1) / 2, nvec = npair * (m / 4);
+    int threads = ((std::max(nblk, nvec) + 31) / 32) * 32;
+    threads = std::min(1024, std::max(64, threads));
+    const size_t bytes = eig2_smem(s);
+    static bool attr2 = false;
+    if (!attr2) {
+      cudaFuncSetAttribute(k_eig2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig2_smem(EIG2_MAX));
+      attr2 = true;
+    }
+    k_eig2<<<1, threads, bytes, st>>>((const float*)G, (float*)C, (float*)Phi, s, warm, max_sweeps, tmin, status,
+                                       used);
+    return;
+  }
   EigCfg cfg = eig_cfg(s, (int)sizeof(T));
   int npair = (s + (s & 1)) / 2;
   int threads = ((npair * EG + 31) / 32) * 32;
@@ -291,12 +627,16 @@ void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, dou
 }
 
 // ------------------------------------------------------------- solve ----
-// Eq. 8 in two row-block kernels (Q: real eigenbasis of L_k, I x I row-major,
-// column i = eigenvector i; C: eigenvectors of G, s x s, column j):
-//   solve_a:  Z[i,:] = ((Q^T R)[i,:] C) / (lam Lambda_i + Phi_j + rho)
-//   solve_b:  A[i,:] = (Q[i,:] Z) C^T, written to the FP64 master (or added
-//             to it, for a refinement pass) and to the compute copy.
-constexpr int SB = 8;  // rows per CTA
+// Eq. 8 with the eigenbasis Q of L_k (I x I row-major, column i =
+// eigenvector i; QT = Q^T) and the eigenvectors C of the Gram (s x s,
+// column j), in two kernels over blocks of TI factor rows:
+//   k_solve_fwd:  P = Q^T R, Z = (P C) / (lam Lambda_i + Phi_j + rho), W = Z C^T
+//   k_solve_bwd:  A = Q W into the FP64 master (stored or added) and the
+//                 compute copy, optionally with the FP64 residual of Eq. 5.
+// The operand that every block needs whole (R or W, I x s) is staged in
+// shared memory in chunks of NC rows by the bulk-copy engine; the sum over
+// the I rows is split over KS thread groups and combined in a fixed order.
+constexpr int SOLVE_NT = 256;
 
 // One bulk copy global -> shared by the TMA engine (cp.async.bulk), completed
 // on an mbarrier by transaction bytes; thread 0 issues, every thread waits
@@ -347,147 +687,300 @@ __device__ __forceinline__ void stage(T* __restrict__ dst, const T* __restrict__
   for (; e < n; e += nt) dst[e] = src[e];
 }
 
-// Row chunks of R (NC x s) and the matching slice of Q are staged in shared
-// memory; each thread owns fixed entries of the SB x s block, accumulated over
-// the chunks in a fixed order.
+// Offsets into dynamic shared memory, 16-byte aligned.
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_solve_a(const T* __restrict__ Q, const T* __restrict__ Rm,
-                                                 const T* __restrict__ C, const double* __restrict__ LamL,
-                                                 const T* __restrict__ Phi, double lam, double rho, int I, int s,
-                                                 int NC, T* __restrict__ Z, int* status) {
+struct FwdLayout {
+  size_t rs, qs, part, ps, cs, total;
+};
+template <typename T>
+__host__ __device__ inline FwdLayout<T> fwd_layout(int I, int s, int NC, int TI, int KS, int stageC) {
+  FwdLayout<T> L;
+  L.rs = 0;
+  L.qs = al16(L.rs + (size_t)NC * s * sizeof(T));
+  L.part = al16(L.qs + (size_t)TI * I * sizeof(T));
+  L.ps = al16(L.part + (size_t)KS * TI * s * sizeof(T));
+  L.cs = al16(L.ps + (size_t)TI * s * sizeof(T));
+  L.total = al16(L.cs + (stageC ? (size_t)s * (s + 1) * sizeof(T) : 0));
+  return L;
+}
+
+template <typename T>
+struct BwdLayout {
+  size_t ws, ad, qs, part, total;
+};
+template <typename T>
+__host__ __device__ inline BwdLayout<T> bwd_layout(int I, int s, int NC, int NR, int KS) {
+  BwdLayout<T> L;
+  L.ws = 0;
+  L.ad = al16(L.ws + (size_t)NC * s * sizeof(T));
+  L.qs = al16(L.ad + (size_t)NR * s * sizeof(double));
+  L.part = al16(L.qs + (size_t)NR * I * sizeof(T));
+  L.total = al16(L.part + (size_t)KS * NR * s * sizeof(T));
+  return L;
+}
+
+// Stage rows [n0, n0 + nc) of an I x s operand into shared memory: one bulk
+// copy when aligned, else plain loads.
+template <typename T>
+__device__ __forceinline__ void stage_rows(T* dst, const T* src_base, int n0, int nc, int s, uint64_t* bar,
+                                           unsigned& phase, int* status) {
+  const T* src = src_base + (int64_t)n0 * s;
+  const size_t bytes = (size_t)nc * s * sizeof(T);
+  if (aligned16(src, bytes) && bytes > 0) {
+    bulk_copy(dst, src, (unsigned)bytes, bar, phase, status);
+    phase ^= 1u;
+  } else {
+    stage(dst, src, nc * s);
+  }
+}
+
+// Partial sums over the rows n = kq, kq + KS, ... of a staged chunk for the
+// NR block rows: acc[t] += Qs[t][n0 + n] * Xs[n][j].
+template <typename T, int NRMAX>
+__device__ __forceinline__ void chunk_product(const T* __restrict__ Qs, int I, const T* __restrict__ Xs, int s,
+                                              int n0, int nc, int j, int kq, int KS, int nr, T* acc) {
+  int n = kq;
+  for (; n + KS < nc; n += 2 * KS) {
+    const T x0 = Xs[n * s + j], x1 = Xs[(n + KS) * s + j];
+#pragma unroll
+    for (int t = 0; t < NRMAX; ++t)
+      if (t < nr) acc[t] = fma(Qs[t * I + n0 + n + KS], x1, fma(Qs[t * I + n0 + n], x0, acc[t]));
+  }
+  if (n < nc) {
+    const T x0 = Xs[n * s + j];
+#pragma unroll
+    for (int t = 0; t < NRMAX; ++t)
+      if (t < nr) acc[t] = fma(Qs[t * I + n0 + n], x0, acc[t]);
+  }
+}
+
+// Forward half of Eq. 8 for factor rows [i0, i0 + TI):
+//   P = (Q^T R)[rows], Z = (P C) / (lam Lambda_i + Phi_j + rho), W = Z C^T.
+template <typename T, int TI>
+__global__ void __launch_bounds__(SOLVE_NT) k_solve_fwd(const T* __restrict__ QT, const T* __restrict__ Rm,
+                                                        const T* __restrict__ C, const double* __restrict__ LamL,
+                                                        const T* __restrict__ Phi, double lam, double rho, int I,
+                                                        int s, int NC, int KS, int stageC, T* __restrict__ W,
+                                                        int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ __align__(8) uint64_t bar;
-  T* Rs = (T*)sm;                  // NC x s (first: 16-byte aligned for the bulk copy)
-  T* W = Rs + (size_t)NC * s;      // SB x s
-  T* Qs = W + (size_t)SB * s;      // NC x SB  (Qs[n][r] = Q[n0 + n][i0 + r])
-  const int i0 = blockIdx.x * SB;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const FwdLayout<T> L = fwd_layout<T>(I, s, NC, TI, KS, stageC);
+  T* Rs = (T*)(sm + L.rs);
+  T* Qs = (T*)(sm + L.qs);
+  T* part = (T*)(sm + L.part);
+  T* Ps = (T*)(sm + L.ps);
+  T* Cs = (T*)(sm + L.cs);
+  const int tid = threadIdx.x, nt = blockDim.x, i0 = blockIdx.x * TI;
+  const int nv = min(TI, I - i0);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
-  for (int e = tid; e < SB * s; e += nt) W[e] = 0;
+  for (int e = tid; e < TI * I; e += nt) {  // rows of Q^T = columns of Q
+    const int r = e / I, n = e % I;
+    Qs[e] = r < nv ? QT[(int64_t)(i0 + r) * I + n] : (T)0;
+  }
+  const int cst = stageC ? s + 1 : s;
+  const T* Cp = stageC ? Cs : C;
+  if (stageC)
+    for (int e = tid; e < s * s; e += nt) Cs[(e / s) * cst + e % s] = C[e];
+  const int j = tid % s, kq = tid / s;
+  const bool act = kq < KS;
+  T acc[TI];
+#pragma unroll
+  for (int t = 0; t < TI; ++t) acc[t] = 0;
+  unsigned phase = 0;
+  for (int n0 = 0; n0 < I; n0 += NC) {
+    const int nc = min(NC, I - n0);
+    __syncthreads();  // previous chunk consumed; on the first pass, Qs and the barrier init visible
+    stage_rows(Rs, Rm, n0, nc, s, &bar, phase, status);
+    __syncthreads();
+    if (act) chunk_product<T, TI>(Qs, I, Rs, s, n0, nc, j, kq, KS, TI, acc);
+  }
+  if (act)
+#pragma unroll
+    for (int t = 0; t < TI; ++t) part[(kq * TI + t) * s + j] = acc[t];
+  __syncthreads();
+  for (int e = tid; e < TI * s; e += nt) {  // fixed-order combine of the KS partial sums
+    T v = 0;
+    for (int q = 0; q < KS; ++q) v += part[q * TI * s + e];
+    Ps[e] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < TI * s; e += nt) {  // Z = (P C) / T  (into part)
+    const int r = e / s, jj = e % s;
+    T a0 = 0, a1 = 0;
+    int q = 0;
+    for (; q + 1 < s; q += 2) {
+      a0 = fma(Ps[r * s + q], Cp[q * cst + jj], a0);
+      a1 = fma(Ps[r * s + q + 1], Cp[(q + 1) * cst + jj], a1);
+    }
+    if (q < s) a0 = fma(Ps[r * s + q], Cp[q * cst + jj], a0);
+    const double tt = r < nv ? lam * LamL[i0 + r] + (double)Phi[jj] + rho : 1.0;
+    part[e] = (T)((double)(a0 + a1) / tt);
+  }
+  __syncthreads();
+  for (int e = tid; e < nv * s; e += nt) {  // W = Z C^T
+    const int r = e / s, jj = e % s;
+    T a0 = 0, a1 = 0;
+    int q = 0;
+    for (; q + 1 < s; q += 2) {
+      a0 = fma(part[r * s + q], Cp[jj * cst + q], a0);
+      a1 = fma(part[r * s + q + 1], Cp[jj * cst + q + 1], a1);
+    }
+    if (q < s) a0 = fma(part[r * s + q], Cp[jj * cst + q], a0);
+    W[(int64_t)(i0 + r) * s + jj] = a0 + a1;
+  }
+}
+
+// Backward half of Eq. 8 for factor rows [i0, i0 + TI): A = (Q W)[rows],
+// stored to (accumulate = 0) or added to (accumulate = 1) the FP64 master,
+// and to the compute copy.  With Rout (accumulate = 0 only), also the FP64
+// residual of Eq. 5 for these rows, R = Y - lam L A - rho A - A G; the block
+// then also forms A for the cyclic neighbour rows i0 - 1 and i0 + nv (slot
+// t holds row (i0 - 1 + t) mod I), with the same arithmetic as the blocks
+// that own them.
+template <typename T, typename Tc, int TI>
+__global__ void __launch_bounds__(SOLVE_NT) k_solve_bwd(const T* __restrict__ Q, const T* __restrict__ Wm, int I,
+                                                        int s, int NC, int KS, int accumulate,
+                                                        double* __restrict__ A64, Tc* __restrict__ Ac,
+                                                        const double* __restrict__ Yd,
+                                                        const double* __restrict__ Gd, double lam, double rho,
+                                                        double c0, double c1, T* __restrict__ Rout, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar;
+  constexpr int NRMAX = TI + 2;
+  const BwdLayout<T> L = bwd_layout<T>(I, s, NC, NRMAX, KS);
+  T* Ws = (T*)(sm + L.ws);
+  double* Ad = (double*)(sm + L.ad);
+  T* Qs = (T*)(sm + L.qs);
+  T* part = (T*)(sm + L.part);
+  const int tid = threadIdx.x, nt = blockDim.x, i0 = blockIdx.x * TI;
+  const int nv = min(TI, I - i0);
+  const bool res = Rout != nullptr;
+  const int nr = res ? nv + 2 : nv, off = res ? 1 : 0;  // slot t <-> row (i0 - off + t) mod I
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  for (int e = tid; e < nr * I; e += nt) {
+    const int t = e / I, n = e % I;
+    const int row = (i0 - off + t + I) % I;
+    Qs[e] = Q[(int64_t)row * I + n];
+  }
+  const int j = tid % s, kq = tid / s;
+  const bool act = kq < KS;
+  T acc[NRMAX];
+#pragma unroll
+  for (int t = 0; t < NRMAX; ++t) acc[t] = 0;
   unsigned phase = 0;
   for (int n0 = 0; n0 < I; n0 += NC) {
     const int nc = min(NC, I - n0);
     __syncthreads();
-    const T* src = Rm + (int64_t)n0 * s;
-    const size_t bytes = (size_t)nc * s * sizeof(T);
-    if (aligned16(src, bytes)) {
-      bulk_copy(Rs, src, (unsigned)bytes, &bar, phase, status);
-      phase ^= 1u;
-    } else {
-      stage(Rs, src, nc * s);
-    }
-    for (int e = tid; e < nc * SB; e += nt) {
-      int n = e / SB, r = e % SB;
-      Qs[e] = (i0 + r < I) ? Q[(int64_t)(n0 + n) * I + i0 + r] : (T)0;
-    }
+    stage_rows(Ws, Wm, n0, nc, s, &bar, phase, status);
     __syncthreads();
-    for (int e = tid; e < SB * s; e += nt) {
-      int r = e / s, j = e % s;
-      T a0 = 0, a1 = 0;
-      int n = 0;
-      for (; n + 1 < nc; n += 2) {
-        a0 = fma(Qs[n * SB + r], Rs[n * s + j], a0);
-        a1 = fma(Qs[(n + 1) * SB + r], Rs[(n + 1) * s + j], a1);
-      }
-      if (n < nc) a0 = fma(Qs[n * SB + r], Rs[n * s + j], a0);
-      W[e] += a0 + a1;
+    if (act) chunk_product<T, NRMAX>(Qs, I, Ws, s, n0, nc, j, kq, KS, nr, acc);
+  }
+  if (act)
+#pragma unroll
+    for (int t = 0; t < NRMAX; ++t)
+      if (t < nr) part[(kq * NRMAX + t) * s + j] = acc[t];
+  __syncthreads();
+  for (int e = tid; e < nr * s; e += nt) {
+    const int t = e / s, jj = e % s;
+    T v = 0;
+    for (int q = 0; q < KS; ++q) v += part[(q * NRMAX + t) * s + jj];
+    const int row = (i0 - off + t + I) % I;
+    const int64_t o = (int64_t)row * s + jj;
+    const double a = accumulate ? A64[o] + (double)v : (double)v;
+    Ad[e] = a;
+    if (t >= off && t < off + nv) {
+      A64[o] = a;
+      Ac[o] = (Tc)a;
     }
   }
+  if (!res) return;
   __syncthreads();
-  for (int e = tid; e < SB * s; e += nt) {
-    int r = e / s, j = e % s;
-    int i = i0 + r;
-    if (i >= I) continue;
-    T a0 = 0, a1 = 0;
+  for (int e = tid; e < nv * s; e += nt) {
+    const int r = e / s, jj = e % s, t = r + 1;
+    const int64_t o = (int64_t)(i0 + r) * s + jj;
+    double g0 = 0.0, g1 = 0.0;
     int q = 0;
     for (; q + 1 < s; q += 2) {
-      a0 = fma(W[r * s + q], C[(int64_t)q * s + j], a0);
-      a1 = fma(W[r * s + q + 1], C[(int64_t)(q + 1) * s + j], a1);
+      g0 = fma(Ad[t * s + q], Gd[(int64_t)q * s + jj], g0);
+      g1 = fma(Ad[t * s + q + 1], Gd[(int64_t)(q + 1) * s + jj], g1);
     }
-    if (q < s) a0 = fma(W[r * s + q], C[(int64_t)q * s + j], a0);
-    double t = lam * LamL[i] + (double)Phi[j] + rho;
-    Z[(int64_t)i * s + j] = (T)((double)(a0 + a1) / t);
+    if (q < s) g0 = fma(Ad[t * s + q], Gd[(int64_t)q * s + jj], g0);
+    const double a = Ad[t * s + jj];
+    const double la = c0 * a + c1 * (Ad[(t - 1) * s + jj] + Ad[(t + 1) * s + jj]);
+    Rout[o] = (T)(Yd[o] - lam * la - rho * a - (g0 + g1));
   }
+}
+
+template <typename T>
+struct SolveCfg {
+  int TI, KS, NC, stageC;
+  size_t bytes;
+};
+
+// Row-block size, K split and chunk of staged rows for the two solve kernels.
+template <typename T>
+SolveCfg<T> solve_cfg(int I, int s, bool bwd, bool res) {
+  SolveCfg<T> c;
+  c.TI = I <= 152 ? 1 : 2;
+  c.KS = std::max(1, SOLVE_NT / s);
+  c.stageC = (!bwd && (size_t)s * (s + 1) * sizeof(T) <= 40 * 1024) ? 1 : 0;
+  const size_t budget = 160 * 1024;
+  size_t fixed = bwd ? bwd_layout<T>(I, s, 0, c.TI + 2, c.KS).total : fwd_layout<T>(I, s, 0, c.TI, c.KS, c.stageC).total;
+  const size_t per = (size_t)s * sizeof(T);
+  long nc = budget > fixed + 32 ? (long)((budget - fixed - 32) / per) : 1;
+  nc = std::max(1L, std::min<long>(nc, I));
+  c.NC = (int)nc;
+  c.bytes = bwd ? bwd_layout<T>(I, s, c.NC, c.TI + 2, c.KS).total : fwd_layout<T>(I, s, c.NC, c.TI, c.KS, c.stageC).total;
+  (void)res;
+  return c;
+}
+
+template <typename T>
+void solve_fwd(const T* QT, const T* R, const T* C, const double* LamL, const T* Phi, double lam, double rho, int I,
+               int s, T* W, int* status, cudaStream_t st) {
+  SolveCfg<T> c = solve_cfg<T>(I, s, false, false);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_solve_fwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_solve_fwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const int grid = (I + c.TI - 1) / c.TI;
+  if (c.TI == 1)
+    k_solve_fwd<T, 1><<<grid, SOLVE_NT, c.bytes, st>>>(QT, R, C, LamL, Phi, lam, rho, I, s, c.NC, c.KS, c.stageC, W,
+                                                        status);
+  else
+    k_solve_fwd<T, 2><<<grid, SOLVE_NT, c.bytes, st>>>(QT, R, C, LamL, Phi, lam, rho, I, s, c.NC, c.KS, c.stageC, W,
+                                                        status);
 }
 
 template <typename T, typename Tc>
-__global__ void __launch_bounds__(256) k_solve_b(const T* __restrict__ Q, const T* __restrict__ Z,
-                                                 const T* __restrict__ C, int I, int s, int NC, int accumulate,
-                                                 double* __restrict__ A64, Tc* __restrict__ Ac, int* status) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar;
-  T* Zs = (T*)sm;                  // NC x s (first: 16-byte aligned for the bulk copy)
-  T* U = Zs + (size_t)NC * s;      // SB x s
-  T* Qs = U + (size_t)SB * s;      // SB x NC (Qs[r][n] = Q[i0 + r][n0 + n])
-  const int i0 = blockIdx.x * SB;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar)));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+void solve_bwd(const T* Q, const T* W, int I, int s, int accumulate, double* A64, Tc* Ac, const double* Yd,
+               const double* Gd, double lam, double rho, double c0, double c1, T* Rout, int* status,
+               cudaStream_t st) {
+  SolveCfg<T> c = solve_cfg<T>(I, s, true, Rout != nullptr);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_solve_bwd<T, Tc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_solve_bwd<T, Tc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
   }
-  for (int e = tid; e < SB * s; e += nt) U[e] = 0;
-  unsigned phase = 0;
-  for (int n0 = 0; n0 < I; n0 += NC) {
-    const int nc = min(NC, I - n0);
-    __syncthreads();
-    const T* src = Z + (int64_t)n0 * s;
-    const size_t bytes = (size_t)nc * s * sizeof(T);
-    if (aligned16(src, bytes)) {
-      bulk_copy(Zs, src, (unsigned)bytes, &bar, phase, status);
-      phase ^= 1u;
-    } else {
-      stage(Zs, src, nc * s);
-    }
-    for (int e = tid; e < SB * nc; e += nt) {
-      int r = e / nc, n = e % nc;
-      Qs[r * NC + n] = (i0 + r < I) ? Q[(int64_t)(i0 + r) * I + n0 + n] : (T)0;
-    }
-    __syncthreads();
-    for (int e = tid; e < SB * s; e += nt) {
-      int r = e / s, j = e % s;
-      T a0 = 0, a1 = 0;
-      int n = 0;
-      for (; n + 1 < nc; n += 2) {
-        a0 = fma(Qs[r * NC + n], Zs[n * s + j], a0);
-        a1 = fma(Qs[r * NC + n + 1], Zs[(n + 1) * s + j], a1);
-      }
-      if (n < nc) a0 = fma(Qs[r * NC + n], Zs[n * s + j], a0);
-      U[e] += a0 + a1;
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < SB * s; e += nt) {
-    int r = e / s, j = e % s;
-    int i = i0 + r;
-    if (i >= I) continue;
-    T a0 = 0, a1 = 0;
-    int q = 0;
-    for (; q + 1 < s; q += 2) {
-      a0 = fma(U[r * s + q], C[(int64_t)j * s + q], a0);
-      a1 = fma(U[r * s + q + 1], C[(int64_t)j * s + q + 1], a1);
-    }
-    if (q < s) a0 = fma(U[r * s + q], C[(int64_t)j * s + q], a0);
-    int64_t o = (int64_t)i * s + j;
-    double v = accumulate ? A64[o] + (double)(a0 + a1) : (double)(a0 + a1);
-    A64[o] = v;
-    Ac[o] = (Tc)v;
-  }
+  const int grid = (I + c.TI - 1) / c.TI;
+  if (c.TI == 1)
+    k_solve_bwd<T, Tc, 1><<<grid, SOLVE_NT, c.bytes, st>>>(Q, W, I, s, c.NC, c.KS, accumulate, A64, Ac, Yd, Gd, lam,
+                                                            rho, c0, c1, Rout, status);
+  else
+    k_solve_bwd<T, Tc, 2><<<grid, SOLVE_NT, c.bytes, st>>>(Q, W, I, s, c.NC, c.KS, accumulate, A64, Ac, Yd, Gd, lam,
+                                                            rho, c0, c1, Rout, status);
 }
-
-// rows of R / Z staged per chunk so that the staging fits in ~96 KB
-int solve_chunk(int I, int s, int elem) {
-  size_t budget = 96 * 1024 / elem;
-  size_t fixed = (size_t)SB * s;
-  size_t per = (size_t)s + SB;
-  int nc = (int)((budget > fixed ? budget - fixed : per) / per);
-  if (nc < 1) nc = 1;
-  return nc < I ? nc : I;
-}
-
-size_t solve_smem(int I, int s, int NC, int elem) { return ((size_t)SB * s + (size_t)NC * s + (size_t)NC * SB) * elem; }
 
 // FP64 residual of Eq. 5, one CTA per row: R = Y - lam L A - rho A - A G.
 template <typename Tout>
@@ -589,35 +1082,23 @@ void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s
                     double tmin, int* status, int* used, cudaStream_t st) {
   eig<double>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
 }
-void launch_solve_a_f32(const float* Q, const float* R, const float* C, const double* LamL, const float* Phi,
-                        double lam, double rho, int I, int s, float* Z, int* status, cudaStream_t st) {
-  int nc = solve_chunk(I, s, sizeof(float));
-  size_t sb = solve_smem(I, s, nc, sizeof(float));
-  if (sb > 48 * 1024) cudaFuncSetAttribute(k_solve_a<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_a<float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z, status);
+void launch_solve_fwd_f32(const float* QT, const float* R, const float* C, const double* LamL, const float* Phi,
+                          double lam, double rho, int I, int s, float* W, int* status, cudaStream_t st) {
+  solve_fwd<float>(QT, R, C, LamL, Phi, lam, rho, I, s, W, status, st);
 }
-void launch_solve_a_f64(const double* Q, const double* R, const double* C, const double* LamL, const double* Phi,
-                        double lam, double rho, int I, int s, double* Z, int* status, cudaStream_t st) {
-  int nc = solve_chunk(I, s, sizeof(double));
-  size_t sb = solve_smem(I, s, nc, sizeof(double));
-  if (sb > 48 * 1024) cudaFuncSetAttribute(k_solve_a<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_a<double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, R, C, LamL, Phi, lam, rho, I, s, nc, Z, status);
+void launch_solve_fwd_f64(const double* QT, const double* R, const double* C, const double* LamL, const double* Phi,
+                          double lam, double rho, int I, int s, double* W, int* status, cudaStream_t st) {
+  solve_fwd<double>(QT, R, C, LamL, Phi, lam, rho, I, s, W, status, st);
 }
-void launch_solve_b_f32(const float* Q, const float* Z, const float* C, int I, int s, int accumulate, double* A64,
-                        float* Ac, int* status, cudaStream_t st) {
-  int nc = solve_chunk(I, s, sizeof(float));
-  size_t sb = solve_smem(I, s, nc, sizeof(float));
-  if (sb > 48 * 1024)
-    cudaFuncSetAttribute(k_solve_b<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_b<float, float><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac, status);
+void launch_solve_bwd_f32(const float* Q, const float* W, int I, int s, int accumulate, double* A64, float* Ac,
+                          const double* Yd, const double* Gd, double lam, double rho, double c0, double c1, float* Rout,
+                          int* status, cudaStream_t st) {
+  solve_bwd<float, float>(Q, W, I, s, accumulate, A64, Ac, Yd, Gd, lam, rho, c0, c1, Rout, status, st);
 }
-void launch_solve_b_f64(const double* Q, const double* Z, const double* C, int I, int s, int accumulate, double* A64,
-                        double* Ac, int* status, cudaStream_t st) {
-  int nc = solve_chunk(I, s, sizeof(double));
-  size_t sb = solve_smem(I, s, nc, sizeof(double));
-  if (sb > 48 * 1024)
-    cudaFuncSetAttribute(k_solve_b<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-  k_solve_b<double, double><<<(I + SB - 1) / SB, 256, sb, st>>>(Q, Z, C, I, s, nc, accumulate, A64, Ac, status);
+void launch_solve_bwd_f64(const double* Q, const double* W, int I, int s, int accumulate, double* A64, double* Ac,
+                          const double* Yd, const double* Gd, double lam, double rho, double c0, double c1,
+                          double* Rout, int* status, cudaStream_t st) {
+  solve_bwd<double, double>(Q, W, I, s, accumulate, A64, Ac, Yd, Gd, lam, rho, c0, c1, Rout, status, st);
 }
 void launch_resid_f32(const double* Y, const double* A, const double* G, int I, int s, double lam, double rho,
                       double c0, double c1, float* R, cudaStream_t st) {
