@@ -81,6 +81,15 @@ enum {
 
 enum { FCTN_HOST = 0, FCTN_DEVICE = 1 };
 
+/* Formation of the Gram M_k M_k^T.  DIRECT: from the merged tensor, as in
+ * Eq. 5.  FACTORED: the same matrix from the Grams of the two operands of
+ * the pair form of M_k (M_k[(a, b), (jL, jR)] = sum_kappa L[a, kappa, jL]
+ * R[b, kappa, jR], so G = sum_{kappa, kappa'} (L L^T) o (R R^T) blockwise);
+ * it has other rounding (more cancellation) than DIRECT.  AUTO: FACTORED in
+ * the FP32 / TF32 / BF16 precisions when it takes fewer multiply-adds, DIRECT
+ * in FP64. */
+enum { FCTN_GRAM_AUTO = 0, FCTN_GRAM_DIRECT = 1, FCTN_GRAM_FACTORED = 2 };
+
 typedef struct fctn_params {
   int32_t order;                                  /* N, 2 <= N <= FCTN_MAX_ORDER       */
   int32_t precision;                              /* FCTN_FP64 / FP32 / TF32 / BF16    */
@@ -95,6 +104,7 @@ typedef struct fctn_params {
   double rho;                                     /* proximal weight rho > 0 (Eq. 3)   */
   double extrap_alpha;  /* asymmetric extrapolation (Sec. 4.3): after each factor update */
   double extrap_beta;   /* A <- A + alpha (A - beta A^(t)); alpha = 0 turns it off       */
+  int32_t gram_mode;    /* FCTN_GRAM_*: how the Gram M_k M_k^T of Eq. 5 is formed        */
 } fctn_params;
 
 typedef struct fctn_stats {

@@ -94,6 +94,12 @@ struct fctn_handle {
   bool mat[FCTN_MAX_ORDER] = {};  // M_k is small enough to keep for the X update
   PairPlan pp[FCTN_MAX_ORDER];    // pair form of every M_k
   TcPlan tp[FCTN_MAX_ORDER];      // tensor-core Gram plan (TF32 / BF16)
+  FactGram fg[FCTN_MAX_ORDER];    // Gram from the operand Grams (when cheaper)
+  void* hbuf = nullptr;           // HL, HR of FactGram
+  // FactGram runs on a second stream, forked from and joined to `st`, so that
+  // it overlaps the right-hand-side kernel (a parallel branch of the graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool tc = false;
   int* tabs = nullptr;            // device index tables of the pair forms
   void* ones = nullptr;           // the constant 1 (second operand when N = 2)
@@ -257,6 +263,15 @@ int prof_post(fctn_handle* h, int cls) {
       prc_ = prof_post(h, (cls));                         \
       if (prc_) return prc_;                              \
     }                                                     \
+  } while (0)
+// The same for a launcher that issues n kernels on `strm` (outside the profiler).
+#define LAUNCH_ON(n, stmt)                                \
+  do {                                                    \
+    if (!h->dry) {                                        \
+      stmt;                                               \
+      CK(cudaGetLastError());                             \
+    }                                                     \
+    h->launches += (n);                                   \
   } while (0)
 #define LCHK()                  \
   do {                          \
@@ -575,7 +590,8 @@ GramPlan gram_plan(const fctn_handle* h, int k) {
   for (int t = 0; t < k; ++t) pre *= h->I[t];
   for (int t = k + 1; t < h->N; ++t) post *= h->I[t];
   g.xv = ModeView{pre, h->I[k], post};
-  g.ncols = g.s + g.I;
+  g.gcols = h->fg[k].use ? 0 : g.s;
+  g.ncols = g.gcols + g.I;
   g.tiles_r = (int)((g.s + 63) / 64);
   g.tiles_c = (int)((g.ncols + 63) / 64);
   int64_t ctas_per_split = g.tiles_r * g.tiles_c;
@@ -601,6 +617,8 @@ int check_params(const fctn_params* p) {
     return fail(FCTN_E_ARG, "unknown order policy %d", p->order_policy);
   if (p->laplacian_sign != FCTN_LAPLACIAN_PSD && p->laplacian_sign != FCTN_LAPLACIAN_PRINTED)
     return fail(FCTN_E_ARG, "unknown laplacian sign %d", p->laplacian_sign);
+  if (p->gram_mode < FCTN_GRAM_AUTO || p->gram_mode > FCTN_GRAM_FACTORED)
+    return fail(FCTN_E_ARG, "unknown gram mode %d", p->gram_mode);
   if (p->refine_steps < 0 || p->refine_steps > 8) return fail(FCTN_E_ARG, "refine_steps %d outside [0, 8]", p->refine_steps);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   if (p->reuse && p->order > 4) return fail(FCTN_E_UNSUPPORTED, "intermediate reuse is built for N <= 4");
@@ -635,7 +653,7 @@ void fill_shapes(fctn_handle* h, const fctn_params* p) {
 }
 
 struct Sizes {
-  int64_t M, chain, T[2], part, Is, ss, maxI, maxs, maxfac, red_blocks, lbuf;
+  int64_t M, chain, T[2], part, Is, ss, maxI, maxs, maxfac, red_blocks, lbuf, hbuf;
 };
 
 // M_k is kept for the X update (Algorithm 2) when it takes at most 64 MB:
@@ -659,6 +677,76 @@ int64_t lbuf_need(const fctn_handle* h) {
 
 // Host-only planning of every factor's pair form (and its index tables) and,
 // for the tensor-core precisions, of the tcgen05 Gram kernel.
+// Factored Gram of M_k (FactGram) from its pair plan: rows sigma split into
+// the distinct L and R row offsets, the F_L / F_R row offsets and column
+// offsets.  FCTN_GRAM_AUTO uses it outside FP64 when its multiply-adds,
+// (nL K)^2 JL + (nR K)^2 JR + s^2 K^2, are fewer than the s^2 P_k of the
+// direct Gram (by 8x against the tensor-core Gram, whose multiply-adds run at
+// a higher rate).
+void plan_fact(const fctn_handle* h, int k, const PairPlan& pp, const std::vector<int>& tab, FactGram* f,
+               std::vector<int>* ftab) {
+  memset(f, 0, sizeof *f);
+  ftab->clear();
+  const int s = (int)h->s[k], K = pp.K;
+  std::vector<int> uL, uR, a(s), b(s);
+  for (int sg = 0; sg < s; ++sg) {
+    const int lo = tab[sg], ro = tab[s + sg];
+    int ia = -1, ib = -1;
+    for (int i = 0; i < (int)uL.size(); ++i)
+      if (uL[i] == lo) ia = i;
+    if (ia < 0) { ia = (int)uL.size(); uL.push_back(lo); }
+    for (int i = 0; i < (int)uR.size(); ++i)
+      if (uR[i] == ro) ib = i;
+    if (ib < 0) { ib = (int)uR.size(); uR.push_back(ro); }
+    a[sg] = ia;
+    b[sg] = ib;
+  }
+  const int nL = (int)uL.size(), nR = (int)uR.size();
+  if ((int64_t)nL * nR != s) return;
+  // the column digits held by each operand
+  int64_t JL = 1, JR = 1;
+  int ndl = 0, ndr = 0;
+  int64_t el[FCTN_MAX_ORDER], sl[FCTN_MAX_ORDER], er[FCTN_MAX_ORDER], sr[FCTN_MAX_ORDER];
+  for (int d = 0; d < pp.nd; ++d) {
+    if (pp.lstr[d] != 0) { el[ndl] = pp.ext[d]; sl[ndl++] = pp.lstr[d]; JL *= pp.ext[d]; }
+    else { er[ndr] = pp.ext[d]; sr[ndr++] = pp.rstr[d]; JR *= pp.ext[d]; }
+  }
+  const int64_t rl = (int64_t)nL * K, rr = (int64_t)nR * K;
+  if (rl > 4096 || rr > 4096 || JL > (1 << 24) || JR > (1 << 24)) return;
+  const double fact = (double)rl * rl * JL + (double)rr * rr * JR + (double)s * s * K * K;
+  const double direct = (double)s * s * h->Pk[k];
+  if (h->p.gram_mode == FCTN_GRAM_DIRECT) return;
+  if (h->p.gram_mode == FCTN_GRAM_AUTO && (h->f64 || fact * (h->tc ? 8.0 : 1.0) >= direct)) return;
+  f->use = 1;
+  f->nL = nL;
+  f->nR = nR;
+  f->K = K;
+  f->rl = (int)rl;
+  f->rr = (int)rr;
+  f->JL = (int)JL;
+  f->JR = (int)JR;
+  const int* lk = tab.data() + 2 * s;
+  const int* rk = lk + K;
+  for (int i = 0; i < nL; ++i)
+    for (int q = 0; q < K; ++q) ftab->push_back(uL[i] + lk[q]);
+  for (int i = 0; i < nR; ++i)
+    for (int q = 0; q < K; ++q) ftab->push_back(uR[i] + rk[q]);
+  ftab->insert(ftab->end(), a.begin(), a.end());
+  ftab->insert(ftab->end(), b.begin(), b.end());
+  auto cols = [&](int nd, const int64_t* ext, const int64_t* str, int64_t J) {
+    for (int64_t j = 0; j < J; ++j) {
+      int64_t r = j, o = 0;
+      for (int d = nd - 1; d >= 0; --d) {
+        o += (r % ext[d]) * str[d];
+        r /= ext[d];
+      }
+      ftab->push_back((int)o);
+    }
+  };
+  cols(ndl, el, sl, JL);
+  cols(ndr, er, sr, JR);
+}
+
 int plan_all(fctn_handle* h, std::vector<int>* all, size_t* offs) {
   for (int k = 0; k < h->N; ++k) {
     View L, R;
@@ -668,6 +756,10 @@ int plan_all(fctn_handle* h, std::vector<int>* all, size_t* offs) {
     if (rc) return rc;
     if (offs) offs[k] = all->size();
     all->insert(all->end(), tab.begin(), tab.end());
+    std::vector<int> ftab;
+    plan_fact(h, k, h->pp[k], tab, &h->fg[k], &ftab);
+    if (offs) offs[FCTN_MAX_ORDER + k] = all->size();
+    all->insert(all->end(), ftab.begin(), ftab.end());
     h->mat[k] = h->p.reuse && materialise_ok(h, k);
     if (h->tc) {
       h->tp[k].n_groups = 0;
@@ -691,6 +783,10 @@ Sizes sizes_of(const fctn_handle* h) {
     if (h->s[k] > z.maxs) z.maxs = h->s[k];
     int64_t b = xupdate_blocks(g);
     if (b > z.red_blocks) z.red_blocks = b;
+    if (h->fg[k].use) {
+      int64_t hb = (int64_t)h->fg[k].rl * h->fg[k].rl + (int64_t)h->fg[k].rr * h->fg[k].rr;
+      if (hb > z.hbuf) z.hbuf = hb;
+    }
   }
   z.maxfac = z.Is;
   z.chain = chain_need(h);
@@ -706,12 +802,22 @@ Sizes sizes_of(const fctn_handle* h) {
   return z;
 }
 
+void release_side(fctn_handle* h) {
+  if (h->side) cudaStreamSynchronize(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
+  h->side = nullptr;
+  h->ev_fork = h->ev_join = nullptr;
+}
+
 size_t footprint(const fctn_handle* h) {
   Sizes z = sizes_of(h);
   size_t e = h->esz, b = 0;
   b += h->P * e + ((h->P + 31) / 32) * 4;                 // X, mask bits
   b += z.M * e + 2 * z.chain * e + z.lbuf * e + (z.T[0] + z.T[1]) * e;  // merged, chain, pairs
   b += z.part * e;                                        // split-K partials
+  b += z.hbuf * e;                                        // operand Grams
   for (int k = 0; k < h->N; ++k) {
     b += h->I[k] * h->s[k] * (8 + e);                     // factors (FP64 master + compute copy)
     b += h->I[k] * h->I[k] * 24 + h->I[k] * 8;            // L_k basis and its transpose
@@ -772,6 +878,10 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   // algorithmic traffic / work of each step ("kernels")
   const double gram_bytes = (double)h->P * e + part_elems * e + (Mout ? (double)g.s * g.Pk * e : 0.0);
   const double gram_flops = 2.0 * (double)g.s * (double)g.ncols * (double)g.Pk;
+  const FactGram& fg = h->fg[k];
+  const double fact_flops = fg.use ? 2.0 * ((double)fg.rl * fg.rl * fg.JL + (double)fg.rr * fg.rr * fg.JR +
+                                            (double)s * s * fg.K * fg.K)
+                                   : 0.0;
   const double red_bytes = part_elems * e + (double)g.s * g.ncols * 8.0 * 2;
   const double fwd_flops = 2.0 * ((double)I * I * s + 2.0 * (double)I * s * s);  // Q^T R, then C and C^T
   const double bwd_flops = 2.0 * (double)I * I * s;                              // Q W
@@ -779,6 +889,36 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   const bool extrap = h->p.extrap_alpha != 0.0;
   if (extrap && !h->dry)
     CK(cudaMemcpyAsync(h->Aprev, h->A64[k], (size_t)I * s * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  // FactGram on the side stream (overlapping the right-hand-side kernel),
+  // except under the per-class profiler, which times launches on `st`
+  const bool fork = fg.use && h->side && h->prof_class < 0;
+  cudaStream_t fst = fork ? h->side : h->st;
+  void* HL = h->hbuf;
+  void* HR = (char*)h->hbuf + (size_t)fg.rl * fg.rl * h->esz;
+  if (fork && !h->dry) {
+    CK(cudaEventRecord(h->ev_fork, h->st));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  }
+  if (fg.use) {
+    if (fork) {
+      if (h->f64)
+        LAUNCH_ON(3, launch_fact_gram_f64(fg, (const double*)L, (const double*)R, (double*)HL, (double*)HR, s, h->Gd,
+                                          fst));
+      else
+        LAUNCH_ON(3, launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
+                                          (float*)h->Gs, fst));
+      if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
+    } else if (h->f64) {
+      LAUNCH(FCTN_KC_GRAM, 0.0, fact_flops,
+             launch_fact_gram_f64(fg, (const double*)L, (const double*)R, (double*)HL, (double*)HR, s, h->Gd, fst));
+      h->launches += 2;
+    } else {
+      LAUNCH(FCTN_KC_GRAM, 0.0, fact_flops,
+             launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
+                                  (float*)h->Gs, fst));
+      h->launches += 2;
+    }
+  }
   if (h->f64) {
     double *Ck = (double*)h->Ck[k], *Phi = (double*)h->Phi, *Z = (double*)h->Z;
     LAUNCH(FCTN_KC_GRAM, gram_bytes, gram_flops,
@@ -786,6 +926,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
                                  (double*)h->part, g, (double*)Mout, h->st));
     LAUNCH(FCTN_KC_REDUCE, red_bytes, part_elems,
            launch_reduce_gram_rhs_f64((const double*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, h->st));
+    if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
     // Eq. 8, then refinement passes on the FP64 residual of Eq. 5 (the
@@ -820,6 +961,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     LAUNCH(FCTN_KC_REDUCE, red_bytes, part_elems,
            launch_reduce_gram_rhs_f32((const float*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, (float*)h->Gs,
                                       (float*)h->Ys, h->st));
+    if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
                           h->eig_used + k, h->st));
@@ -1057,7 +1199,7 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     h->own_stream = true;
   }
   std::vector<int> all_tabs;
-  size_t tab_offs[FCTN_MAX_ORDER];
+  size_t tab_offs[2 * FCTN_MAX_ORDER];  // pair tables, then FactGram tables
   if ((rc = plan_all(h, &all_tabs, tab_offs))) {
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
@@ -1082,6 +1224,7 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
   if (z.chain) { A_(h->chain[0], z.chain * e); A_(h->chain[1], z.chain * e); }
   if (reuse_pairs(h)) { A_(h->T[0], z.T[0] * e); A_(h->T[1], z.T[1] * e); }
   A_(h->part, z.part * e);
+  if (z.hbuf) A_(h->hbuf, z.hbuf * e);
   for (int k = 0; k < h->N; ++k) {
     A_(h->A64[k], h->I[k] * h->s[k] * 8);
     A_(h->Ac[k], h->I[k] * h->s[k] * e);
@@ -1118,7 +1261,10 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     std::vector<int>& all = all_tabs;
     size_t* offs = tab_offs;
     A_(h->tabs, all.size() * sizeof(int));
-    for (int k = 0; k < h->N; ++k) h->pp[k].tab = h->tabs + offs[k];
+    for (int k = 0; k < h->N; ++k) {
+      h->pp[k].tab = h->tabs + offs[k];
+      h->fg[k].tab = h->tabs + offs[FCTN_MAX_ORDER + k];
+    }
     cudaError_t ce = cudaMemcpy(h->tabs, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) {
       if (h->f64) {
@@ -1137,6 +1283,20 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     }
   }
 #undef A_
+  bool any_fact = false;
+  for (int k = 0; k < h->N; ++k) any_fact = any_fact || h->fg[k].use;
+  if (any_fact) {
+    cudaError_t ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      release_side(h);
+      free_all(h);
+      if (h->own_stream) cudaStreamDestroy(h->st);
+      delete h;
+      return fail(FCTN_E_CUDA, "fctn_create: %s", cudaGetErrorString(ce));
+    }
+  }
   for (int k = 0; k < h->N; ++k) {
     // min_i lambda_k Lambda_i over the closed-form spectrum of L_k
     const double sg = p->laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
@@ -1344,6 +1504,7 @@ int fctn_destroy(fctn_handle* h) {
   cudaStreamSynchronize(h->st);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   for (auto e : h->prof_ev) cudaEventDestroy(e);
+  release_side(h);
   free_all(h);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;

@@ -31,11 +31,14 @@ struct ModeView {
   int64_t pre, I, post;
 };
 
-// Split-K contraction D = M [M ; X_(k)]^T (Gram block then RHS block).
+// Split-K contraction D = M [M ; X_(k)]^T (Gram block then RHS block); the
+// Gram block is left out (gcols = 0) when the Gram comes from the operand
+// Grams of the pair form (FactGram).
 struct GramPlan {
   int64_t s, I, Pk;     // M: s x Pk row-major; X_(k): I x Pk through `xv`
   ModeView xv;
-  int64_t ncols;        // s + I
+  int64_t gcols;        // Gram columns of D: s, or 0
+  int64_t ncols;        // gcols + I
   int tiles_r, tiles_c; // 64 x 64 output tiles
   int ksplit;           // number of K chunks
   int64_t kchunk;       // columns of M per chunk (multiple of 32)
@@ -53,6 +56,22 @@ struct PairPlan {
   int K;         // contracted length
   const int* tab;
 };
+
+// Gram of M_k from the Grams of its pair operands.  With rows sigma of M_k
+// split as (L offset, R offset) = (a(sigma), b(sigma)) and F_L[(a, kappa), jL]
+// = L[loffL(jL) + offL[a K + kappa]] (jL over the modes held by L; F_R alike):
+//   G[sigma, sigma'] = sum_{kappa, kappa'} HL[a K + kappa, a' K + kappa'] HR[b K + kappa, b' K + kappa'],
+//   HL = F_L F_L^T, HR = F_R F_R^T.
+struct FactGram {
+  int use;
+  int nL, nR, K, rl, rr;  // rl = nL K rows of F_L, rr = nR K rows of F_R
+  int JL, JR;             // columns of F_L, F_R
+  const int* tab;         // {offL[rl], offR[rr], a[s], b[s], colL[JL], colR[JR]}: F_L[r][j] = L[colL[j] + offL[r]]
+};
+void launch_fact_gram_f32(const FactGram& f, const float* L, const float* R, float* HL, float* HR, int s, double* Gd,
+                          float* Gs, cudaStream_t st);
+void launch_fact_gram_f64(const FactGram& f, const double* L, const double* R, double* HL, double* HR, int s,
+                          double* Gd, cudaStream_t st);
 
 // ---- kernels_tc.cu ------------------------------------------------------------
 // Column groups of the tensor-core Gram kernel: each CTA computes, for all

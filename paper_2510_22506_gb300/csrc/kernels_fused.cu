@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   T* Ls = Xs + (size_t)2 * BK * 64;             // [2][BK * Ljs]
   T* Rs = Ls + (size_t)2 * BK * p.Ljs;          // [2][BK * Rjs]
   __shared__ int lsl[2][32], rsl[2][32], cnt[2][2];  // per stage: row slots of the columns, distinct-row counts
+  __shared__ int64_t xcol[2][32];                    // per stage: offset of X_(k)[0, j] (-1 past the chunk)
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < s; e += NT) {
     lo[e] = p.tab[e];
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   const int64_t kb = (int64_t)blockIdx.z * g.kchunk;
   const int64_t ke = min(kb + g.kchunk, g.Pk);
   const bool write_m = Mout != nullptr && blockIdx.x == 0 && blockIdx.y == 0;
-  const bool has_x = c0 + 64 > g.s;
+  const bool has_x = c0 + 64 > g.gcols;
   const int nchunk = (int)((ke - kb + BK - 1) / BK);
   // steps of (row, column) when a flat index advances by NT
   const int dqL = NT / p.Ljs, dcL = NT % p.Ljs, dqR = NT / p.Rjs, dcR = NT % p.Rjs;
@@ -127,7 +128,15 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
   // decode the columns of chunk c into buffer b (then a barrier), and issue its copies
   auto issue = [&](int c, int b) {
     const int64_t k0 = kb + (int64_t)c * BK;
-    if (tid < 32) fctn_tile::chunk_slots(p, k0, BK, ke, lsl[b], rsl[b], cl + b * BK, cr + b * BK, cnt[b]);
+    if (tid < 32) {
+      fctn_tile::chunk_slots(p, k0, BK, ke, lsl[b], rsl[b], cl + b * BK, cr + b * BK, cnt[b]);
+      if (has_x && g.xv.post != 1 && tid < BK) {  // j = a * post + b'  ->  a * I * post + b'
+        const int64_t j = k0 + tid;
+        const uint32_t post = (uint32_t)g.xv.post, jj = (uint32_t)j;
+        const uint32_t a = jj / post;
+        xcol[b][tid] = j < ke ? ((int64_t)a * g.xv.I) * g.xv.post + (jj - a * post) : -1;
+      }
+    }
     __syncthreads();
     T* ls = Ls + (size_t)b * BK * p.Ljs;
     T* rs = Rs + (size_t)b * BK * p.Rjs;
@@ -155,15 +164,20 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
         for (int e = tid; e < 64 * BK; e += NT) {
           int cc = e % 64, kk = e / 64;
           int64_t col = c0 + cc, j = k0 + kk;
-          bool v = col >= g.s && col < g.ncols && j < ke;
-          cp_async_elem(xs + kk * 64 + cc, v ? X + j * g.xv.I + (col - g.s) : X, v);
+          bool v = col >= g.gcols && col < g.ncols && j < ke;
+          cp_async_elem(xs + kk * 64 + cc, v ? X + j * g.xv.I + (col - g.gcols) : X, v);
         }
       } else {
-        for (int e = tid; e < 64 * BK; e += NT) {
-          int cc = e / BK, kk = e % BK;
-          int64_t col = c0 + cc, j = k0 + kk;
-          bool v = col >= g.s && col < g.ncols && j < ke;
-          cp_async_elem(xs + kk * 64 + cc, v ? X + xaddr(g.xv, col - g.s, j) : X, v);
+        // a warp takes 32 consecutive rows of one column: conflict-free in
+        // shared memory; element (cc, kk) at xcol[kk] + row * post
+        const int cc = tid % 64;
+        const int64_t col = c0 + cc;
+        const bool vc = col >= g.gcols && col < g.ncols;
+        const int64_t roff = (col - g.gcols) * g.xv.post;
+        for (int kk = tid / 64; kk < BK; kk += NT / 64) {
+          const int64_t xc = xcol[b][kk];
+          const bool v = vc && xc >= 0;
+          cp_async_elem(xs + kk * 64 + cc, v ? X + xc + roff : X, v);
         }
       }
     }
@@ -216,10 +230,10 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
     }
     const T* xs = Xs + (size_t)b * BK * 64;
     const T* ap = Ms + r0 + ty * 4;  // rows >= s are zero in Ms
-    if (c0 + 64 <= g.s || c0 >= g.s) {
+    if (c0 + 64 <= g.gcols || c0 >= g.gcols) {
       // the 64 columns of this tile are all Gram columns (from Ms) or all X rows (from xs)
-      const T* bp = (c0 + 64 <= g.s) ? Ms + c0 + tx * 4 : xs + tx * 4;
-      const int bstr = (c0 + 64 <= g.s) ? ldm : 64;
+      const T* bp = (c0 + 64 <= g.gcols) ? Ms + c0 + tx * 4 : xs + tx * 4;
+      const int bstr = (c0 + 64 <= g.gcols) ? ldm : 64;
 #pragma unroll 4
       for (int kk = 0; kk < nb; ++kk) {
         T av[4], bv[4];
@@ -237,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_gram_fused(PairPlan p, const T* __restri
 #pragma unroll
         for (int b2 = 0; b2 < 4; ++b2) {
           int64_t col = c0 + tx * 4 + b2;
-          bv[b2] = col < g.s ? Ms[kk * ldm + col] : xs[kk * 64 + tx * 4 + b2];
+          bv[b2] = col < g.gcols ? Ms[kk * ldm + col] : xs[kk * 64 + tx * 4 + b2];
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)

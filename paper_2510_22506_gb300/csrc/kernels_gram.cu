@@ -37,11 +37,11 @@ __global__ void k_reduce_gram_rhs(const T* __restrict__ part, GramPlan g, const 
     }
     double acc = (double)sum;
     int64_t row = e / g.ncols, col = e % g.ncols;
-    if (col < g.s) {
+    if (col < g.gcols) {
       Gd[row * g.s + col] = acc;
       if (Gs) Gs[row * g.s + col] = (float)acc;
     } else {
-      int64_t i = col - g.s;
+      int64_t i = col - g.gcols;
       double y = acc + rho * A_old[i * g.s + row];
       Yd[i * g.s + row] = y;
       if (Ys) Ys[i * g.s + row] = (float)y;
@@ -136,6 +136,108 @@ unsigned rgrid(int64_t n) {
   return (unsigned)b;
 }
 
+
+// ---- Gram of M_k from the Grams of its pair operands (FactGram) -------------
+// H = F F^T, F[r][j] = Src[col[j] + roff[r]] (r < rows, j < J): one 64 x 64
+// tile of H per CTA over all j, in chunks of 32 columns gathered into shared
+// memory; the next chunk's gathers are in flight while the current one is
+// consumed.  Fixed summation order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_op_gram(const T* __restrict__ Src, const int* __restrict__ roff,
+                                                 const int* __restrict__ col, int rows, int J, T* __restrict__ H) {
+  constexpr int BJ = 32;
+  __shared__ __align__(16) T Fa[BJ][64];
+  __shared__ __align__(16) T Fb[BJ][64];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int rr = tid % 64, jq = tid / 64;  // gathers rows r0 + rr and c0 + rr at columns j0 + jq + 4u
+  const int oa = r0 + rr < rows ? roff[r0 + rr] : -1;
+  const int ob = c0 + rr < rows ? roff[c0 + rr] : -1;
+  T va[8], vb[8];
+  auto gather = [&](int j0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + jq + 4 * u;
+      const int o = j < J ? col[j] : -1;
+      va[u] = (o >= 0 && oa >= 0) ? Src[(int64_t)o + oa] : (T)0;
+      vb[u] = (o >= 0 && ob >= 0) ? Src[(int64_t)o + ob] : (T)0;
+    }
+  };
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  gather(0);
+  for (int j0 = 0; j0 < J; j0 += BJ) {
+    __syncthreads();  // the previous chunk is consumed
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      Fa[jq + 4 * u][rr] = va[u];
+      Fb[jq + 4 * u][rr] = vb[u];
+    }
+    __syncthreads();
+    if (j0 + BJ < J) gather(j0 + BJ);
+    const int nb = min(BJ, J - j0);
+    for (int jj = 0; jj < nb; ++jj) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        av[a] = Fa[jj][ty * 4 + a];
+        bv[a] = Fb[jj][tx * 4 + a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = r0 + ty * 4 + a;
+    if (r >= rows) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = c0 + tx * 4 + b;
+      if (c < rows) H[(int64_t)r * rows + c] = acc[a][b];
+    }
+  }
+}
+
+// G[sigma, sigma'] = sum_{kappa, kappa'} HL[a K + kappa, a' K + kappa'] HR[b K + kappa, b' K + kappa']
+// with a = a_of[sigma], b = b_of[sigma] (FactGram); into Gd (FP64) and Gs.
+template <typename T>
+__global__ void k_gram_combine(const T* __restrict__ HL, const T* __restrict__ HR, const int* __restrict__ a_of,
+                               const int* __restrict__ b_of, int s, int K, int rl, int rr, double* __restrict__ Gd,
+                               float* __restrict__ Gs) {
+  const int64_t total = (int64_t)s * s;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int sg = (int)(e / s), sg2 = (int)(e % s);
+    const T* hl = HL + (int64_t)a_of[sg] * K * rl + (int64_t)a_of[sg2] * K;
+    const T* hr = HR + (int64_t)b_of[sg] * K * rr + (int64_t)b_of[sg2] * K;
+    T acc = 0;
+    for (int q = 0; q < K; ++q)
+      for (int q2 = 0; q2 < K; ++q2) acc = fma(hl[(int64_t)q * rl + q2], hr[(int64_t)q * rr + q2], acc);
+    Gd[e] = (double)acc;
+    if (Gs) Gs[e] = (float)acc;
+  }
+}
+
+template <typename T>
+void fact_gram(const FactGram& f, const T* L, const T* R, T* HL, T* HR, int s, double* Gd, float* Gs,
+               cudaStream_t st) {
+  const int* offL = f.tab;
+  const int* offR = offL + f.rl;
+  const int* a_of = offR + f.rr;
+  const int* b_of = a_of + s;
+  const int* colL = b_of + s;
+  const int* colR = colL + f.JL;
+  dim3 gl((f.rl + 63) / 64, (f.rl + 63) / 64), gr((f.rr + 63) / 64, (f.rr + 63) / 64);
+  k_op_gram<T><<<gl, 256, 0, st>>>(L, offL, colL, f.rl, f.JL, HL);
+  k_op_gram<T><<<gr, 256, 0, st>>>(R, offR, colR, f.rr, f.JR, HR);
+  k_gram_combine<T><<<rgrid((int64_t)s * s), 256, 0, st>>>(HL, HR, a_of, b_of, s, f.K, f.rl, f.rr, Gd, Gs);
+}
+
 }  // namespace
 
 void launch_reduce_gram_rhs_f32(const float* partials, const GramPlan& g, const double* A_old, double rho,
@@ -158,4 +260,13 @@ void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint
                         const GramPlan& g, double* red, cudaStream_t s) {
   dim3 grid((unsigned)((g.Pk + TN - 1) / TN), (unsigned)((g.I + TM - 1) / TM));
   k_xupdate<double><<<grid, NT, 0, s>>>(Ak, M, X, bits, rho, g, red);
+}
+
+void launch_fact_gram_f32(const FactGram& f, const float* L, const float* R, float* HL, float* HR, int s, double* Gd,
+                          float* Gs, cudaStream_t st) {
+  fact_gram<float>(f, L, R, HL, HR, s, Gd, Gs, st);
+}
+void launch_fact_gram_f64(const FactGram& f, const double* L, const double* R, double* HL, double* HR, int s,
+                          double* Gd, cudaStream_t st) {
+  fact_gram<double>(f, L, R, HL, HR, s, Gd, nullptr, st);
 }

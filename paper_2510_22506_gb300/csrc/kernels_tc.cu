@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
             const int cc = c0 + q;
             int64_t col;
             if (cc < grp.mw) col = cc;                       // Gram column
-            else col = g.s + grp.xi0 + (cc - grp.mw);          // right-hand-side column
+            else col = g.gcols + grp.xi0 + (cc - grp.mw);      // right-hand-side column
             bool valid = (cc < grp.mw) ? (cc < s) : (grp.xi0 + (cc - grp.mw) < g.I);
             if (valid) P[(int64_t)row * g.ncols + col] = __uint_as_float(v[q]);
           }
@@ -395,7 +395,7 @@ int tc_plan(const PairPlan& p, const GramPlan& g, int precision, TcPlan* tp) {
   const int s = (int)g.s, I = (int)g.I;
   if (s > 256) return FCTN_E_UNSUPPORTED;
   tp->n_mb = (s + 127) / 128;
-  const int mw = (s + 15) / 16 * 16;
+  const int mw = g.gcols > 0 ? (s + 15) / 16 * 16 : 0;  // no Gram columns when the Gram is factored
   const int xw_all = (I + 15) / 16 * 16;
   int ng = 0;
   if (tp->n_mb * (mw + xw_all) <= 512 && mw + xw_all <= 512) {
@@ -405,7 +405,7 @@ int tc_plan(const PairPlan& p, const GramPlan& g, int precision, TcPlan* tp) {
     }
   }
   if (ng == 0) {
-    tp->groups[ng++] = TcGroup{mw, 0, 0, mw};
+    if (mw > 0) tp->groups[ng++] = TcGroup{mw, 0, 0, mw};
     for (int x0 = 0; x0 < I; x0 += 256) {
       int w = I - x0 < 256 ? (I - x0 + 15) / 16 * 16 : 256;
       if (ng >= TC_MAX_GROUPS) return FCTN_E_UNSUPPORTED;

@@ -44,6 +44,7 @@ class fctn_params(ctypes.Structure):
         ("rho", ctypes.c_double),
         ("extrap_alpha", ctypes.c_double),
         ("extrap_beta", ctypes.c_double),
+        ("gram_mode", ctypes.c_int32),
     ]
 
 
@@ -151,7 +152,7 @@ def fctn_version():
 
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
-                laplacian_sign="psd", refine_steps=None, extrapolation=None):
+                laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto"):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -175,6 +176,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     p.rho = float(rho)
     if extrapolation is not None:
         p.extrap_alpha, p.extrap_beta = float(extrapolation[0]), float(extrapolation[1])
+    p.gram_mode = {"auto": 0, "direct": 1, "factored": 2}[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
     return p
 
 

@@ -126,6 +126,30 @@ def test_nothing_observed_is_nonfinite(F):
     assert ei.value.code == F.FCTN_E_NONFINITE
 
 
+# ---- the Gram of Eq. 5 from the operand Grams of the pair form -------------
+@pytest.mark.parametrize("dims,r,cap,reuse", [((30, 30, 10), 3, None, True), ((30, 30, 10), 3, None, False),
+                                              ((13, 7, 3, 5), 3, (3, 2), True), ((13, 7, 3, 5), 3, (3, 2), False),
+                                              ((37, 29), 5, None, True), ((2, 9, 1), 2, None, True)])
+def test_fp64_factored_gram_matches_oracle(F, dims, r, cap, reuse):
+    """FCTN_GRAM_FACTORED: G_k = sum over the contracted pair of (L L^T) o (R R^T) blocks."""
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=45, noise=0.0, cap=cap)
+    st, _ = oracle_run(d, 8, reuse=reuse)
+    g = gpu_run(F, d, 8, precision="fp64", reuse=reuse, gram_mode="factored")
+    assert rel(g["X"], st.X) <= 1e-9, rel(g["X"], st.X)
+    for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+        assert rel(a, b) <= 1e-9, (k, rel(a, b))
+
+
+def test_fp32_factored_and_direct_gram(F):
+    d = inputs(None, dims=(48, 40, 9), r=4, p=0.2, idx=44, noise=0.0, cap=None, dtype=np.float32)
+    st, _ = oracle_run(d, 10)
+    for mode in ("factored", "direct"):
+        g = gpu_run(F, d, 10, precision="fp32", gram_mode=mode)
+        assert rel(g["X"], st.X) <= 1e-4, (mode, rel(g["X"], st.X))
+        for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+            assert rel(a, b) <= 1e-4, (mode, k, rel(a, b))
+
+
 # ---- FP32 path ------------------------------------------------------------
 def test_fp32_small_matches_oracle(F):
     d = inputs(None, dims=(48, 40, 9), r=4, p=0.2, idx=44, noise=0.0, cap=None, dtype=np.float32)
