@@ -302,49 +302,50 @@ __device__ __forceinline__ void round_pair(int m, int round, int idx, int& p, in
 }
 
 // out[i][j] = ca * sum_k op(X)[i][k] Y[k][j] (+ cb * Add[i][j]) for i, j < m,
-// op(X) = X or X^T; m % 4 == 0.  Each thread owns rows {ti, ti + m/2} x
-// columns {tj + u m/4}: the Y loads of a warp are consecutive words.
+// op(X) = X or X^T; m % 4 == 0; X, Y rows 16-byte aligned with strides that
+// are multiples of 4.  Each thread owns a 4 x 4 tile; the Y rows are read as
+// float4 (a warp reads consecutive words), X as a float4 of row k (TN) or as
+// four words of column k (NN), shared by the threads of the same tile row.
 template <bool TN>
 __device__ __forceinline__ void sm_mm(float* __restrict__ out, int so, const float* __restrict__ X, int sx,
                                       const float* __restrict__ Y, int sy, int m, float ca,
                                       const float* __restrict__ Add, int sa, float cb) {
-  const int mh = m / 2, mq = m / 4, ntile = mh * mq;
+  const int mq = m / 4, ntile = mq * mq;
   for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-    const int ti = t / mq, tj = t % mq;
-    float a00 = 0.f, a01 = 0.f, a02 = 0.f, a03 = 0.f, a10 = 0.f, a11 = 0.f, a12 = 0.f, a13 = 0.f;
+    const int i0 = (t / mq) * 4, j0 = (t % mq) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 #pragma unroll 4
     for (int k = 0; k < m; ++k) {
-      float x0, x1;
+      float x[4];
       if (TN) {
-        x0 = X[k * sx + ti];
-        x1 = X[k * sx + ti + mh];
+        const float4 xv = *(const float4*)(X + k * sx + i0);
+        x[0] = xv.x;
+        x[1] = xv.y;
+        x[2] = xv.z;
+        x[3] = xv.w;
       } else {
-        x0 = X[ti * sx + k];
-        x1 = X[(ti + mh) * sx + k];
-      }
-      const float* yr = Y + k * sy + tj;
-      const float y0 = yr[0], y1 = yr[mq], y2 = yr[2 * mq], y3 = yr[3 * mq];
-      a00 = fmaf(x0, y0, a00);
-      a01 = fmaf(x0, y1, a01);
-      a02 = fmaf(x0, y2, a02);
-      a03 = fmaf(x0, y3, a03);
-      a10 = fmaf(x1, y0, a10);
-      a11 = fmaf(x1, y1, a11);
-      a12 = fmaf(x1, y2, a12);
-      a13 = fmaf(x1, y3, a13);
-    }
-    const float r0[4] = {a00, a01, a02, a03}, r1[4] = {a10, a11, a12, a13};
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = tj + u * mq;
-      float v0 = ca * r0[u], v1 = ca * r1[u];
-      if (Add) {
-        v0 = fmaf(cb, Add[ti * sa + j], v0);
-        v1 = fmaf(cb, Add[(ti + mh) * sa + j], v1);
+        for (int a = 0; a < 4; ++a) x[a] = X[(i0 + a) * sx + k];
       }
-      out[ti * so + j] = v0;
-      out[(ti + mh) * so + j] = v1;
+      const float4 yv = *(const float4*)(Y + k * sy + j0);
+      const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(x[a], y[b], acc[a][b]);
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        float v = ca * acc[a][b];
+        if (Add) v = fmaf(cb, Add[(i0 + a) * sa + j0 + b], v);
+        out[(i0 + a) * so + j0 + b] = v;
+      }
   }
 }
 
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
       X1[r * sp + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
     }
     __syncthreads();
-    sm_mm<false>(X2, sp, X1, sp, X3, sp, m, 1.f, nullptr, 0, 0.f);  // W = G V
+    sm_mm<true>(X2, sp, X1, sp, X3, sp, m, 1.f, nullptr, 0, 0.f);  // W = G V = G^T V (G symmetric)
     __syncthreads();
     sm_mm<true>(X1, sb, X3, sp, X2, sp, m, 1.f, nullptr, 0, 0.f);  // B = V^T W
     __syncthreads();
