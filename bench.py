@@ -42,6 +42,9 @@ DESC = {
     "c4": "256x256x31x8 multispectral sequence, FCTN rank 6, SR 0.1",
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maximum SM clock
+# DRAM bytes (read + write) per launch of the dominant kernel class, from one
+# ncu capture of the current kernel (profiles/); None when not captured.
+TRAFFIC = {}
 
 
 def dist_env():
@@ -248,9 +251,11 @@ def run_ours(args):
     svals = [int(np.prod([R[min(k, t), max(k, t)] for t in range(N) if t != k])) for k in range(N)]
     if dom == "eig":
         # one CTA by construction: the roof is one SM's FP32 FMA rate.  Algorithmic
-        # flops of one-sided Jacobi: warm start 6 s^3 + 9 s^2 (s-1) per sweep.
+        # flops of the two-sided Jacobi: warm start 4 products of 2 s^3, then per
+        # Jacobi sweep s (s-1) / 2 rotations of 18 s flops (rows and columns of B,
+        # columns of V).
         sw = max(int(st["eig_sweeps"]), 1)
-        flops = float(np.mean([6 * sv ** 3 + 9 * sw * sv * sv * (sv - 1) for sv in svals]))
+        flops = float(np.mean([8 * sv ** 3 + 9 * sw * sv * sv * (sv - 1) for sv in svals]))
         bound, unit = "alu", "TFLOP/s"
         achieved = flops / (avg_ms / 1e3) / 1e12
         peak = 128 * 2 * 2.07e9 / 1e12
@@ -283,7 +288,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": {"kernel_class": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "peak_source": peak_note, "traffic": None,
+                     "frac": achieved / peak, "peak_source": peak_note, "traffic": TRAFFIC.get((dom, precision)),
                      "avg_launch_us": avg_ms * 1e3, "launches": prof["launches"],
                      "measured": "CUDA events around each launch of the class, second timed pass of K eager sweeps",
                      "class_ms_2sweeps": {c: round(v["ms"], 4) for c, v in per_class.items()}},
@@ -292,7 +297,7 @@ def run_ours(args):
                 "step": f"set_data + set_factors from host, {e2e_sweeps} sweeps, X back to host"},
     }
     if ws == 1 and not args.no_extras:
-        line["precision_modes"] = precision_modes(F, name, Y, mask, init, R, args.steps)
+        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps)
         line["serving"] = serving_mix(args.serve_jobs)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
@@ -301,11 +306,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def precision_modes(F, name, Y, mask, init, R, steps):
-    """Sweeps/s of the same workload in every precision (graphs, L2 flushed between sweeps)."""
+def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100):
+    """Sweeps/s of the same workload in every precision (graphs, L2 flushed
+    between sweeps), and PSNR / SSIM against the truth (Sec. 4, computed by
+    libfctn) after `quality_sweeps` sweeps from the same start."""
     import torch
-    out = {}
+    out, quality = {}, {}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    truth32 = np.ascontiguousarray(truth.astype(np.float32))
     for prec in ("fp32", "tf32", "bf16"):
         p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=prec)
         st = torch.cuda.Stream()
@@ -325,9 +333,13 @@ def precision_modes(F, name, Y, mask, init, R, steps):
                     if i >= 3:
                         tot += a.elapsed_time(b)
             out[prec] = steps / (tot / 1e3)
+            F.fctn_pam_sweep(h, max(quality_sweeps - steps - 3, 0), want_stats=False)
+            ps, ss = F.fctn_quality(h, truth32)
+            quality[prec] = {"psnr_db": ps, "ssim": ss}
         finally:
             F.fctn_destroy(h)
-    return {"unit": UNIT, "sweeps_per_s": out, "workload": name}
+    return {"unit": UNIT, "sweeps_per_s": out, "workload": name,
+            "quality_after_sweeps": max(quality_sweeps, steps + 3), "quality": quality}
 
 
 def serving_mix(n_jobs):

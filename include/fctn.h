@@ -159,6 +159,16 @@ int fctn_pam_sweep(fctn_handle* h, int nsweeps, fctn_stats* stats);
  * NULL).  tol <= 0 runs exactly up to max_sweeps. */
 int fctn_complete(fctn_handle* h, double tol, int max_sweeps, void* out_X, int where, fctn_stats* stats);
 
+/* Quality of the current X against the ground truth, as the paper evaluates
+ * its results (Sec. 4): the mean over the slices spanned by modes 1 and 2
+ * (the mean over i_3, ..., i_N) of PSNR with Max = 1 (slice MSE floored at
+ * 1e-12) and of SSIM in its global per-slice form, with c1 = (0.01)^2,
+ * c2 = (0.03)^2 and sample statistics (divisor n - 1).  `truth`: the full
+ * tensor, row-major, in the compute precision (double for FCTN_FP64, float
+ * otherwise), on the host or device per `where`; it is not kept.  Writes
+ * *psnr and *ssim (either may be NULL) and synchronises the stream. */
+int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, double* ssim);
+
 /* Copy factor k (FCTN shape) / the completed tensor X out. */
 int fctn_get_factor(fctn_handle* h, int k, void* out, int where);
 int fctn_get_X(fctn_handle* h, void* out, int where);

@@ -328,6 +328,34 @@ def psnr(X, truth):
     return float(np.mean(10.0 * np.log10(1.0 / np.maximum(mse, 1e-12))))
 
 
+SSIM_C1 = 0.01 ** 2   # (0.01 L)^2 with dynamic range L = 1 (data in [0, 1])
+SSIM_C2 = 0.03 ** 2   # (0.03 L)^2
+
+
+def ssim(X, truth, c1=SSIM_C1, c2=SSIM_C2):
+    """Mean SSIM over the slices spanned by modes 1-2 (Sec. 4, global form).
+
+    Per slice: ((2 nu_T nu_X + c1)(2 omega_TX + c2)) / ((nu_T^2 + nu_X^2 + c1)
+    (omega_T^2 + omega_X^2 + c2)) with nu the slice mean, omega_T, omega_X the
+    standard deviations and omega_TX the covariance (sample statistics,
+    divisor n - 1); the mean runs over the remaining indices as in psnr().
+    """
+    T = np.asarray(truth, dtype=np.float64)
+    X = np.asarray(X, dtype=np.float64)
+    n = T.shape[0] * T.shape[1]
+    Ts = T.reshape(n, -1)
+    Xs = X.reshape(n, -1)
+    vals = []
+    for t in range(Ts.shape[1]):
+        a, b = Ts[:, t], Xs[:, t]
+        mu_a, mu_b = a.mean(), b.mean()
+        sd_a, sd_b = a.std(ddof=1), b.std(ddof=1)
+        cov = np.cov(a, b, ddof=1)[0, 1]
+        vals.append(((2 * mu_a * mu_b + c1) * (2 * cov + c2)) /
+                    ((mu_a ** 2 + mu_b ** 2 + c1) * (sd_a ** 2 + sd_b ** 2 + c2)))
+    return float(np.mean(vals))
+
+
 # --------------------------------------------------------------------------
 # PAM sweeps: Algorithm 1 (reuse off) and Algorithm 2 (reuse on)
 # --------------------------------------------------------------------------

@@ -96,6 +96,8 @@ struct fctn_handle {
   TcPlan tp[FCTN_MAX_ORDER];      // tensor-core Gram plan (TF32 / BF16)
   FactGram fg[FCTN_MAX_ORDER];    // Gram from the operand Grams (when cheaper)
   void* hbuf = nullptr;           // HL, HR of FactGram
+  double* qwork = nullptr;        // fctn_quality partial sums (allocated on first use)
+  size_t qwork_n = 0;
   // FactGram runs on a second stream, forked from and joined to `st`, so that
   // it overlaps the right-hand-side kernel (a parallel branch of the graph)
   cudaStream_t side = nullptr;
@@ -1344,6 +1346,43 @@ int fctn_set_data(fctn_handle* h, const void* Y, const uint8_t* mask, int where)
   h->t = 0;
   h->Tvalid[0] = h->Tvalid[1] = false;
   for (int k = 0; k < h->N; ++k) h->cvalid[k] = false;
+  return FCTN_OK;
+}
+
+int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, double* ssim) {
+  if (!h || !truth) return fail(FCTN_E_ARG, "NULL argument");
+  if (!h->data_set) return fail(FCTN_E_STATE, "no data set");
+  if (where != FCTN_HOST && where != FCTN_DEVICE) return fail(FCTN_E_ARG, "where must be FCTN_HOST or FCTN_DEVICE");
+  int rc;
+  const void* tsrc = truth;
+  if (where == FCTN_HOST) {
+    if ((rc = copy_in(h, h->stage, truth, h->P * h->esz, where))) return rc;
+    tsrc = h->stage;
+  }
+  const int64_t rows = h->N >= 2 ? h->I[0] * h->I[1] : h->I[0];
+  const int64_t ncol = h->P / rows;
+  const int nblocks = 152;
+  const size_t need = quality_work_doubles(ncol, nblocks) + 2;
+  if (h->qwork_n < need) {
+    void* p = nullptr;
+    if ((rc = dalloc(h, &p, need * sizeof(double)))) return rc;
+    h->qwork = (double*)p;
+    h->qwork_n = need;
+  }
+  double* out = h->qwork + need - 2;
+  if (h->f64)
+    launch_quality_f64((const double*)h->X, (const double*)tsrc, rows, ncol, 1e-4, 9e-4, h->qwork, nblocks, out,
+                       h->st);
+  else
+    launch_quality_f32((const float*)h->X, (const float*)tsrc, rows, ncol, 1e-4, 9e-4, h->qwork, nblocks, out,
+                       h->st);
+  h->launches += 2;
+  CK(cudaGetLastError());
+  double v[2];
+  CK(cudaMemcpyAsync(v, out, sizeof v, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (psnr) *psnr = v[0];
+  if (ssim) *ssim = v[1];
   return FCTN_OK;
 }
 

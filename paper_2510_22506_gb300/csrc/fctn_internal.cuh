@@ -114,6 +114,15 @@ int fctn_internal_fail(int code, const char* msg);
 int fctn_internal_sweep_async(fctn_handle* h, double* pinned);
 cudaStream_t fctn_internal_stream(fctn_handle* h);
 
+// ---- kernels_quality.cu ----------------------------------------------------
+// PSNR and SSIM (Sec. 4) of X against the truth Y, both (rows x ncol)
+// row-major with rows = I_1 I_2 (slice index = column); out = {psnr, ssim}.
+size_t quality_work_doubles(int64_t ncol, int nblocks);
+void launch_quality_f32(const float* X, const float* Y, int64_t rows, int64_t ncol, double c1, double c2,
+                        double* work, int nblocks, double* out, cudaStream_t st);
+void launch_quality_f64(const double* X, const double* Y, int64_t rows, int64_t ncol, double c1, double c2,
+                        double* work, int nblocks, double* out, cudaStream_t st);
+
 // ---- kernels_contract.cu ---------------------------------------------------
 void launch_contract_f32(const float* A, const float* B, float* out, const ContractPlan& p, cudaStream_t s);
 void launch_contract_f64(const double* A, const double* B, double* out, const ContractPlan& p, cudaStream_t s);

@@ -77,6 +77,7 @@ lib.fctn_pam_sweep.argtypes = [_vp, _i, ctypes.POINTER(fctn_stats)]
 lib.fctn_complete.argtypes = [_vp, ctypes.c_double, _i, _vp, _i, ctypes.POINTER(fctn_stats)]
 lib.fctn_get_factor.argtypes = [_vp, _i, _vp, _i]
 lib.fctn_get_X.argtypes = [_vp, _vp, _i]
+lib.fctn_quality.argtypes = [_vp, _vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
 lib.fctn_sync.argtypes = [_vp]
 lib.fctn_launch_count.argtypes = [_vp, _i64p]
 lib.fctn_destroy.argtypes = [_vp]
@@ -96,7 +97,7 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
-            "fctn_server_finished")
+            "fctn_server_finished", "fctn_quality")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
 
 
@@ -268,6 +269,14 @@ def fctn_get_X(h, out):
     p, w = _ptr(out)
     _check(lib.fctn_get_X(h, p, w))
     return out
+
+
+def fctn_quality(h, truth):
+    """(PSNR, SSIM) of the current X against `truth` (Sec. 4), computed by libfctn."""
+    p, w = _ptr(truth)
+    ps, ss = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib.fctn_quality(h, p, w, ctypes.byref(ps), ctypes.byref(ss)))
+    return ps.value, ss.value
 
 
 def fctn_sync(h):

@@ -401,3 +401,39 @@ def test_extrapolation_step_is_alpha_times_the_proximal_gradient_step():
         grad_D = (O.objective(st.X, fp, Ls, prob.lam) - O.objective(st.X, fm, Ls, prob.lam)) / (2 * h)
         step_D = float(np.sum((Aext - Anew) * D))
         assert abs(step_D - (-alpha / prob.rho) * grad_D) <= 1e-6 * max(1.0, abs(step_D))
+
+
+# ---- SSIM (Sec. 4), global per-slice form ----------------------------------
+def test_ssim_identical_is_one():
+    rng = np.random.default_rng(11)
+    T = rng.random((9, 7, 4))
+    assert abs(O.ssim(T, T) - 1.0) < 1e-14
+
+
+def test_ssim_symmetric_and_below_one():
+    rng = np.random.default_rng(12)
+    T = rng.random((8, 6, 3, 2))
+    X = T + 0.1 * rng.standard_normal(T.shape)
+    s = O.ssim(X, T)
+    assert abs(s - O.ssim(T, X)) < 1e-14
+    assert s < 1.0
+
+
+def test_ssim_constant_slices_closed_form():
+    """Constant slices: only the luminance factor is left, (2ab + c1)/(a^2 + b^2 + c1)."""
+    T = np.full((5, 4, 1), 0.3)
+    X = np.full((5, 4, 1), 0.7)
+    c1 = O.SSIM_C1
+    want = (2 * 0.3 * 0.7 + c1) / (0.3 ** 2 + 0.7 ** 2 + c1)
+    assert abs(O.ssim(X, T) - want) < 1e-14
+
+
+def test_ssim_scaled_zero_mean_structure_term():
+    """X = a T with zero-mean slices of large variance: SSIM -> 2a / (1 + a^2)."""
+    rng = np.random.default_rng(13)
+    T = rng.standard_normal((40, 30, 2))
+    T -= T.reshape(1200, 2).mean(axis=0)
+    T *= 100.0
+    for a in (0.5, 2.0, -1.0):
+        want = 2 * a / (1 + a * a)
+        assert abs(O.ssim(a * T, T) - want) < 1e-6, a
