@@ -61,3 +61,59 @@ __device__ __forceinline__ void chunk_slots(const PairPlan& p, int64_t j0, int n
 }
 
 }  // namespace fctn_tile
+
+namespace fctn_tile {
+
+// Offset of X_(k)[i, j] in the row-major tensor (view (pre, I, post), j = a * post + b).
+__device__ __forceinline__ int64_t x_offset(const ModeView& v, int64_t i, int64_t j) {
+  const uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
+  const uint32_t a = jj / post, b = jj - a * post;
+  return ((int64_t)a * v.I + i) * v.post + b;
+}
+
+// Eq. 10 on one 64 x 64 tile (rows i0.., columns j0.. of X_(k)) of
+// F = A_(k) M_k held as acc[4][4] by thread (ty, tx) = (tid / 16, tid % 16)
+// of a 256-thread block.  F goes through shared memory (Fs: 64 x 65) so that
+// X and the mask are read and written in memory order: runs along i when the
+// mode is the fastest one (post == 1: X_(k)[i, j] at j I + i), along j
+// otherwise.  Adds the thread's parts of ||Xnew - Xold||^2, ||Xold||^2 and
+// ||Xnew - F||^2 to d2, x2, r2.  Ends with the block synchronised.
+template <typename T>
+__device__ __forceinline__ void xupdate_tile(const T (&acc)[4][4], T* Fs, int64_t i0, int64_t j0, const GramPlan& g,
+                                             T* __restrict__ X, const uint32_t* __restrict__ bits, double rho,
+                                             T& d2, T& x2, T& r2) {
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16, nt = blockDim.x;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Fs[(ty * 4 + a) * 65 + tx * 4 + b] = acc[a][b];
+  __syncthreads();
+  const int ni = (int)min((int64_t)64, g.I - i0), nj = (int)min((int64_t)64, g.Pk - j0);
+  const T r = (T)rho, inv = (T)(1.0 / (1.0 + rho));
+  auto upd = [&](int64_t e, T f) {
+    const T xo = X[e];
+    const bool obs = (bits[e >> 5] >> (e & 31)) & 1u;
+    const T xn = obs ? xo : (f + r * xo) * inv;
+    X[e] = xn;
+    const T d = xn - xo, q = xn - f;
+    d2 = fma(d, d, d2);
+    x2 = fma(xo, xo, x2);
+    r2 = fma(q, q, r2);
+  };
+  if (ni > 0 && nj > 0) {
+    if (g.xv.post == 1) {
+      for (int e = tid; e < ni * nj; e += nt) {
+        const int jj = e / ni, ii = e - jj * ni;
+        upd((j0 + jj) * g.xv.I + i0 + ii, Fs[ii * 65 + jj]);
+      }
+    } else {
+      for (int e = tid; e < ni * nj; e += nt) {
+        const int ii = e / nj, jj = e - ii * nj;
+        upd(x_offset(g.xv, i0 + ii, j0 + jj), Fs[ii * 65 + jj]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace fctn_tile

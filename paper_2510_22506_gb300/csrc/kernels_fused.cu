@@ -10,6 +10,8 @@
 //                  of the factor updated last, reused by the X update).
 //   xupdate_fused: F = A_k(k) M_k and the masked proximal update of Eq. 10.
 #include "fctn_internal.cuh"
+#include <algorithm>
+
 #include "fctn_tile.cuh"
 
 namespace {
@@ -330,28 +332,9 @@ __global__ void __launch_bounds__(NT) k_xupdate_fused(PairPlan p, const T* __res
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
   }
-  const T r = (T)rho, inv = (T)(1.0 / (1.0 + rho));
   T d2 = 0, x2 = 0, r2 = 0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int64_t i = i0 + ty * 4 + a;
-    if (i >= g.I) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int64_t j = j0 + tx * 4 + b;
-      if (j >= g.Pk) continue;
-      int64_t e = xaddr(g.xv, i, j);
-      T xo = X[e];
-      bool obs = (bits[e >> 5] >> (e & 31)) & 1u;
-      T f = acc[a][b];
-      T xn = obs ? xo : (f + r * xo) * inv;
-      X[e] = xn;
-      T d = xn - xo, q = xn - f;
-      d2 = fma(d, d, d2);
-      x2 = fma(xo, xo, x2);
-      r2 = fma(q, q, r2);
-    }
-  }
+  __syncthreads();  // Ms and As are consumed: the F tile reuses Ms
+  fctn_tile::xupdate_tile<T>(acc, Ms, i0, j0, g, X, bits, rho, d2, x2, r2);
   double v[3] = {(double)d2, (double)x2, (double)r2};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -390,14 +373,15 @@ int gram_fused_bk(const PairPlan& p, int s, int elem) {
 
 int xupdate_fused_cb(const PairPlan& p, int s, int elem) {
   for (int cb = 32; cb >= 1; cb /= 2) {
-    size_t b = head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * (size_t)(s + 1) + 64 * (size_t)s) * elem;
+    size_t b = head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * std::max((size_t)(2 * s + 1), (size_t)65)) * elem;
     if (b <= 200 * 1024) return cb;
   }
   return 1;
 }
 
 size_t xupdate_fused_smem(const PairPlan& p, int s, int cb, int elem) {
-  return head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * (size_t)(s + 1) + 64 * (size_t)s) * elem;
+  // Ms (64 x (s+1)) and As (64 x s); afterwards the F tile (64 x 65) in their place
+  return head_bytes(p, s, cb) + ((size_t)cb * (p.Ljs + p.Rjs) + 64 * std::max((size_t)(2 * s + 1), (size_t)65)) * elem;
 }
 
 template <typename T>

@@ -9,6 +9,7 @@
 //           fused with the masked proximal update of Eq. 10 and the
 //           stop-test reductions.
 #include "fctn_internal.cuh"
+#include "fctn_tile.cuh"
 
 namespace {
 
@@ -53,8 +54,11 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_xupdate(const T* __restrict__ Ak, const T* __restrict__ M,
                                                 T* __restrict__ X, const uint32_t* __restrict__ bits, double rho,
                                                 GramPlan g, double* __restrict__ red) {
-  __shared__ T As[TK][TM + 4];
-  __shared__ T Bs[TK][TN + 4];
+  // As, Bs for the product; afterwards the F tile (64 x 65) in their place
+  constexpr int kAB = 2 * TK * (TM + 4), kF = 64 * 65;
+  __shared__ __align__(16) T sbuf[kAB > kF ? kAB : kF];
+  T(*As)[TM + 4] = reinterpret_cast<T(*)[TM + 4]>(sbuf);
+  T(*Bs)[TN + 4] = reinterpret_cast<T(*)[TN + 4]>(sbuf + TK * (TM + 4));
   __shared__ double sred[3][NT / 32];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
@@ -91,28 +95,8 @@ __global__ void __launch_bounds__(NT) k_xupdate(const T* __restrict__ Ak, const 
     }
     __syncthreads();
   }
-  const T r = (T)rho, inv = (T)(1.0 / (1.0 + rho));
   T d2 = 0, x2 = 0, r2 = 0;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int64_t i = i0 + ty * 4 + a;
-    if (i >= g.I) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int64_t j = j0 + tx * 4 + b;
-      if (j >= g.Pk) continue;
-      int64_t e = xaddr(g.xv, i, j);
-      T xo = X[e];
-      bool obs = (bits[e >> 5] >> (e & 31)) & 1u;
-      T f = acc[a][b];
-      T xn = obs ? xo : (f + r * xo) * inv;
-      X[e] = xn;
-      T d = xn - xo, q = xn - f;
-      d2 = fma(d, d, d2);
-      x2 = fma(xo, xo, x2);
-      r2 = fma(q, q, r2);
-    }
-  }
+  fctn_tile::xupdate_tile<T>(acc, sbuf, i0, j0, g, X, bits, rho, d2, x2, r2);
   double v[3] = {(double)d2, (double)x2, (double)r2};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
