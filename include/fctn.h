@@ -159,6 +159,19 @@ int fctn_pam_sweep(fctn_handle* h, int nsweeps, fctn_stats* stats);
  * NULL).  tol <= 0 runs exactly up to max_sweeps. */
 int fctn_complete(fctn_handle* h, double tol, int max_sweeps, void* out_X, int where, fctn_stats* stats);
 
+/* FCTN-rank growth (Algorithms 1-2 start from all-ones ranks and grow them
+ * to the maximal FCTN-rank; the schedule is the caller's).  Raises the rank
+ * of every bond (a, b), a < b, to ranks[a][b] (>= the current rank; a bond
+ * left unchanged keeps its factors' values).  The factors keep their entries
+ * and get new slices along the grown bonds, filled with scale (2u - 1): u is
+ * the (c + 1)-th output of SplitMix64 seeded with `seed`, c = k 2^40 + idx,
+ * idx the row-major index of the entry in factor k's new FCTN shape, mapped
+ * to [0, 1) by its top 53 bits.  X, the mask and the sweep count carry over;
+ * the handle is re-planned for the new ranks (tables, buffers, graphs, warm
+ * starts).  FCTN_E_ARG if a rank would shrink. */
+int fctn_grow_ranks(fctn_handle* h, const int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX_ORDER], double scale,
+                    uint64_t seed);
+
 /* Quality of the current X against the ground truth, as the paper evaluates
  * its results (Sec. 4): the mean over the slices spanned by modes 1 and 2
  * (the mean over i_3, ..., i_N) of PSNR with Max = 1 (slice MSE floored at

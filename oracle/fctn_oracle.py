@@ -328,6 +328,79 @@ def psnr(X, truth):
     return float(np.mean(10.0 * np.log10(1.0 / np.maximum(mse, 1e-12))))
 
 
+# --------------------------------------------------------------------------
+# FCTN-rank growth (Algorithms 1-2 start from all-ones ranks and grow them to
+# the maximal FCTN-rank; the schedule below is this build's reading)
+# --------------------------------------------------------------------------
+_U64 = np.uint64
+
+
+def splitmix64(seed, counters):
+    """SplitMix64 (Steele, Lea & Flood 2014): output number c + 1 of the
+    generator seeded with `seed`, for every counter c (uint64 arithmetic mod 2^64)."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = _U64(seed) + (c + _U64(1)) * _U64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> _U64(30))) * _U64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> _U64(27))) * _U64(0x94D049BB133111EB)
+        z = z ^ (z >> _U64(31))
+    return z
+
+
+def growth_values(seed, k, n, scale):
+    """Entries 0..n-1 of factor k's new slices: scale (2u - 1), u = top 53 bits / 2^53."""
+    c = (np.uint64(k) << np.uint64(40)) + np.arange(n, dtype=np.uint64)
+    u = (splitmix64(seed, c) >> _U64(11)).astype(np.float64) / 2.0 ** 53
+    return scale * (2.0 * u - 1.0)
+
+
+def grow_factors(factors, R_old, R_new, scale, seed):
+    """Factors padded from ranks R_old to R_new: old entries kept, new ones from growth_values."""
+    N = len(factors)
+    out = []
+    for k, A in enumerate(factors):
+        shape = tuple(A.shape[t] if t == k else int(R_new[min(t, k)][max(t, k)]) for t in range(N))
+        new = growth_values(seed, k, int(np.prod(shape)), scale).reshape(shape)
+        new[tuple(slice(0, s) for s in A.shape)] = A
+        out.append(new)
+    return out
+
+
+def complete_growth(Y, mask, init, R_max, prob_kw, grow_every, scale, seed, tol, max_sweeps, reuse=True,
+                    policy=ORDER_ALTERNATE):
+    """Completion with rank growth: `init` are factors of rank one on every
+    bond; after every `grow_every` sweeps every bond below its maximum grows by
+    one, the factors getting new slices from growth_values(seed + e, ...) for
+    the e-th growth (e = 0, 1, ...).  Stops when rel <= tol with every bond at
+    its maximum, or after max_sweeps sweeps.  Returns (state, history, ranks
+    during each sweep)."""
+    dims = Y.shape
+    N = len(dims)
+    R = np.ones((N, N), dtype=int)
+    st = init_state(np.asarray(Y, dtype=np.float64), mask, [np.asarray(a, dtype=np.float64) for a in init])
+    hist, rank_hist = [], []
+    e = 0
+    while st.t < max_sweeps:
+        prob = Problem(dims=dims, R=R.copy(), **prob_kw)
+        h = pam_sweep(st, prob, reuse=reuse, policy=policy)
+        hist.append(h)
+        rank_hist.append(R.copy())
+        at_max = all(R[a][b] >= R_max[a][b] for a in range(N) for b in range(a + 1, N))
+        if at_max and h["rel"] <= tol:
+            break
+        if not at_max and st.t % grow_every == 0:
+            R_new = R.copy()
+            for a in range(N):
+                for b in range(a + 1, N):
+                    R_new[a][b] = R_new[b][a] = min(R[a][b] + 1, R_max[a][b])
+            st.factors = grow_factors(st.factors, R, R_new, scale, (seed + e) % 2 ** 64)
+            st.versions = [v + 1 for v in st.versions]  # every factor changed: cached pairs are stale
+            st.cache = {}
+            R = R_new
+            e += 1
+    return st, hist, rank_hist
+
+
 SSIM_C1 = 0.01 ** 2   # (0.01 L)^2 with dynamic range L = 1 (data in [0, 1])
 SSIM_C2 = 0.03 ** 2   # (0.03 L)^2
 

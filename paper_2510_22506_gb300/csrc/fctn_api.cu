@@ -1349,6 +1349,107 @@ int fctn_set_data(fctn_handle* h, const void* Y, const uint8_t* mask, int where)
   return FCTN_OK;
 }
 
+// New entries of a factor under rank growth: scale (2u - 1) with u the
+// (c + 1)-th output of SplitMix64 (Steele, Lea & Flood 2014) seeded with
+// `seed`, c = k 2^40 + idx (idx: row-major index in factor k's new FCTN
+// shape), mapped to [0, 1) by its top 53 bits.
+static double growth_noise(uint64_t seed, int k, uint64_t idx, double scale) {
+  uint64_t z = seed + ((((uint64_t)k) << 40) + idx + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  return scale * (2.0 * u - 1.0);
+}
+
+int fctn_grow_ranks(fctn_handle* h, const int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX_ORDER], double scale,
+                    uint64_t seed) {
+  if (!h || !ranks) return fail(FCTN_E_ARG, "NULL argument");
+  if (!h->data_set || !h->factors_set) return fail(FCTN_E_STATE, "data and factors must be set");
+  const int N = h->N;
+  fctn_params p2 = h->p;
+  bool grow = false;
+  for (int a = 0; a < N; ++a)
+    for (int b = a + 1; b < N; ++b) {
+      if (ranks[a][b] < h->R[a][b]) return fail(FCTN_E_ARG, "rank (%d,%d) would shrink", a, b);
+      grow = grow || ranks[a][b] > h->R[a][b];
+      p2.ranks[a][b] = ranks[a][b];
+    }
+  if (!grow) return FCTN_OK;
+  int rc = check_params(&p2);
+  if (rc) return rc;
+  // current factors, FP64 master, in the FCTN layout
+  std::vector<std::vector<double>> old(N);
+  for (int k = 0; k < N; ++k) {
+    const size_t n = (size_t)(h->I[k] * h->s[k]);
+    View src = factor_view(h, k), dst = factor_d1_view(h, k);
+    ContractPlan pl;
+    View ov;
+    if ((rc = make_plan(src, nullptr, dst.lab, dst.n, &pl, &ov))) return rc;
+    launch_contract_f64(h->A64[k], nullptr, h->Aprev, pl, h->st);
+    h->launches++;
+    CK(cudaGetLastError());
+    old[k].resize(n);
+    CK(cudaMemcpyAsync(old[k].data(), h->Aprev, n * 8, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
+  fctn_handle* h2 = nullptr;
+  if ((rc = fctn_create(&p2, (void*)h->st, &h2))) return rc;
+  // the completed tensor, mask and sweep count carry over
+  cudaError_t ce = cudaMemcpyAsync(h2->X, h->X, (size_t)h->P * h->esz, cudaMemcpyDeviceToDevice, h->st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(h2->bits, h->bits, (size_t)((h->P + 31) / 32) * 4, cudaMemcpyDeviceToDevice, h->st);
+  if (ce != cudaSuccess) {
+    fctn_destroy(h2);
+    return fail(FCTN_E_CUDA, "fctn_grow_ranks: %s", cudaGetErrorString(ce));
+  }
+  h2->data_set = true;
+  // factors padded along the grown bonds
+  std::vector<std::vector<unsigned char>> nf(N);
+  std::vector<const void*> ptrs(N);
+  for (int k = 0; k < N; ++k) {
+    int64_t oe[FCTN_MAX_ORDER], ne[FCTN_MAX_ORDER];
+    for (int t = 0; t < N; ++t) {
+      oe[t] = t == k ? h->I[k] : h->R[t < k ? t : k][t < k ? k : t];
+      ne[t] = t == k ? h->I[k] : h2->R[t < k ? t : k][t < k ? k : t];
+    }
+    const size_t n = (size_t)(h2->I[k] * h2->s[k]);
+    nf[k].resize(n * h2->esz);
+    int64_t d[FCTN_MAX_ORDER] = {};
+    for (size_t e = 0; e < n; ++e) {
+      // multi-index of e (row-major over ne), old flat index if inside
+      int64_t r = (int64_t)e, of = 0, ost = 1;
+      bool inside = true;
+      for (int t = N - 1; t >= 0; --t) {
+        d[t] = r % ne[t];
+        r /= ne[t];
+      }
+      for (int t = N - 1; t >= 0; --t) {
+        inside = inside && d[t] < oe[t];
+        of += d[t] * ost;
+        ost *= oe[t];
+      }
+      const double v = inside ? old[k][(size_t)of] : growth_noise(seed, k, (uint64_t)e, scale);
+      if (h2->f64)
+        ((double*)nf[k].data())[e] = v;
+      else
+        ((float*)nf[k].data())[e] = (float)v;
+    }
+    ptrs[k] = nf[k].data();
+  }
+  if ((rc = fctn_set_factors(h2, ptrs.data(), FCTN_HOST))) {
+    fctn_destroy(h2);
+    return rc;
+  }
+  h2->t = h->t;  // after fctn_set_factors, which starts a new run at t = 0
+  CK(cudaStreamSynchronize(h->st));
+  // h takes the new state; h2 takes the old one (and not the stream) and goes
+  std::swap(*h, *h2);
+  std::swap(h->own_stream, h2->own_stream);
+  h->launches += h2->launches;
+  return fctn_destroy(h2);
+}
+
 int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, double* ssim) {
   if (!h || !truth) return fail(FCTN_E_ARG, "NULL argument");
   if (!h->data_set) return fail(FCTN_E_STATE, "no data set");

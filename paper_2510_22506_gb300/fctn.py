@@ -77,6 +77,8 @@ lib.fctn_pam_sweep.argtypes = [_vp, _i, ctypes.POINTER(fctn_stats)]
 lib.fctn_complete.argtypes = [_vp, ctypes.c_double, _i, _vp, _i, ctypes.POINTER(fctn_stats)]
 lib.fctn_get_factor.argtypes = [_vp, _i, _vp, _i]
 lib.fctn_get_X.argtypes = [_vp, _vp, _i]
+lib.fctn_grow_ranks.argtypes = [_vp, ctypes.POINTER((ctypes.c_int32 * MAX_ORDER) * MAX_ORDER), ctypes.c_double,
+                                ctypes.c_uint64]
 lib.fctn_quality.argtypes = [_vp, _vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
 lib.fctn_sync.argtypes = [_vp]
 lib.fctn_launch_count.argtypes = [_vp, _i64p]
@@ -97,7 +99,7 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
-            "fctn_server_finished", "fctn_quality")
+            "fctn_server_finished", "fctn_quality", "fctn_grow_ranks")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
 
 
@@ -269,6 +271,16 @@ def fctn_get_X(h, out):
     p, w = _ptr(out)
     _check(lib.fctn_get_X(h, p, w))
     return out
+
+
+def fctn_grow_ranks(h, R, scale, seed):
+    """Raise the FCTN ranks to R (N x N, a < b read); see include/fctn.h."""
+    r = ((ctypes.c_int32 * MAX_ORDER) * MAX_ORDER)()
+    N = len(R)
+    for a in range(N):
+        for b in range(a + 1, N):
+            r[a][b] = int(R[a][b])
+    _check(lib.fctn_grow_ranks(h, ctypes.byref(r), float(scale), ctypes.c_uint64(int(seed) & (2 ** 64 - 1))))
 
 
 def fctn_quality(h, truth):

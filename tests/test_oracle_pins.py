@@ -437,3 +437,29 @@ def test_ssim_scaled_zero_mean_structure_term():
     for a in (0.5, 2.0, -1.0):
         want = 2 * a / (1 + a * a)
         assert abs(O.ssim(a * T, T) - want) < 1e-6, a
+
+
+# ---- rank growth: SplitMix64 and the padding of the factors ---------------
+def test_splitmix64_reference_outputs():
+    """First outputs of SplitMix64 seeded with 0 (the published reference values)."""
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC, 0x1B39896A51A8749B]
+    got = [int(x) for x in O.splitmix64(0, np.arange(5))]
+    assert got == want
+
+
+def test_growth_values_range_and_padding():
+    v = O.growth_values(7, 2, 10000, 0.5)
+    assert v.min() >= -0.5 and v.max() < 0.5 and abs(v.mean()) < 0.02
+    rng = np.random.default_rng(3)
+    dims = (4, 5, 6)
+    R0 = np.full((3, 3), 1)
+    R1 = np.array([[0, 2, 1], [2, 0, 3], [1, 3, 0]])
+    fs = [rng.standard_normal(O.factor_shape(dims, R0, k)) for k in range(3)]
+    g = O.grow_factors(fs, R0, R1, 0.1, 99)
+    for k in range(3):
+        assert g[k].shape == O.factor_shape(dims, R1, k)
+        np.testing.assert_array_equal(g[k][tuple(slice(0, s) for s in fs[k].shape)], fs[k])
+    # unchanged ranks: the factors are returned as they are
+    same = O.grow_factors(fs, R0, R0, 0.1, 99)
+    for a, b in zip(same, fs):
+        np.testing.assert_array_equal(a, b)
