@@ -298,6 +298,7 @@ def run_ours(args):
     }
     if ws == 1 and not args.no_extras:
         line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps)
+        line["rank_growth"] = rank_growth_run(F, name, truth, Y, mask, init, R)
         line["serving"] = serving_mix(args.serve_jobs)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
@@ -340,6 +341,45 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100)
             F.fctn_destroy(h)
     return {"unit": UNIT, "sweeps_per_s": out, "workload": name,
             "quality_after_sweeps": max(quality_sweeps, steps + 3), "quality": quality}
+
+
+def rank_growth_run(F, name, truth, Y, mask, init, R, grow_every=5, tol=1e-4, max_sweeps=150):
+    """Plain FP32 to rel < tol (or max_sweeps) with fixed ranks R, and with the
+    ranks grown from one to R (growth.complete_with_growth); wall time, sweeps,
+    PSNR and SSIM of each."""
+    import torch
+    from paper_2510_22506_gb300 import growth
+    N = Y.ndim
+    kw = dict(lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO)
+    truth32 = np.ascontiguousarray(truth.astype(np.float32))
+    out = {"workload": name, "tol": tol, "max_sweeps": max_sweeps}
+    p = F.make_params(Y.shape, R, precision="fp32", **kw)
+    h = F.fctn_create(p)
+    try:
+        F.fctn_set_data(h, np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8))
+        F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(np.float32)) for a in init])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = F.fctn_complete(h, tol, max_sweeps)
+        wall = time.perf_counter() - t0
+        ps, ss = F.fctn_quality(h, truth32)
+        out["fixed_ranks"] = {"sweeps": st["t"], "wall_s": wall, "rel_change": st["rel_change"], "psnr_db": ps,
+                              "ssim": ss}
+    finally:
+        F.fctn_destroy(h)
+    init1 = synth.init_factors(Y.shape, np.ones((N, N), dtype=int), 3900)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h, hist = growth.complete_with_growth(Y, mask, init1, R, grow_every, 0.1, 4242, tol, max_sweeps,
+                                          precision="fp32", **kw)
+    try:
+        wall = time.perf_counter() - t0
+        ps, ss = F.fctn_quality(h, truth32)
+        out["grown_from_one"] = {"grow_every": grow_every, "sweeps": len(hist), "wall_s": wall,
+                                 "rel_change": hist[-1]["rel_change"], "psnr_db": ps, "ssim": ss}
+    finally:
+        F.fctn_destroy(h)
+    return out
 
 
 def serving_mix(n_jobs):

@@ -15,7 +15,11 @@
  * the solution of the Sylvester system of Eq. 5, solved through the
  * eigenbases of L_k and of the Gram M_k M_k^T (Eqs. 7-9), then X is updated
  * in closed form (Eq. 10).  Algorithm 2 adds intermediate-tensor reuse and a
- * permuted update order (Sec. 3.3).
+ * permuted update order (Sec. 3.3): for N >= 4 the merged tensors of one
+ * half of the modes (1..N/2 or N/2+1..N) share the contraction of the other
+ * half (for N = 4 the pairs of Sec. 3.3; for N >= 5 this build's reading of
+ * Table 2), and the alternating order starts every even sweep with the
+ * second half.
  *
  * Layout: all tensors are dense row-major (C order).  X and Y have shape
  * (I_1, ..., I_N).  Factor k has the shape above (A_k's own mode at position

@@ -38,7 +38,9 @@ Readings of passages the paper leaves open (each is also listed in the design doc):
   ``"alternate"``: for N = 4, odd sweeps update (1,2,3,4) and even sweeps
   (3,4,1,2), so each sweep starts with the pair whose shared intermediate
   tensor is still valid (this reproduces the t >= 2 row of Table 1).  For
-  N != 4 the order stays (1..N).
+  N >= 5 the same with the halves (1..N/2) and (N/2+1..N) of the modes,
+  whose intermediates are shared (Table 2's general-order reuse, whose
+  scheme is not printed).  For N <= 3 the order stays (1..N).
 * Eq. (8) is evaluated with the real orthonormal eigenbasis of the symmetric
   circulant L_k (numpy.linalg.eigh) in place of the complex DFT; the solution
   is the same.  The orientation of T is I_k x s_k with
@@ -201,6 +203,49 @@ def merged_from_pair(factors, k, T, Tl, counter=None):
     N = len(factors)
     _, b = pair_of(N, k)
     cur, cl = _contract(factors[b], _factor_labels(N, b), T, Tl, counter, "M")
+    out, _ = _to_order(cur, cl, merged_labels(N, k))
+    return np.ascontiguousarray(out)
+
+
+def halves(N):
+    """The two halves of the modes whose intermediates are shared: modes
+    0 .. N//2 - 1 and N//2 .. N-1 (for N = 4 the pairs (1,2), (3,4) of Sec. 3.3)."""
+    return list(range(N // 2)), list(range(N // 2, N))
+
+
+def half_of(N, k):
+    """For N >= 4: the other half (whose intermediate M_k reuses) and the
+    members of k's own half except k.  Generalises pair_of: every M_k of one
+    half shares the contraction of the whole other half."""
+    if N < 4:
+        raise ValueError("half sharing is defined for N >= 4")
+    H = halves(N)
+    q = 0 if k < N // 2 else 1
+    return tuple(H[1 - q]), [t for t in H[q] if t != k]
+
+
+def half_intermediate(factors, members, counter=None):
+    """T_H: the contraction of the factors of a half, in ascending order
+    (for two members the pair intermediate T_cd)."""
+    if len(members) == 2:
+        return pair_intermediate(factors, members[0], members[1], counter)
+    N = len(factors)
+    cur, cl = factors[members[0]], _factor_labels(N, members[0])
+    for t in members[1:]:
+        cur, cl = _contract(cur, cl, factors[t], _factor_labels(N, t), counter, "M")
+    return cur, cl
+
+
+def merged_from_half(factors, k, T, Tl, counter=None):
+    """M_k = (contraction of k's own half except k) x T_other (reuse path)."""
+    N = len(factors)
+    _, own = half_of(N, k)
+    if len(own) == 1 and N == 4:
+        return merged_from_pair(factors, k, T, Tl, counter)
+    cur, cl = factors[own[0]], _factor_labels(N, own[0])
+    for t in own[1:]:
+        cur, cl = _contract(cur, cl, factors[t], _factor_labels(N, t), counter, "M")
+    cur, cl = _contract(cur, cl, T, Tl, counter, "M")
     out, _ = _to_order(cur, cl, merged_labels(N, k))
     return np.ascontiguousarray(out)
 
@@ -455,9 +500,12 @@ class State:
 
 
 def sweep_order(N, t_next, policy):
-    """Update order n of sweep number t_next (1-based), Algorithm 2."""
-    if policy == ORDER_ALTERNATE and N == 4 and t_next % 2 == 0:
-        return [2, 3, 0, 1]
+    """Update order n of sweep number t_next (1-based), Algorithm 2: with the
+    alternating order (N >= 4) even sweeps take the second half of the modes
+    first, whose shared intermediate (of the first half) is still valid."""
+    if policy == ORDER_ALTERNATE and N >= 4 and t_next % 2 == 0:
+        h0, h1 = halves(N)
+        return h1 + h0
     if policy not in (ORDER_PLAIN, ORDER_ALTERNATE):
         raise ValueError(policy)
     return list(range(N))
@@ -475,16 +523,15 @@ def init_state(Y, mask, factors):
 
 def _merged(state, prob, k, reuse):
     N = len(prob.dims)
-    if reuse and N == 4:
-        (c, d), _ = pair_of(N, k)
-        ent = state.cache.get((c, d))
-        if ent is None or ent[2] != (state.versions[c], state.versions[d]):
-            T, Tl = pair_intermediate(state.factors, c, d, state.counter)
-            state.cache[(c, d)] = (T, Tl, (state.versions[c], state.versions[d]))
-        T, Tl, _ = state.cache[(c, d)]
-        return merged_from_pair(state.factors, k, T, Tl, state.counter)
-    if reuse and N > 4:
-        raise NotImplementedError("intermediate reuse is defined here for N <= 4")
+    if reuse and N >= 4:
+        other, _ = half_of(N, k)
+        vers = tuple(state.versions[t] for t in other)
+        ent = state.cache.get(other)
+        if ent is None or ent[2] != vers:
+            T, Tl = half_intermediate(state.factors, list(other), state.counter)
+            state.cache[other] = (T, Tl, vers)
+        T, Tl, _ = state.cache[other]
+        return merged_from_half(state.factors, k, T, Tl, state.counter)
     return merged_sequential(state.factors, k, state.counter)
 
 
@@ -500,8 +547,8 @@ def pam_sweep(state, prob, reuse=True, policy=ORDER_ALTERNATE, trace_blocks=Fals
     asymmetric extrapolation right after its update (the multi-temporal HSI
     variant of Sec. 4.3); None is the plain method.
 
-    With ``reuse`` the merged tensors come from cached pair intermediates
-    (N = 4) and FCTN(A^{t+1}) for the X update is A_last(last) M'_last, where
+    With ``reuse`` the merged tensors come from cached half intermediates
+    (N >= 4; pairs for N = 4) and FCTN(A^{t+1}) for the X update is A_last(last) M'_last, where
     M'_last is the merged tensor of the factor updated last (every other
     factor is already new there).  Without ``reuse`` every merged tensor and
     FCTN(A^{t+1}) are contracted from scratch.

@@ -107,8 +107,7 @@ struct fctn_handle {
   void* ones = nullptr;           // the constant 1 (second operand when N = 2)
   void* Lbuf = nullptr;           // chain intermediate (no pair cache, N >= 4)
   void* T[2] = {nullptr, nullptr};
-  View Tv[2];
-  int Tver[2][2] = {{-1, -1}, {-1, -1}};
+  int Tver[2][FCTN_MAX_ORDER] = {};  // versions of the members of each half when T was built
   bool Tvalid[2] = {false, false};
   void* chain[2] = {nullptr, nullptr};
   void* part = nullptr;
@@ -329,6 +328,48 @@ int run_chain(fctn_handle* h, const int* ids, int nids, const Lab* final_order, 
   return FCTN_OK;
 }
 
+// Halves of the modes whose intermediates are shared (Algorithm 2; for
+// N = 4 the pairs (1,2) and (3,4); for N >= 5 the generalisation of Table 2's
+// reuse): half 0 = modes 0 .. N/2 - 1, half 1 = the rest.  Every M_k of one
+// half contracts the other half's intermediate with its own half's other
+// factors.
+int half_lo(const fctn_handle* h, int q) { return q == 0 ? 0 : h->N / 2; }
+int half_hi(const fctn_handle* h, int q) { return q == 0 ? h->N / 2 : h->N; }
+int half_of(const fctn_handle* h, int k) { return k < h->N / 2 ? 0 : 1; }
+
+// The members of k's own half except k; returns their count.
+int own_others(const fctn_handle* h, int k, int* ids) {
+  const int q = half_of(h, k);
+  int n = 0;
+  for (int u = half_lo(h, q); u < half_hi(h, q); ++u)
+    if (u != k) ids[n++] = u;
+  return n;
+}
+
+// Intermediate of half q: its modes ascending, then for every member u
+// (ascending) its bonds (u, v) to the other half, v ascending.
+View half_out_view(const fctn_handle* h, int q, Lab* ord, int* n) {
+  int m = 0;
+  const int lo = half_lo(h, q), hi = half_hi(h, q);
+  for (int u = lo; u < hi; ++u) ord[m++] = mode_lab(u);
+  for (int u = lo; u < hi; ++u)
+    for (int v = 0; v < h->N; ++v)
+      if (v < lo || v >= hi) ord[m++] = bond_lab(u, v);
+  *n = m;
+  int64_t ext[FCTN_MAXD];
+  for (int i = 0; i < m; ++i) ext[i] = ord[i].kind == 0 ? h->I[ord[i].a] : rank_of(h, ord[i].a, ord[i].b);
+  return dense_view(m, ord, ext);
+}
+bool reuse_pairs(const fctn_handle* h) { return h->p.reuse && h->N >= 4; }
+
+// The cached intermediate of half q is current (built from the members' present versions).
+bool half_valid(const fctn_handle* h, int q) {
+  if (!h->Tvalid[q]) return false;
+  for (int u = half_lo(h, q); u < half_hi(h, q); ++u)
+    if (h->Tver[q][u - half_lo(h, q)] != h->ver[u]) return false;
+  return true;
+}
+
 // Sizes of every intermediate of the chains (for allocation).
 int64_t chain_need(const fctn_handle* h) {
   int64_t need = 0;
@@ -356,31 +397,18 @@ int64_t chain_need(const fctn_handle* h) {
   }
   for (int t = 0; t < h->N; ++t) ids[t] = t;
   sim(ids, h->N);
+  if (reuse_pairs(h)) {  // half intermediates and the own-half chains
+    for (int q = 0; q < 2; ++q) {
+      int m = 0;
+      for (int u = half_lo(h, q); u < half_hi(h, q); ++u) ids[m++] = u;
+      sim(ids, m);
+    }
+    for (int k = 0; k < h->N; ++k) sim(ids, own_others(h, k, ids));
+  }
   return need;
 }
 
 // Pair intermediates of Algorithm 2 (N = 4): index 0 = (A_1, A_2), 1 = (A_3, A_4).
-void pair_info(int k, int* pidx, int* c, int* d, int* b) {
-  if (k < 2) { *pidx = 1; *c = 2; *d = 3; *b = 1 - k; }
-  else { *pidx = 0; *c = 0; *d = 1; *b = 5 - k; }
-}
-
-View pair_out_view(const fctn_handle* h, int c, int d, Lab* ord, int* n) {
-  int m = 0;
-  ord[m++] = mode_lab(c);
-  ord[m++] = mode_lab(d);
-  for (int u = 0; u < h->N; ++u)
-    if (u != c && u != d) ord[m++] = bond_lab(c, u);
-  for (int u = 0; u < h->N; ++u)
-    if (u != c && u != d) ord[m++] = bond_lab(d, u);
-  *n = m;
-  int64_t ext[FCTN_MAXD];
-  for (int i = 0; i < m; ++i) ext[i] = ord[i].kind == 0 ? h->I[ord[i].a] : rank_of(h, ord[i].a, ord[i].b);
-  return dense_view(m, ord, ext);
-}
-
-bool reuse_pairs(const fctn_handle* h) { return h->p.reuse && h->N == 4; }
-
 int64_t view_row(const View& v) {
   int64_t r = 1;
   for (int i = 0; i < v.n; ++i)
@@ -443,12 +471,13 @@ void pair_operands(const fctn_handle* h, int k, View* L, View* R) {
     return;
   }
   if (reuse_pairs(h)) {
-    int pidx, c, d, b;
-    pair_info(k, &pidx, &c, &d, &b);
+    const int o = 1 - half_of(h, k);
+    int ids[FCTN_MAX_ORDER];
+    const int n = own_others(h, k, ids);
     Lab ord[FCTN_MAXD];
-    int n;
-    *L = factor_view(h, b);
-    *R = pair_out_view(h, c, d, ord, &n);
+    int no;
+    *R = half_out_view(h, o, ord, &no);
+    *L = n == 1 ? factor_view(h, ids[0]) : chain_result_view(h, ids, n, ord, &no);
     return;
   }
   int ids[FCTN_MAX_ORDER], n, lo;
@@ -551,24 +580,31 @@ int prepare_pair(fctn_handle* h, int k, const void** L, const void** R) {
     return FCTN_OK;
   }
   if (reuse_pairs(h)) {
-    int pidx, c, d, b;
-    pair_info(k, &pidx, &c, &d, &b);
-    if (!h->Tvalid[pidx] || h->Tver[pidx][0] != h->ver[c] || h->Tver[pidx][1] != h->ver[d]) {
+    const int o = 1 - half_of(h, k);
+    if (!half_valid(h, o)) {
       Lab ord[FCTN_MAXD];
       int n;
-      pair_out_view(h, c, d, ord, &n);
-      View A = factor_view(h, c), B = factor_view(h, d);
-      ContractPlan p;
-      int rc = make_plan(A, &B, ord, n, &p, &h->Tv[pidx]);
+      half_out_view(h, o, ord, &n);
+      int ids[FCTN_MAX_ORDER], m = 0;
+      for (int u = half_lo(h, o); u < half_hi(h, o); ++u) ids[m++] = u;
+      int rc = run_chain(h, ids, m, ord, n, h->T[o]);
       if (rc) return rc;
-      rc = launch_plan(h, h->Ac[c], h->Ac[d], h->T[pidx], p);
-      if (rc) return rc;
-      h->Tvalid[pidx] = true;
-      h->Tver[pidx][0] = h->ver[c];
-      h->Tver[pidx][1] = h->ver[d];
+      h->Tvalid[o] = true;
+      for (int u = half_lo(h, o); u < half_hi(h, o); ++u) h->Tver[o][u - half_lo(h, o)] = h->ver[u];
     }
-    *L = h->Ac[b];
-    *R = h->T[pidx];
+    int ids[FCTN_MAX_ORDER];
+    const int n = own_others(h, k, ids);
+    if (n == 1) {
+      *L = h->Ac[ids[0]];
+    } else {
+      Lab ord[FCTN_MAXD];
+      int no;
+      chain_result_view(h, ids, n, ord, &no);
+      int rc = run_chain(h, ids, n, ord, no, h->Lbuf);
+      if (rc) return rc;
+      *L = h->Lbuf;
+    }
+    *R = h->T[o];
     return FCTN_OK;
   }
   int ids[FCTN_MAX_ORDER], n, lo;
@@ -623,7 +659,6 @@ int check_params(const fctn_params* p) {
     return fail(FCTN_E_ARG, "unknown gram mode %d", p->gram_mode);
   if (p->refine_steps < 0 || p->refine_steps > 8) return fail(FCTN_E_ARG, "refine_steps %d outside [0, 8]", p->refine_steps);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
-  if (p->reuse && p->order > 4) return fail(FCTN_E_UNSUPPORTED, "intermediate reuse is built for N <= 4");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
     if (!(p->lambda[k] >= 0) || !(p->delta[k] >= 0)) return fail(FCTN_E_ARG, "lambda/delta[%d] must be >= 0", k);
@@ -664,8 +699,20 @@ struct Sizes {
 bool materialise_ok(const fctn_handle* h, int k) { return (double)h->s[k] * h->Pk[k] * h->esz <= 64.0 * 1024 * 1024; }
 
 int64_t lbuf_need(const fctn_handle* h) {
-  if (h->N < 4 || reuse_pairs(h)) return 0;
+  if (h->N < 4) return 0;
   int64_t need = 0;
+  if (reuse_pairs(h)) {  // the own-half chains of M_k (more than one other member: N >= 5)
+    for (int k = 0; k < h->N; ++k) {
+      int ids[FCTN_MAX_ORDER];
+      const int n = own_others(h, k, ids);
+      if (n < 2) continue;
+      Lab ord[FCTN_MAXD];
+      int no;
+      int64_t sz = chain_result_view(h, ids, n, ord, &no).size();
+      if (sz > need) need = sz;
+    }
+    return need;
+  }
   for (int k = 0; k < h->N; ++k) {
     int ids[FCTN_MAX_ORDER], n, lo;
     chain_ids(h, k, ids, &n, &lo);
@@ -794,11 +841,10 @@ Sizes sizes_of(const fctn_handle* h) {
   z.chain = chain_need(h);
   z.lbuf = lbuf_need(h);
   if (reuse_pairs(h)) {
-    for (int pidx = 0; pidx < 2; ++pidx) {
+    for (int q = 0; q < 2; ++q) {
       Lab ord[FCTN_MAXD];
       int n;
-      int c = pidx == 0 ? 0 : 2, d = c + 1;
-      z.T[pidx] = pair_out_view(h, c, d, ord, &n).size();
+      z.T[q] = half_out_view(h, q, ord, &n).size();
     }
   }
   return z;
@@ -1002,8 +1048,10 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
 }
 
 void sweep_order(const fctn_handle* h, int64_t t_next, int* order) {
-  if (h->p.order_policy == FCTN_ORDER_ALTERNATE && h->N == 4 && t_next % 2 == 0) {
-    order[0] = 2; order[1] = 3; order[2] = 0; order[3] = 1;
+  if (h->p.order_policy == FCTN_ORDER_ALTERNATE && h->N >= 4 && t_next % 2 == 0) {
+    int m = 0;  // second half first: the first half's intermediate is still valid
+    for (int u = half_lo(h, 1); u < half_hi(h, 1); ++u) order[m++] = u;
+    for (int u = half_lo(h, 0); u < half_hi(h, 0); ++u) order[m++] = u;
     return;
   }
   for (int k = 0; k < h->N; ++k) order[k] = k;
@@ -1069,8 +1117,7 @@ uint64_t sweep_key(const fctn_handle* h) {
   uint64_t key = (uint64_t)((h->t + 1) % 2);
   for (int k = 0; k < h->N; ++k) key |= (uint64_t)(h->cvalid[k] ? 1 : 0) << (1 + k);
   for (int q = 0; q < 2; ++q) {
-    int c = q == 0 ? 0 : 2, d = c + 1;
-    bool v = reuse_pairs(h) && h->Tvalid[q] && h->Tver[q][0] == h->ver[c] && h->Tver[q][1] == h->ver[d];
+    bool v = reuse_pairs(h) && half_valid(h, q);
     key |= (uint64_t)(v ? 1 : 0) << (12 + q);
   }
   return key;

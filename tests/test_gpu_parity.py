@@ -75,6 +75,27 @@ def test_fp64_fourth_order_ragged_alternate_order(F):
             assert rel(a, b) <= 1e-9
 
 
+@pytest.mark.parametrize("dims,r", [((5, 4, 3, 4, 3), 2), ((3, 4, 2, 3, 2, 3), 2)])
+def test_fp64_order_5_and_6_half_reuse(F, dims, r):
+    """N >= 5: half-network intermediates (reuse) and the alternating order."""
+    d = inputs(None, dims=dims, r=r, p=0.4, idx=49, noise=0.0, cap=None)
+    for reuse in (True, False):
+        st, _ = oracle_run(d, 6, reuse=reuse, policy="alternate")
+        g = gpu_run(F, d, 6, precision="fp64", reuse=reuse, policy="alternate")
+        assert rel(g["X"], st.X) <= 1e-9, (reuse, rel(g["X"], st.X))
+        for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+            assert rel(a, b) <= 1e-9, (reuse, k, rel(a, b))
+
+
+def test_fp32_order_5_half_reuse(F):
+    d = inputs(None, dims=(9, 8, 6, 7, 5), r=2, p=0.3, idx=50, noise=0.0, cap=None, dtype=np.float32)
+    st, _ = oracle_run(d, 8, reuse=True, policy="alternate")
+    g = gpu_run(F, d, 8, precision="fp32", reuse=True, policy="alternate")
+    assert rel(g["X"], st.X) <= 1e-4, rel(g["X"], st.X)
+    for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+        assert rel(a, b) <= 1e-4, (k, rel(a, b))
+
+
 def test_fp64_second_order(F):
     d = inputs(None, dims=(37, 29), r=5, p=0.4, idx=41, noise=0.0, cap=None)
     st, _ = oracle_run(d, 10)

@@ -463,3 +463,51 @@ def test_growth_values_range_and_padding():
     same = O.grow_factors(fs, R0, R0, 0.1, 99)
     for a, b in zip(same, fs):
         np.testing.assert_array_equal(a, b)
+
+
+# ---- order N >= 5: half-network intermediates (Table 2's reuse) ---------
+@pytest.mark.parametrize("dims,r", [((3, 4, 2, 3, 2), 2), ((2, 3, 2, 2, 3, 2), 2)])
+def test_half_intermediates_give_the_merged_tensor(dims, r):
+    N = len(dims)
+    R = np.full((N, N), r)
+    fs = _rand_factors(dims, R, 5)
+    for k in range(N):
+        other, own = O.half_of(N, k)
+        T, Tl = O.half_intermediate(fs, list(other))
+        M1 = O.merged_matrix(O.merged_from_half(fs, k, T, Tl), dims, R, k)
+        M0 = O.merged_matrix(O.merged_sequential(fs, k), dims, R, k)
+        np.testing.assert_allclose(M1, M0, rtol=1e-12, atol=1e-12)
+
+
+def test_fifth_order_reuse_on_off_agree_and_share_halves():
+    dims, r = (3, 4, 3, 2, 3), 2
+    N = len(dims)
+    R = np.full((N, N), r)
+    rng = np.random.default_rng(21)
+    truth = O.fctn_full(_rand_factors(dims, R, 6))
+    mask = rng.random(dims) < 0.5
+    Y = np.where(mask, truth, 0.0)
+    init = _rand_factors(dims, R, 7)
+    prob = O.Problem(dims=dims, R=R, lam=(0.01,) * N, delta=(0.5,) * N, rho=0.1)
+    a = O.init_state(Y, mask, init)
+    b = O.init_state(Y, mask, init)
+    built = []
+    orig = O.half_intermediate
+
+    def spy(fs, members, counter=None):
+        built.append((a.t, tuple(members)))
+        return orig(fs, members, counter)
+
+    O.half_intermediate = spy
+    try:
+        for _ in range(4):
+            O.pam_sweep(a, prob, reuse=True, policy=O.ORDER_ALTERNATE)
+            O.pam_sweep(b, prob, reuse=False, policy=O.ORDER_ALTERNATE)
+    finally:
+        O.half_intermediate = orig
+    np.testing.assert_allclose(a.X, b.X, rtol=1e-12, atol=1e-12)
+    for x, y in zip(a.factors, b.factors):
+        np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-12)
+    # both halves at t = 1, then one per sweep (the other is still valid)
+    per = [sum(1 for c in built if c[0] == t) for t in range(4)]
+    assert per == [2, 1, 1, 1], built
