@@ -635,9 +635,9 @@ GramPlan gram_plan(const fctn_handle* h, int k) {
   int64_t ctas_per_split = g.tiles_r * g.tiles_c;
   if (h->tc) ctas_per_split = h->tp[k].n_groups > 0 ? h->tp[k].n_groups : 1;
   int64_t target = (2 * 152 + ctas_per_split - 1) / ctas_per_split;
-  // tensor-core path: at least four 32-column chunks per CTA, so the per-split
+  // tensor-core path: at least two 32-column chunks per CTA, so the per-split
   // partial (s x (s + I) floats) stays small against the columns it consumes
-  int64_t maxsplit = h->tc ? (g.Pk + 127) / 128 : (g.Pk + 31) / 32;
+  int64_t maxsplit = h->tc ? (g.Pk + 63) / 64 : (g.Pk + 31) / 32;
   int64_t ks = target < maxsplit ? target : maxsplit;
   if (ks < 1) ks = 1;
   int64_t chunk = (g.Pk + ks - 1) / ks;

@@ -27,16 +27,11 @@
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 512;  // 16 warps; TMEM lane quarter = warp % 4
 constexpr long long kSpinLimit = 1ll << 26;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ int64_t xaddr(const ModeView& v, int64_t i, int64_t j) {
-  uint32_t jj = (uint32_t)j, post = (uint32_t)v.post;
-  uint32_t a = jj / post, b = jj - a * post;
-  return ((int64_t)a * v.I + i) * v.post + b;
-}
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0));
@@ -76,6 +71,18 @@ __device__ __forceinline__ uint32_t op_off(int r, int k, int BK) {
   const uint32_t sbo = (uint32_t)(BK / Op::kc) * 128u;
   return (uint32_t)(r >> 3) * sbo + (uint32_t)(k / Op::kc) * 128u + (uint32_t)(r & 7) * 16u +
          (uint32_t)(k % Op::kc) * (16u / Op::kc);
+}
+
+// Element e of an operand with BK columns taken in core-matrix order: core
+// matrix e / (8 kc) (row block, column block; lg_nkc = log2(BK / kc)), then its
+// 8 rows x kc columns row-major, so that consecutive e are consecutive bytes
+// (a warp's stores hit distinct banks).
+template <class Op>
+__device__ __forceinline__ void cm_rc(int e, int lg_nkc, int& r, int& k) {
+  constexpr int per = 8 * Op::kc;
+  const int cm = e / per, w = e - cm * per;
+  r = ((cm >> lg_nkc) << 3) + w / Op::kc;
+  k = (cm & ((1 << lg_nkc) - 1)) * Op::kc + w % Op::kc;
 }
 
 // tcgen05 shared-memory matrix descriptor (no swizzle, version 1).
@@ -172,6 +179,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   __shared__ int abort_flag;
   __shared__ int lsl[32], rsl[32], cnt[2];  // row slot of every column, distinct-row counts
+  __shared__ int64_t xcol[32];              // offset of X_(k)[0, j] of every column (-1 past the chunk)
+  const int lg_nkc = __ffs(BK / Op::kc) - 1;
 
   for (int e = tid; e < s; e += TC_THREADS) {
     lo[e] = p.tab[e];
@@ -235,7 +244,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
       if (abort_flag) break;
     }
     // 1. the distinct L and R rows of the chunk's columns
-    if (warp == 0) fctn_tile::chunk_slots(p, k0, BK, ke, lsl, rsl, cl, cr, cnt);
+    if (warp == 0) {
+      fctn_tile::chunk_slots(p, k0, BK, ke, lsl, rsl, cl, cr, cnt);
+      if (lane < BK) {  // j = a * post + b'  ->  a * I * post + b'
+        const int64_t j = k0 + lane;
+        const uint32_t post = (uint32_t)g.xv.post, jj = (uint32_t)j;
+        const uint32_t a = jj / post;
+        xcol[lane] = j < ke ? ((int64_t)a * g.xv.I) * g.xv.post + (jj - a * post) : -1;
+      }
+    }
     __syncthreads();
     for (int e = tid; e < cnt[0] * p.Ljs; e += TC_THREADS) {
       int q = e / p.Ljs, c_ = e - q * p.Ljs;
@@ -246,46 +263,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
       cp_async4(Rs + e, R + cr[q] + c_, true);
     }
     asm volatile("cp.async.commit_group;\n" ::);
-    // 3. X rows of this group into the X operand (overlaps the slab copies)
+    // 3. X rows of this group into the X operand (overlaps the slab copies),
+    //    in core-matrix order; rows >= xvalid stay zero
     if (grp.xw > 0) {
       unsigned char* xb = X_buf[b];
-      if (g.xv.post == 1) {
-        const int xvalid = (int)min((int64_t)grp.xw, g.I - grp.xi0);
-        for (int e = tid; e < xvalid * BK; e += TC_THREADS) {
-          int r = e % xvalid, kk = e / xvalid;  // r fastest: X[j*I + i] contiguous in i
-          int64_t i = grp.xi0 + r, j = k0 + kk;
-          float v = (j < ke) ? X[j * g.xv.I + i] : 0.f;
-          Op::put(xb, op_off<Op>(r, kk, BK), x_lo, v);
-        }
-      } else if (g.xv.post % 4 == 0) {
-        // four consecutive columns of one row are contiguous and 16-byte aligned
-        const int xvalid = (int)min((int64_t)grp.xw, g.I - grp.xi0);
-        const int ng = BK / 4;
-        for (int e = tid; e < xvalid * ng; e += TC_THREADS) {
-          int r = e / ng, kq = (e % ng) * 4;
-          int64_t i = grp.xi0 + r, j = k0 + kq;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j + 3 < ke) {
-            v = __ldg((const float4*)(X + xaddr(g.xv, i, j)));
-          } else {
-            float t[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int q = 0; q < 4; ++q)
-              if (j + q < ke) t[q] = X[xaddr(g.xv, i, j + q)];
-            v = make_float4(t[0], t[1], t[2], t[3]);
-          }
-          Op::put(xb, op_off<Op>(r, kq, BK), x_lo, v.x);
-          Op::put(xb, op_off<Op>(r, kq + 1, BK), x_lo, v.y);
-          Op::put(xb, op_off<Op>(r, kq + 2, BK), x_lo, v.z);
-          Op::put(xb, op_off<Op>(r, kq + 3, BK), x_lo, v.w);
-        }
-      } else {
-        const int xvalid = (int)min((int64_t)grp.xw, g.I - grp.xi0);
-        for (int e = tid; e < xvalid * BK; e += TC_THREADS) {
-          int kk = e % BK, r = e / BK;
-          int64_t i = grp.xi0 + r, j = k0 + kk;
-          float v = (j < ke) ? X[xaddr(g.xv, i, j)] : 0.f;
-          Op::put(xb, op_off<Op>(r, kk, BK), x_lo, v);
-        }
+      const int xvalid = (int)min((int64_t)grp.xw, g.I - grp.xi0);
+      const int rows8 = (xvalid + 7) & ~7;
+      for (int e = tid; e < rows8 * BK; e += TC_THREADS) {
+        int r, kk;
+        cm_rc<Op>(e, lg_nkc, r, kk);
+        if (r >= xvalid) continue;
+        const int64_t xc = xcol[kk];
+        const float v = xc >= 0 ? __ldg(X + xc + (int64_t)(grp.xi0 + r) * g.xv.post) : 0.f;
+        Op::put(xb, op_off<Op>(r, kk, BK), x_lo, v);
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -295,8 +285,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
     {
       unsigned char* ab = A_buf[b];
       const bool wm = Mout != nullptr && blockIdx.x == 0;
-      for (int e = tid; e < BK * s; e += TC_THREADS) {
-        int sg = e / BK, jj = e - sg * BK;
+      const int rows8 = (s + 7) & ~7;
+      for (int e = tid; e < rows8 * BK; e += TC_THREADS) {  // core-matrix order
+        int sg, jj;
+        cm_rc<Op>(e, lg_nkc, sg, jj);
+        if (sg >= s) continue;
         const float* l = Ls + lsl[jj] * p.Ljs + lo[sg];
         const float* r = Rs + rsl[jj] * p.Rjs + ro[sg];
         float a = 0.f;
@@ -357,11 +350,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(PairPlan p, const float*
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   if (!abort_flag && nchunk > 0) {
     float* P = part + (int64_t)blockIdx.z * g.s * g.ncols;
+    // a warp reads the TMEM lanes of its quarter (warp % 4); the warps of a
+    // quarter take turns over the groups of 8 columns
+    const int wq = warp & 3, wh = warp >> 2, nwh = TC_THREADS / 128;
     for (int mb = 0; mb < tp.n_mb; ++mb) {
-      const int row = mb * 128 + warp * 32 + lane;  // TMEM lane = row within the block
-      for (int c0 = 0; c0 < grp.width; c0 += 8) {
+      const int row = mb * 128 + wq * 32 + lane;  // TMEM lane = row within the block
+      for (int c0 = wh * 8; c0 < grp.width; c0 += 8 * nwh) {
         uint32_t v[8];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mb * grp.width + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(mb * grp.width + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
