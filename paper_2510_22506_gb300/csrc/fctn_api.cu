@@ -937,8 +937,10 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   const bool extrap = h->p.extrap_alpha != 0.0;
   if (extrap && !h->dry)
     CK(cudaMemcpyAsync(h->Aprev, h->A64[k], (size_t)I * s * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-  // FactGram on the side stream (overlapping the right-hand-side kernel),
-  // except under the per-class profiler, which times launches on `st`
+  // FactGram and the eigendecomposition of its Gram (which does not depend
+  // on X) on the side stream, overlapping the right-hand-side kernel and its
+  // reduction; the solve joins both.  The per-class profiler times launches
+  // on `st` one by one, so it runs them there.
   const bool fork = fg.use && h->side && h->prof_class < 0;
   cudaStream_t fst = fork ? h->side : h->st;
   void* HL = h->hbuf;
@@ -949,12 +951,17 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   }
   if (fg.use) {
     if (fork) {
-      if (h->f64)
+      if (h->f64) {
         LAUNCH_ON(3, launch_fact_gram_f64(fg, (const double*)L, (const double*)R, (double*)HL, (double*)HR, s, h->Gd,
                                           fst));
-      else
+        LAUNCH_ON(1, launch_eig_f64(h->Gd, (double*)h->Ck[k], (double*)h->Phi, (double*)h->gwork, s, warm, 60, tmin,
+                                    h->status, h->eig_used + k, fst));
+      } else {
         LAUNCH_ON(3, launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
                                           (float*)h->Gs, fst));
+        LAUNCH_ON(1, launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
+                                    60, tmin, h->status, h->eig_used + k, fst));
+      }
       if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
     } else if (h->f64) {
       LAUNCH(FCTN_KC_GRAM, 0.0, fact_flops,
@@ -975,8 +982,9 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     LAUNCH(FCTN_KC_REDUCE, red_bytes, part_elems,
            launch_reduce_gram_rhs_f64((const double*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, h->st));
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-    LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-           launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
+    if (!fork)
+      LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
+             launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
     // Eq. 8, then refinement passes on the FP64 residual of Eq. 5 (the
     // first residual is fused into the first backward pass)
     const int nref = h->p.refine_steps;
@@ -1010,9 +1018,10 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
            launch_reduce_gram_rhs_f32((const float*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, (float*)h->Gs,
                                       (float*)h->Ys, h->st));
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-    LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-           launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
-                          h->eig_used + k, h->st));
+    if (!fork)
+      LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
+             launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
+                            h->eig_used + k, h->st));
     const int nref = h->p.refine_steps;
     LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
            launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
