@@ -634,7 +634,11 @@ GramPlan gram_plan(const fctn_handle* h, int k) {
   g.tiles_c = (int)((g.ncols + 63) / 64);
   int64_t ctas_per_split = g.tiles_r * g.tiles_c;
   if (h->tc) ctas_per_split = h->tp[k].n_groups > 0 ? h->tp[k].n_groups : 1;
-  int64_t target = (2 * 152 + ctas_per_split - 1) / ctas_per_split;
+  // CTAs of the right-hand-side kernel: about 2 per SM; with the factored
+  // Gram (whose eigensolver runs beside it on the side branch) at most 144,
+  // so that SMs stay free for that branch
+  const int64_t ctas = h->fg[k].use ? 96 : 2 * 152;
+  int64_t target = (ctas + ctas_per_split - 1) / ctas_per_split;
   // tensor-core path: at least two 32-column chunks per CTA, so the per-split
   // partial (s x (s + I) floats) stays small against the columns it consumes
   int64_t maxsplit = h->tc ? (g.Pk + 63) / 64 : (g.Pk + 31) / 32;
