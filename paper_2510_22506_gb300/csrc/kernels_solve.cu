@@ -52,15 +52,19 @@ __device__ __forceinline__ T group_sum(T v) {
 // approximations (an inexact angle only leaves the pair slightly less
 // orthogonal), while c = 1/sqrt(1 + t^2) gets a Newton step so that the
 // rotation stays orthogonal to working precision.
-__device__ __forceinline__ void rot_cs(float al, float be, float ga, float& cs, float& sn) {
+__device__ __forceinline__ void rot_cs(float al, float be, float ga, float& cs, float& sn, float& t) {
   float zeta = __fdividef(be - al, 2.f * ga);
   float w = fmaf(zeta, zeta, 1.f);
   float sq = w * rsqrtf(w);
-  float t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sq);
+  t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sq);
   float x = fmaf(t, t, 1.f);
   float y = rsqrtf(x);
   cs = y * fmaf(-0.5f * x * y, y, 1.5f);  // one Newton step: c^2 (1 + t^2) = 1 to about an ulp
   sn = cs * t;
+}
+__device__ __forceinline__ void rot_cs(float al, float be, float ga, float& cs, float& sn) {
+  float t;
+  rot_cs(al, be, ga, cs, sn, t);
 }
 __device__ __forceinline__ void rot_cs(double al, double be, double ga, double& cs, double& sn) {
   double zeta = (be - al) / (2.0 * ga);
@@ -257,33 +261,16 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
   }
 }
 
-// ---------------------------------------- two-sided Jacobi, FP32, s <= 132 ----
+// ---------------------------------------- two-sided Jacobi, FP32, s <= 128 ----
 // The same decomposition G = C Phi C^T (Eq. 7) by the classical two-sided
-// cyclic Jacobi method on B = V^T G V (Jacobi 1846; parallel round-robin
-// order as in Golub & Van Loan, Sec. 8.5): each rotation J(p, q) zeroes
-// B_pq, B <- J^T B J, V <- V J; at convergence Phi = diag(B), C = V.
+// cyclic Jacobi method on B = V^T G V (Jacobi 1846; parallel orderings as in
+// Golub & Van Loan, Sec. 8.5): each rotation J(p, q) zeroes B_pq,
+// B <- J^T B J, V <- V J; at convergence Phi = diag(B), C = V.
 // Warm start: V = V0 (3I - V0^T V0)/2 (one Newton-Schulz step on the previous
-// sweep's C), B = V^T (G V).
-// Layout, one CTA: the index set is padded to m = s rounded up to 4 (the
-// padding rows/columns of B are zero and never rotate).  A round is two
-// phases.  (A) every pair k of the round is (p_k, q_k) with rotation
-// (c_k, s_k); a thread owns the 2x2 blocks (rows of pair k, columns of pair
-// l), k <= l, and replaces them in place by J_k^T X J_l (both triangles), and
-// rotates rows p_k, q_k of V^T (float4 along r); blocks and rows of pairs
-// that do not rotate are left alone.  (B) one thread per pair of the next
-// round reads B_pp, B_qq, B_pq and sets its rotation.
-// Rotation test and stop test as in k_eig1, on B: rotate iff
-// B_pq^2 > tol^2 |B_pp B_qq| + floor^2 (tol = sqrt(s) eps, floor =
-// eps ||G||_F / sqrt(s)); stop after a sweep whose largest rotated
-// B_pq^2 / |B_pp B_qq| was below tol (quadratic convergence).
-constexpr int EIG2_MAX = 132;
-constexpr int EIG2_PT = 3;  // B blocks and V units per thread: 66 * 67 / 2 <= 3 * 1024
+// sweep's C), B = V^T (G V).  The index set is padded to m = s rounded up to
+// 8 (the padding rows and columns of B are zero and never rotate).
 
-struct __align__(16) PairRot {
-  int p, q;
-  float c, sn;
-};
-
+// Pair idx of round `round` of the round-robin schedule over m indices.
 __device__ __forceinline__ void round_pair(int m, int round, int idx, int& p, int& q) {
   if (idx == 0) {
     p = m - 1;
@@ -349,41 +336,135 @@ __device__ __forceinline__ void sm_mm(float* __restrict__ out, int so, const flo
   }
 }
 
-// Rotation of pair (p, q) of round `round` from the current B.  Returns
-// B_pq^2 / |B_pp B_qq| if the pair rotates, else -1.
-__device__ __forceinline__ float set_rot(const float* __restrict__ B, int sb, int m, int round, int k, float tol2,
-                                         float floor2, PairRot* __restrict__ pt) {
-  int p, q;
-  round_pair(m, round, k, p, q);
-  const float bpp = B[p * sb + p], bqq = B[q * sb + q], bpq = B[p * sb + q];
-  const float ab = fabsf(bpp * bqq), g2 = bpq * bpq;
-  float c = 1.f, sn = 0.f, mu = -1.f;
-  if (g2 > tol2 * ab + floor2) {
-    rot_cs(bpp, bqq, bpq, c, sn);
-    mu = g2 / fmaxf(ab, FLT_MIN);
+// Block-ordered two-sided Jacobi (FP32, s <= EIG3_MAX), one CTA: cyclic
+// Jacobi sweeps whose pairs are ordered so that one parallel step
+// touches only the index sets of disjoint 8 x 8 subproblems.  The m indices
+// form nb = m / 4 blocks of four; outer round r pairs block P with block Q by
+// the round-robin schedule, and a warp rotates the submatrix B[S, S] of such
+// a pair (S = P u Q, local indices 0-3 and 4-7) in four rounds of cross pairs
+// (i, 4 + (i xor t)), preceded in the first outer round of a sweep by three
+// rounds of pairs within a block, accumulating the product U of its
+// rotations.  Every pair (p, q) is thus rotated once per sweep, as in a
+// scalar cyclic sweep, and the rotation of a pair sees the same B_pp, B_qq,
+// B_pq as it would there (rotations of other subproblems touch other rows
+// and columns).  The CTA then applies J = diag(U) over the subproblems by
+// 8 x 8 products held in registers: B <- J^T B and V^T <- J^T V^T (rows,
+// 8 x 4 tiles), then B <- B J (columns, 4 x 8 tiles), the diagonal
+// superblocks taking the warp's rotated submatrix.  Inner rounds cost warp
+// synchronisations only; an outer round costs three block barriers.
+// Rotation test and stop test: rotate iff B_pq^2 > tol^2 |B_pp B_qq| +
+// floor^2 (tol = sqrt(s) eps, floor = eps ||G||_F / sqrt(s)); stop after a
+// sweep whose largest rotated B_pq^2 / |B_pp B_qq| was below tol (quadratic
+// convergence: the next sweep would rotate nothing).
+constexpr int EIG3_MAX = 128;
+constexpr int EJ_SUB = 132;  // floats per subproblem: S (8 x 8), U (8 x 8), 4 against bank conflicts
+constexpr int EJ_NT = 512;   // most threads
+constexpr int EJ_TPT = 2;    // row tasks per thread: 128 * 128 / 16 <= 2 * 512
+
+// Pair k (0-3) of inner round t: within-block rounds t = 0-2 pair (0,1)(2,3),
+// (0,2)(1,3), (0,3)(1,2) inside block P (k = 0, 1) and block Q (k = 2, 3);
+// cross rounds pair (k, 4 + (k xor t)).
+__device__ __forceinline__ void ej_pair(bool within, int t, int k, int& p, int& q) {
+  if (within) {
+    constexpr unsigned code = 4u | 14u << 4 | 8u << 8 | 13u << 12 | 12u << 16 | 9u << 20;  // a | b << 2 per (t, k & 1)
+    const unsigned v = (code >> ((t * 2 + (k & 1)) * 4)) & 15u;
+    const int base = (k & 2) << 1;
+    p = base + (int)(v & 3u);
+    q = base + (int)(v >> 2);
+  } else {
+    p = k;
+    q = 4 + (k ^ t);
   }
-  pt[k] = {p, q, c, sn};
-  return mu;
 }
 
-__global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, float* __restrict__ Cio,
-                                               float* __restrict__ Phi, int s, int warm, int max_sweeps, double tmin,
-                                               int* status, int* sweeps_used) {
+// Rotation of a pair from its 2 x 2 block [a g; g b] without a branch:
+// t = sgn(d) 2g / (|d| + hypot(d, 2g)), d = b - a (the smaller root of
+// t^2 + 2 zeta t - 1 = 0, zeta = d / 2g), c = 1 / sqrt(1 + t^2) with one
+// Newton step (so that c^2 + sn^2 = 1 to about an ulp), sn = c t.  Returns
+// g^2 / |a b| if the pair rotates, else -1 with c = 1, sn = t = 0.
+__device__ __forceinline__ float ej_rot(float a, float b, float g, float tol2, float floor2, float& c, float& sn,
+                                        float& t) {
+  const float ab = fabsf(a * b), g2 = g * g;
+  const bool rot = g2 > tol2 * ab + floor2;
+  const float d = b - a, tg = 2.f * g;
+  const float h = fmaf(d, d, tg * tg);
+  const float hy = h * rsqrtf(h);
+  const float tt = __fdividef(d >= 0.f ? tg : -tg, fabsf(d) + hy);
+  const float x = fmaf(tt, tt, 1.f);
+  const float y = rsqrtf(x);
+  const float cc = y * fmaf(-0.5f * x * y, y, 1.5f);
+  c = rot ? cc : 1.f;
+  sn = rot ? cc * tt : 0.f;
+  t = rot ? tt : 0.f;
+  return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
+}
+
+// One inner round of a warp on its subproblem (S, U in shared memory), the
+// same instructions on every lane.  Lane L < 16 updates the 2 x 2 block
+// (L >> 2, L & 3) of the grid of this round's four pairs (rows rotated by
+// the first pair, columns by the second; a diagonal block keeps the exact
+// Jacobi update with zeroed off-diagonal), and every lane rotates row L >> 2
+// of U by pair L & 3.  Lanes 0, 5, 10, 15 count their pair's rotation.
+template <bool W, int T>
+__device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restrict__ Uw, int lane, float tol2,
+                                         float floor2, unsigned& cnt, float& cmu) {
+  const int k = (lane >> 2) & 3, l = lane & 3, ui = lane >> 2;
+  int pk, qk, pl, ql;
+  ej_pair(W, T, k, pk, qk);
+  ej_pair(W, T, l, pl, ql);
+  const float ak = Sw[pk * 9], bk = Sw[qk * 9], gk = Sw[pk * 8 + qk];
+  const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
+  const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
+  const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
+  const float u0 = Uw[ui * 8 + pl], u1 = Uw[ui * 8 + ql];
+  __syncwarp();  // every read of this round before any write
+  float ck, sk, tk, cl, sl, tl;
+  const float mu = ej_rot(ak, bk, gk, tol2, floor2, ck, sk, tk);
+  ej_rot(al, bl, gl, tol2, floor2, cl, sl, tl);
+  const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+  const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+  float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
+  float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
+  const bool dg = (k == l) && mu >= 0.f;
+  if (dg) {
+    z00 = fmaf(-tk, gk, ak);
+    z11 = fmaf(tk, gk, bk);
+    z01 = 0.f;
+    z10 = 0.f;
+  }
+  if (lane < 16) {
+    Sw[pk * 8 + pl] = z00;
+    Sw[pk * 8 + ql] = z01;
+    Sw[qk * 8 + pl] = z10;
+    Sw[qk * 8 + ql] = z11;
+  }
+  if (dg && lane < 16) {
+    ++cnt;
+    cmu = fmaxf(cmu, mu);
+  }
+  Uw[ui * 8 + pl] = cl * u0 - sl * u1;
+  Uw[ui * 8 + ql] = sl * u0 + cl * u1;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, float* __restrict__ Cio,
+                                                float* __restrict__ Phi, int s, int warm, int max_sweeps,
+                                                double tmin, int* status, int* sweeps_used) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int m = (s + 3) & ~3, sp = m + 4, sb = m + 1, npair = m / 2, m4 = m / 4;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int m = (s + 7) & ~7, sp = m + 4, nb = m / 4, nsub = m / 8;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   float* X1 = (float*)sm;
   float* X2 = X1 + m * sp;
-  float* X3 = X2 + m * sp;
-  PairRot* pt = (PairRot*)(X3 + m * sp);  // [npair]
+  float* X3 = X2 + m * sp;  // warm-start scratch
+  float* SC = X3 + m * sp;  // the subproblems
   __shared__ float red[32];
-  __shared__ unsigned wrot[3], wmu[3];  // per angle warp: rotations and largest ratio of a sweep
-  // ||G||_F
+  __shared__ unsigned wrot[32], wmu[32];  // per warp: rotations and largest ratio of a sweep
+  __shared__ int pq[16];                  // per subproblem: blocks P | Q << 16
   float fr = 0.f;
   for (int e = tid; e < s * s; e += nt) fr = fmaf(G[e], G[e], fr);
   fr = warp_sum(fr);
-  if ((tid & 31) == 0) red[tid >> 5] = fr;
-  // B in X1 (stride sb), V^T in X2 (stride sp)
+  if (lane == 0) red[warp] = fr;
+  // B in X1, V^T in X2 (both stride sp)
   if (warm) {
     for (int e = tid; e < m * m; e += nt) {  // X1 <- V0 (row r, column j), zero padded
       const int r = e / m, j = e % m;
@@ -401,7 +482,7 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
     __syncthreads();
     sm_mm<true>(X2, sp, X1, sp, X3, sp, m, 1.f, nullptr, 0, 0.f);  // W = G V = G^T V (G symmetric)
     __syncthreads();
-    sm_mm<true>(X1, sb, X3, sp, X2, sp, m, 1.f, nullptr, 0, 0.f);  // B = V^T W
+    sm_mm<true>(X1, sp, X3, sp, X2, sp, m, 1.f, nullptr, 0, 0.f);  // B = V^T W
     __syncthreads();
     for (int e = tid; e < m * m; e += nt) {  // V^T
       const int r = e / m, j = e % m;
@@ -410,7 +491,7 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
   } else {
     for (int e = tid; e < m * m; e += nt) {
       const int r = e / m, j = e % m;
-      X1[r * sb + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
+      X1[r * sp + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
       X2[r * sp + j] = (r == j) ? 1.f : 0.f;
     }
   }
@@ -418,14 +499,14 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
   for (int e = tid; e < m * m; e += nt) {  // symmetrise B
     const int r = e / m, j = e % m;
     if (r < j) {
-      const float v = 0.5f * (X1[r * sb + j] + X1[j * sb + r]);
-      X1[r * sb + j] = v;
-      X1[j * sb + r] = v;
+      const float v = 0.5f * (X1[r * sp + j] + X1[j * sp + r]);
+      X1[r * sp + j] = v;
+      X1[j * sp + r] = v;
     }
   }
   if (tid == 0) {
     float t = 0.f;
-    for (int w = 0; w < nt / 32; ++w) t += red[w];
+    for (int w = 0; w < nwarp; ++w) t += red[w];
     red[0] = sqrtf(t);
   }
   __syncthreads();
@@ -436,129 +517,156 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
   const float floor2 = floor_abs * floor_abs;
   float* B = X1;
   float* Vt = X2;
-  // this thread's B blocks (k, l), k <= l, row-major over the upper triangle
-  // (a warp reads consecutive columns of the same rows), and V^T units
-  // (pair k, float4 column c4)
-  const int nblk = npair * (npair + 1) / 2, nvec = npair * m4;
-  int kl[EIG2_PT], vu[EIG2_PT];
+  // This thread's row tasks (subproblem a, column quad cq; on V^T if v) and
+  // column task (subproblem b, row quad rq), fixed for the whole call; a
+  // quarter warp shares a and takes consecutive quads, resp. shares rq and
+  // takes eight subproblems.
+  const int nq = m / 4, nr1 = nsub * nq;
+  int rt[EJ_TPT];
 #pragma unroll
-  for (int i = 0; i < EIG2_PT; ++i) {
-    int b = tid + i * nt, k = 0;
-    if (b < nblk) {
-      while (b >= npair - k) {
-        b -= npair - k;
-        ++k;
-      }
-      kl[i] = k | ((k + b) << 16);
+  for (int i = 0; i < EJ_TPT; ++i) {
+    const int t1 = tid + i * nt;
+    if (t1 < 2 * nr1) {
+      const int v = t1 >= nr1, tt = v ? t1 - nr1 : t1;
+      rt[i] = (tt / nq) | (tt % nq) << 8 | v << 16;
     } else {
-      kl[i] = -1;
-    }
-    const int u = tid + i * nt;
-    vu[i] = u < nvec ? ((u / m4) | ((u % m4) << 16)) : -1;
-  }
-  // rotation count and largest ratio of the current and of the next sweep,
-  // per angle thread (tid < npair <= 66: at most three warps)
-  const int nw = (npair + 31) / 32;
-  unsigned c_cnt = 0, n_cnt = 0;
-  float c_mu = 0.f, n_mu = 0.f;
-  if (tid < npair) {
-    const float mu = set_rot(B, sb, m, 0, tid, tol2, floor2, pt);
-    if (mu >= 0.f) {
-      ++c_cnt;
-      c_mu = mu;
+      rt[i] = -1;
     }
   }
-  __syncthreads();
+  const int ctk = tid < nr1 ? (tid % nsub) | (tid / nsub) << 8 : -1;
+  unsigned cnt = 0;  // rotations and largest ratio of this lane's pair in the current sweep
+  float cmu = 0.f;
   int sweep = 0;
   bool converged = (s <= 1);
   for (; sweep < max_sweeps && !converged; ++sweep) {
-    for (int round = 0; round < m - 1; ++round) {
-      // (A) rotate the blocks and V^T rows of this round's rotating pairs
-#pragma unroll
-      for (int i = 0; i < EIG2_PT; ++i) {
-        if (kl[i] < 0) break;
-        const int k = kl[i] & 0xffff, l = kl[i] >> 16;
-        const PairRot rk = pt[k];
-        if (k == l) {
-          if (rk.sn == 0.f) continue;
-          const float a = B[rk.p * sb + rk.p], bq = B[rk.q * sb + rk.q], g = B[rk.p * sb + rk.q];
-          const float t = rk.sn / rk.c;
-          B[rk.p * sb + rk.p] = fmaf(-t, g, a);
-          B[rk.q * sb + rk.q] = fmaf(t, g, bq);
-          B[rk.p * sb + rk.q] = 0.f;
-          B[rk.q * sb + rk.p] = 0.f;
-        } else {
-          const PairRot rl = pt[l];
-          if (rk.sn == 0.f && rl.sn == 0.f) continue;
-          const float x00 = B[rk.p * sb + rl.p], x01 = B[rk.p * sb + rl.q];
-          const float x10 = B[rk.q * sb + rl.p], x11 = B[rk.q * sb + rl.q];
-          const float y00 = rk.c * x00 - rk.sn * x10, y01 = rk.c * x01 - rk.sn * x11;
-          const float y10 = rk.sn * x00 + rk.c * x10, y11 = rk.sn * x01 + rk.c * x11;
-          const float z00 = rl.c * y00 - rl.sn * y01, z01 = rl.sn * y00 + rl.c * y01;
-          const float z10 = rl.c * y10 - rl.sn * y11, z11 = rl.sn * y10 + rl.c * y11;
-          B[rk.p * sb + rl.p] = z00;
-          B[rk.p * sb + rl.q] = z01;
-          B[rk.q * sb + rl.p] = z10;
-          B[rk.q * sb + rl.q] = z11;
-          B[rl.p * sb + rk.p] = z00;
-          B[rl.q * sb + rk.p] = z01;
-          B[rl.p * sb + rk.q] = z10;
-          B[rl.q * sb + rk.q] = z11;
+    for (int r = 0; r < nb - 1; ++r) {
+      for (int sub = warp; sub < nsub; sub += nwarp) {
+        float* Sw = SC + sub * EJ_SUB;
+        float* Uw = Sw + 64;
+        int P, Q;
+        round_pair(nb, r, sub, P, Q);
+        if (lane == 0) pq[sub] = P | Q << 16;
+        for (int e = lane; e < 64; e += 32) {
+          const int i = e >> 3, j = e & 7;
+          const int gi = i < 4 ? 4 * P + i : 4 * Q + i - 4, gj = j < 4 ? 4 * P + j : 4 * Q + j - 4;
+          Sw[e] = B[gi * sp + gj];
+          Uw[e] = (i == j) ? 1.f : 0.f;
         }
+        __syncwarp();
+        if (r == 0) {
+          ej_round<true, 0>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+          ej_round<true, 1>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+          ej_round<true, 2>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+        }
+        ej_round<false, 0>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+        ej_round<false, 1>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+        ej_round<false, 2>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+        ej_round<false, 3>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
       }
-#pragma unroll
-      for (int i = 0; i < EIG2_PT; ++i) {
-        if (vu[i] < 0) break;
-        const PairRot rk = pt[vu[i] & 0xffff];
-        if (rk.sn == 0.f) continue;
-        float4* vp = (float4*)(Vt + rk.p * sp) + (vu[i] >> 16);
-        float4* vq = (float4*)(Vt + rk.q * sp) + (vu[i] >> 16);
-        const float4 x = *vp, y = *vq;
-        *vp = make_float4(rk.c * x.x - rk.sn * y.x, rk.c * x.y - rk.sn * y.y, rk.c * x.z - rk.sn * y.z,
-                          rk.c * x.w - rk.sn * y.w);
-        *vq = make_float4(rk.sn * x.x + rk.c * y.x, rk.sn * x.y + rk.c * y.y, rk.sn * x.z + rk.c * y.z,
-                          rk.sn * x.w + rk.c * y.w);
+      if (r == nb - 2 && warp < nsub) {  // this sweep's totals per warp
+        const unsigned cn = __reduce_add_sync(0xffffffffu, cnt);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(cmu));  // cmu >= 0
+        if (lane == 0) {
+          wrot[warp] = cn;
+          wmu[warp] = mx;
+        }
+        cnt = 0;
+        cmu = 0.f;
       }
       __syncthreads();
-      // (B) rotations of the next round (round 0 of the next sweep after the
-      // last round, counted for that sweep)
-      const bool last = (round == m - 2);
-      if (tid < npair) {
-        const float mu = set_rot(B, sb, m, last ? 0 : round + 1, tid, tol2, floor2, pt);
-        if (mu >= 0.f) {
-          if (last) {
-            ++n_cnt;
-            n_mu = fmaxf(n_mu, mu);
-          } else {
-            ++c_cnt;
-            c_mu = fmaxf(c_mu, mu);
+      // rows: B[S_a, quad] <- U_a^T B[S_a, quad] outside S_a's own columns,
+      // and V^T[S_a, quad] <- U_a^T V^T[S_a, quad]
+#pragma unroll
+      for (int i = 0; i < EJ_TPT; ++i) {
+        if (rt[i] < 0) break;
+        const int a = rt[i] & 0xff, cq = (rt[i] >> 8) & 0xff;
+        const bool isv = rt[i] >> 16;
+        const int P = pq[a] & 0xffff, Q = pq[a] >> 16;
+        if (!isv && (cq == P || cq == Q)) continue;
+        float* Mx = (isv ? Vt : B) + 4 * cq;
+        const float* Ua = SC + a * EJ_SUB + 64;
+        float acc[8][4];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const float4 x = *(const float4*)(Mx + (kk < 4 ? 4 * P + kk : 4 * Q + kk - 4) * sp);
+          const float4 ua = *(const float4*)(Ua + kk * 8), ub = *(const float4*)(Ua + kk * 8 + 4);
+          const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            acc[o][0] = fmaf(u[o], x.x, acc[o][0]);
+            acc[o][1] = fmaf(u[o], x.y, acc[o][1]);
+            acc[o][2] = fmaf(u[o], x.z, acc[o][2]);
+            acc[o][3] = fmaf(u[o], x.w, acc[o][3]);
+          }
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          *(float4*)(Mx + (o < 4 ? 4 * P + o : 4 * Q + o - 4) * sp) =
+              make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+      }
+      __syncthreads();
+      // columns: B[quad, S_b] <- B[quad, S_b] U_b; the subproblem's own
+      // superblock from its warp
+      if (ctk >= 0) {
+        const int b = ctk & 0xff, rq = ctk >> 8;
+        const int P = pq[b] & 0xffff, Q = pq[b] >> 16;
+        const float* Sb = SC + b * EJ_SUB;
+        float* row0 = B + 4 * rq * sp;
+        if (rq == P || rq == Q) {
+          const int l0 = rq == P ? 0 : 4;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            *(float4*)(row0 + i * sp + 4 * P) = *(const float4*)(Sb + (l0 + i) * 8);
+            *(float4*)(row0 + i * sp + 4 * Q) = *(const float4*)(Sb + (l0 + i) * 8 + 4);
+          }
+        } else {
+          float w[4][8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 w0 = *(const float4*)(row0 + i * sp + 4 * P), w1 = *(const float4*)(row0 + i * sp + 4 * Q);
+            w[i][0] = w0.x;
+            w[i][1] = w0.y;
+            w[i][2] = w0.z;
+            w[i][3] = w0.w;
+            w[i][4] = w1.x;
+            w[i][5] = w1.y;
+            w[i][6] = w1.z;
+            w[i][7] = w1.w;
+          }
+          const float* Ub = Sb + 64;
+          float o[4][8];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[i][j] = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const float4 ua = *(const float4*)(Ub + kk * 8), uc = *(const float4*)(Ub + kk * 8 + 4);
+            const float u[8] = {ua.x, ua.y, ua.z, ua.w, uc.x, uc.y, uc.z, uc.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) o[i][j] = fmaf(w[i][kk], u[j], o[i][j]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            *(float4*)(row0 + i * sp + 4 * P) = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+            *(float4*)(row0 + i * sp + 4 * Q) = make_float4(o[i][4], o[i][5], o[i][6], o[i][7]);
           }
         }
       }
-      if (last && tid < 32 * nw) {  // whole warps: this sweep's totals per warp
-        const unsigned cn = __reduce_add_sync(0xffffffffu, c_cnt);
-        const unsigned mx = __reduce_max_sync(0xffffffffu, (unsigned)__float_as_int(c_mu));  // mu >= 0
-        if ((tid & 31) == 0) {
-          wrot[tid >> 5] = cn;
-          wmu[tid >> 5] = mx;
-        }
-        c_cnt = n_cnt;
-        c_mu = n_mu;
-        n_cnt = 0;
-        n_mu = 0.f;
-      }
       __syncthreads();
     }
-    // cyclic Jacobi converges quadratically: after a sweep whose largest
-    // rotated ratio was below sqrt(tol), the next would rotate nothing above tol
     unsigned cn = 0, mx = 0;
-    for (int w = 0; w < nw; ++w) {
+    for (int w = 0; w < min(nsub, nwarp); ++w) {
       cn += wrot[w];
       mx = max(mx, wmu[w]);
     }
-    converged = (cn == 0) || (__int_as_float((int)mx) < tol);
+    converged = (cn == 0) || (__uint_as_float(mx) < tol);
   }
-  for (int j = tid; j < s; j += nt) Phi[j] = B[j * sb + j];
+  for (int j = tid; j < s; j += nt) Phi[j] = B[j * sp + j];
   for (int e = tid; e < s * s; e += nt) {
     const int r = e / s, j = e % s;
     Cio[e] = Vt[j * sp + r];
@@ -572,10 +680,11 @@ __global__ void __launch_bounds__(1024) k_eig2(const float* __restrict__ G, floa
   }
 }
 
-size_t eig2_smem(int s) {
-  const int m = (s + 3) & ~3, sp = m + 4, npair = m / 2;
-  return (size_t)3 * m * sp * sizeof(float) + (size_t)npair * sizeof(PairRot);
+size_t eig3_smem(int s) {
+  const int m = (s + 7) & ~7, sp = m + 4;
+  return (size_t)(3 * m * sp + (m / 8) * EJ_SUB) * sizeof(float);
 }
+
 
 struct EigCfg {
   int a_smem, v_smem;
@@ -593,18 +702,17 @@ EigCfg eig_cfg(int s, int elem) {
 template <typename T>
 void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, double tmin, int* status, int* used,
          cudaStream_t st) {
-  if (sizeof(T) == 4 && s <= EIG2_MAX) {
-    const int m = (s + 3) & ~3, npair = m / 2;
-    const int nblk = npair * (npair + 1) / 2, nvec = npair * (m / 4);
-    int threads = ((std::max(nblk, nvec) + 31) / 32) * 32;
-    threads = std::min(1024, std::max(64, threads));
-    const size_t bytes = eig2_smem(s);
-    static bool attr2 = false;
-    if (!attr2) {
-      cudaFuncSetAttribute(k_eig2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig2_smem(EIG2_MAX));
-      attr2 = true;
+  if (sizeof(T) == 4 && s <= EIG3_MAX) {
+    const int m = (s + 7) & ~7, nsub = m / 8;
+    // one warp per subproblem; one thread per row task up to EJ_NT
+    const int threads = std::min(EJ_NT, std::max({64, 32 * nsub, ((m * m / 16 + 31) / 32) * 32}));
+    const size_t bytes = eig3_smem(s);
+    static bool attr3 = false;
+    if (!attr3) {
+      cudaFuncSetAttribute(k_eig3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig3_smem(EIG3_MAX));
+      attr3 = true;
     }
-    k_eig2<<<1, threads, bytes, st>>>((const float*)G, (float*)C, (float*)Phi, s, warm, max_sweeps, tmin, status,
+    k_eig3<<<1, threads, bytes, st>>>((const float*)G, (float*)C, (float*)Phi, s, warm, max_sweeps, tmin, status,
                                        used);
     return;
   }
