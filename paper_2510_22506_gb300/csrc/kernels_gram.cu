@@ -8,8 +8,12 @@
 //           merged tensor of the factor updated last, kept from its update)
 //           fused with the masked proximal update of Eq. 10 and the
 //           stop-test reductions.
+#include <cooperative_groups.h>
+
 #include "fctn_internal.cuh"
 #include "fctn_tile.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -122,18 +126,38 @@ unsigned rgrid(int64_t n) {
 
 
 // ---- Gram of M_k from the Grams of its pair operands (FactGram) -------------
-// H = F F^T, F[r][j] = Src[col[j] + roff[r]] (r < rows, j < J): one 64 x 64
-// tile of H per CTA over all j, in chunks of 32 columns gathered into shared
-// memory; the next chunk's gathers are in flight while the current one is
-// consumed.  Fixed summation order.
+// H = F F^T, F[r][j] = Src[col[j] + roff[r]] (r < rows, j < J), for both
+// operands in one launch: one cluster of OG_SPLIT CTAs per 64 x 64 tile of H
+// (the tiles of HL, then those of HR).  CTA q of a cluster sums its share of
+// the columns j in chunks of 32 gathered into shared memory (the next chunk's
+// gathers in flight while the current one is consumed); the cluster then adds
+// the OG_SPLIT partial tiles through distributed shared memory, CTA q
+// reducing rows 8q..8q+7 of the tile in rank order (a fixed summation order).
+constexpr int OG_SPLIT = 8;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_op_gram(const T* __restrict__ Src, const int* __restrict__ roff,
-                                                 const int* __restrict__ col, int rows, int J, T* __restrict__ H) {
+__global__ void __cluster_dims__(OG_SPLIT, 1, 1) __launch_bounds__(256)
+    k_op_gram(const T* __restrict__ SrcL, const int* __restrict__ roffL, const int* __restrict__ colL, int rowsL,
+              int JL, T* __restrict__ HL, const T* __restrict__ SrcR, const int* __restrict__ roffR,
+              const int* __restrict__ colR, int rowsR, int JR, T* __restrict__ HR) {
   constexpr int BJ = 32;
-  __shared__ __align__(16) T Fa[BJ][64];
-  __shared__ __align__(16) T Fb[BJ][64];
+  __shared__ __align__(16) T Fs[2 * BJ * 64];  // the two gathered chunks, then the partial tile
+  T* Fa = Fs;
+  T* Fb = Fs + BJ * 64;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank();
+  const int tile = blockIdx.x / OG_SPLIT;
+  const int txL = (rowsL + 63) / 64, ntL = txL * txL;
+  const bool isL = tile < ntL;
+  const T* Src = isL ? SrcL : SrcR;
+  const int* roff = isL ? roffL : roffR;
+  const int* col = isL ? colL : colR;
+  const int rows = isL ? rowsL : rowsR, J = isL ? JL : JR;
+  T* H = isL ? HL : HR;
+  const int tx_ = (rows + 63) / 64, t = isL ? tile : tile - ntL;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  const int r0 = (t / tx_) * 64, c0 = (t % tx_) * 64;
+  const int per = (J + OG_SPLIT - 1) / OG_SPLIT, jb = min(J, q * per), je = min(J, jb + per);
   const int rr = tid % 64, jq = tid / 64;  // gathers rows r0 + rr and c0 + rr at columns j0 + jq + 4u
   const int oa = r0 + rr < rows ? roff[r0 + rr] : -1;
   const int ob = c0 + rr < rows ? roff[c0 + rr] : -1;
@@ -142,7 +166,7 @@ __global__ void __launch_bounds__(256) k_op_gram(const T* __restrict__ Src, cons
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int j = j0 + jq + 4 * u;
-      const int o = j < J ? col[j] : -1;
+      const int o = j < je ? col[j] : -1;
       va[u] = (o >= 0 && oa >= 0) ? Src[(int64_t)o + oa] : (T)0;
       vb[u] = (o >= 0 && ob >= 0) ? Src[(int64_t)o + ob] : (T)0;
     }
@@ -152,23 +176,23 @@ __global__ void __launch_bounds__(256) k_op_gram(const T* __restrict__ Src, cons
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-  gather(0);
-  for (int j0 = 0; j0 < J; j0 += BJ) {
+  if (jb < je) gather(jb);
+  for (int j0 = jb; j0 < je; j0 += BJ) {
     __syncthreads();  // the previous chunk is consumed
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      Fa[jq + 4 * u][rr] = va[u];
-      Fb[jq + 4 * u][rr] = vb[u];
+      Fa[(jq + 4 * u) * 64 + rr] = va[u];
+      Fb[(jq + 4 * u) * 64 + rr] = vb[u];
     }
     __syncthreads();
-    if (j0 + BJ < J) gather(j0 + BJ);
-    const int nb = min(BJ, J - j0);
+    if (j0 + BJ < je) gather(j0 + BJ);
+    const int nb = min(BJ, je - j0);
     for (int jj = 0; jj < nb; ++jj) {
       T av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        av[a] = Fa[jj][ty * 4 + a];
-        bv[a] = Fb[jj][tx * 4 + a];
+        av[a] = Fa[jj * 64 + ty * 4 + a];
+        bv[a] = Fb[jj * 64 + tx * 4 + a];
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -176,16 +200,20 @@ __global__ void __launch_bounds__(256) k_op_gram(const T* __restrict__ Src, cons
         for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
   }
+  __syncthreads();  // the last chunk is consumed: Fs takes the partial tile
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int r = r0 + ty * 4 + a;
-    if (r >= rows) continue;
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = c0 + tx * 4 + b;
-      if (c < rows) H[(int64_t)r * rows + c] = acc[a][b];
-    }
+    for (int b = 0; b < 4; ++b) Fs[(ty * 4 + a) * 64 + tx * 4 + b] = acc[a][b];
+  cluster.sync();
+  for (int e = tid; e < 8 * 64; e += blockDim.x) {
+    const int rl = 8 * q + e / 64, c = e % 64;
+    T v = 0;
+    for (int rk = 0; rk < OG_SPLIT; ++rk) v += cluster.map_shared_rank(Fs, rk)[rl * 64 + c];
+    const int r = r0 + rl, cc = c0 + c;
+    if (r < rows && cc < rows) H[(int64_t)r * rows + cc] = v;
   }
+  cluster.sync();  // every partial tile stays in place until the cluster has read it
 }
 
 // G[sigma, sigma'] = sum_{kappa, kappa'} HL[a K + kappa, a' K + kappa'] HR[b K + kappa, b' K + kappa']
@@ -216,9 +244,9 @@ void fact_gram(const FactGram& f, const T* L, const T* R, T* HL, T* HR, int s, d
   const int* b_of = a_of + s;
   const int* colL = b_of + s;
   const int* colR = colL + f.JL;
-  dim3 gl((f.rl + 63) / 64, (f.rl + 63) / 64), gr((f.rr + 63) / 64, (f.rr + 63) / 64);
-  k_op_gram<T><<<gl, 256, 0, st>>>(L, offL, colL, f.rl, f.JL, HL);
-  k_op_gram<T><<<gr, 256, 0, st>>>(R, offR, colR, f.rr, f.JR, HR);
+  const int tl = (f.rl + 63) / 64, tr = (f.rr + 63) / 64;
+  k_op_gram<T><<<(tl * tl + tr * tr) * OG_SPLIT, 256, 0, st>>>(L, offL, colL, f.rl, f.JL, HL, R, offR, colR, f.rr,
+                                                                f.JR, HR);
   k_gram_combine<T><<<rgrid((int64_t)s * s), 256, 0, st>>>(HL, HR, a_of, b_of, s, f.K, f.rl, f.rr, Gd, Gs);
 }
 
