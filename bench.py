@@ -170,6 +170,13 @@ def run_ours(args):
     initd = [torch.from_numpy(np.ascontiguousarray(a.astype(dt))).to(dev) for a in init]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     torch.cuda.synchronize()
+    # launch shape of the Gram / right-hand-side kernel from libfctn's
+    # autotuner (probe handles on the same inputs, before the timed region)
+    tune = None
+    if not args.no_tune:
+        best, tms = F.fctn_autotune(p, Yd, Md, initd, sweeps=3, stream=stream)
+        p.rhs_ctas = best
+        tune = {"rhs_ctas": best, "sweep_ms": {str(c): round(v, 4) for c, v in tms.items()}}
     h = F.fctn_create(p, stream)
     try:
         F.fctn_set_data(h, Yd, Md)
@@ -282,7 +289,8 @@ def run_ours(args):
         "config": {"workload": f"{name}: {DESC[name]}", "dims": list(w["dims"]), "rank": w["r"], "sampling": w["p"],
                    "precision": precision, "reuse": True, "order_policy": "alternate", "lambda": synth.LAMBDA,
                    "delta": synth.DELTA, "rho": synth.RHO, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{ws}", "graphs": True},
+                   "parallelism": f"replicas x{ws}", "graphs": True,
+                   "autotune": tune if tune else "off (built-in launch shape)"},
         "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
         "rel_change_last": st["rel_change"], "eig_sweeps_last": st["eig_sweeps"],
         "gpu_launches": int(launches),
@@ -297,9 +305,9 @@ def run_ours(args):
                 "step": f"set_data + set_factors from host, {e2e_sweeps} sweeps, X back to host"},
     }
     if ws == 1 and not args.no_extras:
-        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps)
+        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps, tune=not args.no_tune)
         line["rank_growth"] = rank_growth_run(F, name, truth, Y, mask, init, R)
-        line["serving"] = serving_mix(args.serve_jobs)
+        line["serving"] = serving_mix(args.serve_jobs, tune=not args.no_tune)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -307,7 +315,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100):
+def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100, tune=True):
     """Sweeps/s of the same workload in every precision (graphs, L2 flushed
     between sweeps), and PSNR / SSIM against the truth (Sec. 4, computed by
     libfctn) after `quality_sweeps` sweeps from the same start."""
@@ -315,13 +323,19 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100)
     out, quality = {}, {}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     truth32 = np.ascontiguousarray(truth.astype(np.float32))
+    Y32, M8 = np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8)
+    init32 = [np.ascontiguousarray(a.astype(np.float32)) for a in init]
+    tuned = {}
     for prec in ("fp32", "tf32", "bf16"):
         p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=prec)
         st = torch.cuda.Stream()
+        if tune:
+            p.rhs_ctas, _ = F.fctn_autotune(p, Y32, M8, init32, sweeps=3, stream=st)
+            tuned[prec] = p.rhs_ctas
         h = F.fctn_create(p, st)
         try:
-            F.fctn_set_data(h, np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8))
-            F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(np.float32)) for a in init])
+            F.fctn_set_data(h, Y32, M8)
+            F.fctn_set_factors(h, init32)
             tot = 0.0
             with torch.cuda.stream(st):
                 for i in range(steps + 3):
@@ -339,7 +353,7 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100)
             quality[prec] = {"psnr_db": ps, "ssim": ss}
         finally:
             F.fctn_destroy(h)
-    return {"unit": UNIT, "sweeps_per_s": out, "workload": name,
+    return {"unit": UNIT, "sweeps_per_s": out, "workload": name, "rhs_ctas_autotuned": tuned or "off",
             "quality_after_sweeps": max(quality_sweeps, steps + 3), "quality": quality}
 
 
@@ -382,19 +396,24 @@ def rank_growth_run(F, name, truth, Y, mask, init, R, grow_every=5, tol=1e-4, ma
     return out
 
 
-def serving_mix(n_jobs):
+def serving_mix(n_jobs, tune=True):
     """Serving mix (Poisson 20 jobs/s; shapes 64x64x16, 128x128x31, 144x176x3x20,
     256x256x31; ranks {3,4,6}; SR {0.05,0.1,0.2}; to rel < 1e-4, cap 500):
     served concurrently in TF32 vs the same jobs one by one in plain FP32."""
     from paper_2510_22506_gb300 import serve as S
     jobs = S.mix_jobs(n_jobs, seed=5000, rate=20.0)
-    served = S.run_mix(jobs, precision="tf32", tol=1e-4, max_sweeps=500, max_jobs=32)
+    # launch shapes of every job class from the autotuner, before traffic
+    # (a server's stored tuning cache), outside the timed mix
+    tuner = S.TuneCache().fill(jobs, "tf32") if tune else None
+    served = S.run_mix(jobs, precision="tf32", tol=1e-4, max_sweeps=500, max_jobs=32, tuner=tuner)
     seq = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500)
     keys = ("jobs", "failed", "wall_s", "jobs_per_s", "sweeps", "sweeps_per_s", "latency_p50_s", "latency_p99_s",
             "ttt_p50_s", "ttt_p99_s")
     return {"served_tf32": {k: served.get(k) for k in keys},
             "sequential_fp32": {k: seq.get(k) for k in keys if k in seq},
-            "jobs_per_s_ratio": served["jobs_per_s"] / seq["jobs_per_s"]}
+            "jobs_per_s_ratio": served["jobs_per_s"] / seq["jobs_per_s"],
+            "autotune": ({"classes": len(tuner.table), "tune_s": round(tuner.tune_s, 3),
+                          "rhs_ctas": sorted(set(tuner.table.values()))} if tuner else "off")}
 
 
 def oracle_setup(name):
@@ -458,6 +477,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision and serving comparisons")
+    ap.add_argument("--no-tune", action="store_true", help="built-in launch shape instead of the autotuner's")
     ap.add_argument("--serve-jobs", type=int, default=48)
     args = ap.parse_args()
     if args.warmup < 3:

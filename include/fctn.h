@@ -109,6 +109,9 @@ typedef struct fctn_params {
   double extrap_alpha;  /* asymmetric extrapolation (Sec. 4.3): after each factor update */
   double extrap_beta;   /* A <- A + alpha (A - beta A^(t)); alpha = 0 turns it off       */
   int32_t gram_mode;    /* FCTN_GRAM_*: how the Gram M_k M_k^T of Eq. 5 is formed        */
+  int32_t rhs_ctas;     /* launch shape of the Gram / right-hand-side kernel: about this
+                           many CTAs per factor update, the columns of M_k split among
+                           them; 0 = built-in rule (see fctn_autotune), <= 2432        */
 } fctn_params;
 
 typedef struct fctn_stats {
@@ -185,6 +188,24 @@ int fctn_grow_ranks(fctn_handle* h, const int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX
  * otherwise), on the host or device per `where`; it is not kept.  Writes
  * *psnr and *ssim (either may be NULL) and synchronises the stream. */
 int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, double* ssim);
+
+/* Autotuner of the launch shape (fctn_params.rhs_ctas).  For each candidate
+ * value it creates a probe handle with *p and that rhs_ctas on cuda_stream,
+ * copies in Y, mask and factors (as fctn_set_data / fctn_set_factors, host
+ * or device per `where`), runs one untimed sweep (graph capture, warm
+ * starts) and times `sweeps` sweeps with CUDA events; then destroys the
+ * probe.  *best gets the fastest candidate; ms_out[i] (may be NULL) the mean
+ * sweep time of candidate i in milliseconds.  cand = NULL takes the built-in
+ * candidates {96, 152, 228, 304} (ncand is then ignored; ms_out needs 4
+ * entries).  No existing handle changes.  Handles created with different
+ * rhs_ctas give results that agree within rounding (the split changes the
+ * summation order of the Gram and right-hand side).  Needs the device
+ * memory of one more handle with *p (fctn_footprint_bytes); synchronises
+ * cuda_stream.  Errors: FCTN_E_ARG (NULL pointers, sweeps outside [1, 1000],
+ * ncand outside [1, 64], a candidate outside [0, 2432]); any error of the
+ * probe's create / set / sweep calls. */
+int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors, int where,
+                  const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best, double* ms_out);
 
 /* Copy factor k (FCTN shape) / the completed tensor X out. */
 int fctn_get_factor(fctn_handle* h, int k, void* out, int where);

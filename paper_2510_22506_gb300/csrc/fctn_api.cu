@@ -634,10 +634,10 @@ GramPlan gram_plan(const fctn_handle* h, int k) {
   g.tiles_c = (int)((g.ncols + 63) / 64);
   int64_t ctas_per_split = g.tiles_r * g.tiles_c;
   if (h->tc) ctas_per_split = h->tp[k].n_groups > 0 ? h->tp[k].n_groups : 1;
-  // CTAs of the right-hand-side kernel: about 2 per SM; with the factored
-  // Gram (whose eigensolver runs beside it on the side branch) at most 144,
-  // so that SMs stay free for that branch
-  const int64_t ctas = h->fg[k].use ? 96 : 2 * 152;
+  // CTAs of the right-hand-side kernel: the tuned budget, else about 2 per
+  // SM, or 96 with the factored Gram (whose eigensolver runs beside it on
+  // the side branch), so that SMs stay free for that branch
+  const int64_t ctas = h->p.rhs_ctas > 0 ? h->p.rhs_ctas : (h->fg[k].use ? 96 : 2 * 152);
   int64_t target = (ctas + ctas_per_split - 1) / ctas_per_split;
   // tensor-core path: at least two 32-column chunks per CTA, so the per-split
   // partial (s x (s + I) floats) stays small against the columns it consumes
@@ -662,6 +662,7 @@ int check_params(const fctn_params* p) {
   if (p->gram_mode < FCTN_GRAM_AUTO || p->gram_mode > FCTN_GRAM_FACTORED)
     return fail(FCTN_E_ARG, "unknown gram mode %d", p->gram_mode);
   if (p->refine_steps < 0 || p->refine_steps > 8) return fail(FCTN_E_ARG, "refine_steps %d outside [0, 8]", p->refine_steps);
+  if (p->rhs_ctas < 0 || p->rhs_ctas > 16 * 152) return fail(FCTN_E_ARG, "rhs_ctas %d outside [0, 2432]", p->rhs_ctas);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
@@ -1508,6 +1509,60 @@ int fctn_grow_ranks(fctn_handle* h, const int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX
   std::swap(h->own_stream, h2->own_stream);
   h->launches += h2->launches;
   return fctn_destroy(h2);
+}
+
+int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors, int where,
+                  const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best, double* ms_out) {
+  static const int32_t builtin[4] = {96, 152, 228, 304};
+  if (!p || !Y || !mask || !factors || !best) return fail(FCTN_E_ARG, "NULL argument");
+  if (sweeps < 1 || sweeps > 1000) return fail(FCTN_E_ARG, "sweeps %d outside [1, 1000]", sweeps);
+  if (!cand) {
+    cand = builtin;
+    ncand = 4;
+  }
+  if (ncand < 1 || ncand > 64) return fail(FCTN_E_ARG, "ncand %d outside [1, 64]", ncand);
+  for (int i = 0; i < ncand; ++i)
+    if (cand[i] < 0 || cand[i] > 16 * 152) return fail(FCTN_E_ARG, "candidate %d outside [0, 2432]", cand[i]);
+  int rc = check_params(p);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(FCTN_E_CUDA, "fctn_autotune: cudaEventCreate failed");
+  }
+  double best_ms = 0.0;
+  for (int i = 0; i < ncand && rc == FCTN_OK; ++i) {
+    fctn_params q = *p;
+    q.rhs_ctas = cand[i];
+    fctn_handle* h = nullptr;
+    if ((rc = fctn_create(&q, cuda_stream, &h))) break;
+    fctn_stats st{};
+    float ms = 0.f;
+    if (!(rc = fctn_set_data(h, Y, mask, where)) && !(rc = fctn_set_factors(h, factors, where)) &&
+        !(rc = fctn_pam_sweep(h, 1, nullptr))) {
+      cudaError_t ce = cudaEventRecord(e0, h->st);
+      if (ce == cudaSuccess) rc = fctn_pam_sweep(h, sweeps, nullptr);
+      if (ce == cudaSuccess && !rc) ce = cudaEventRecord(e1, h->st);
+      if (ce == cudaSuccess && !rc) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess && !rc) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) rc = fail(FCTN_E_CUDA, "fctn_autotune: %s", cudaGetErrorString(ce));
+      if (!rc && !(rc = fctn_pam_sweep(h, 0, &st)) && st.status != FCTN_OK)
+        rc = fail(st.status, "fctn_autotune: probe sweep failed with status %d", st.status);
+    }
+    const int drc = fctn_destroy(h);
+    if (!rc) rc = drc;
+    if (rc) break;
+    const double per = (double)ms / sweeps;
+    if (ms_out) ms_out[i] = per;
+    if (i == 0 || per < best_ms) {
+      best_ms = per;
+      *best = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, double* ssim) {

@@ -45,6 +45,7 @@ class fctn_params(ctypes.Structure):
         ("extrap_alpha", ctypes.c_double),
         ("extrap_beta", ctypes.c_double),
         ("gram_mode", ctypes.c_int32),
+        ("rhs_ctas", ctypes.c_int32),
     ]
 
 
@@ -99,7 +100,7 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
-            "fctn_server_finished", "fctn_quality", "fctn_grow_ranks")
+            "fctn_server_finished", "fctn_quality", "fctn_grow_ranks", "fctn_autotune")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6}
 
 
@@ -155,7 +156,7 @@ def fctn_version():
 
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
-                laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto"):
+                laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -180,6 +181,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     if extrapolation is not None:
         p.extrap_alpha, p.extrap_beta = float(extrapolation[0]), float(extrapolation[1])
     p.gram_mode = {"auto": 0, "direct": 1, "factored": 2}[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
+    p.rhs_ctas = int(rhs_ctas)
     return p
 
 
@@ -281,6 +283,38 @@ def fctn_grow_ranks(h, R, scale, seed):
         for b in range(a + 1, N):
             r[a][b] = int(R[a][b])
     _check(lib.fctn_grow_ranks(h, ctypes.byref(r), float(scale), ctypes.c_uint64(int(seed) & (2 ** 64 - 1))))
+
+
+TUNE_CANDIDATES = (96, 152, 228, 304)
+
+
+def fctn_autotune(params, Y, mask, factors, candidates=None, sweeps=3, stream=None):
+    """Fastest rhs_ctas for these parameters and inputs (libfctn's autotuner).
+
+    Returns (best, {candidate: mean sweep ms}).  ``candidates`` None takes the
+    library's built-in list.  Y, mask and factors as for fctn_set_data /
+    fctn_set_factors, all on the host or all on the device."""
+    py, wy = _ptr(Y)
+    pm, wm = _ptr(mask)
+    ptrs, where = [], wy
+    for a in factors:
+        pa, wa = _ptr(a)
+        ptrs.append(pa)
+        if wa != wy:
+            raise ValueError("Y, mask and factors must all be on the host or all on the device")
+    if wm != wy:
+        raise ValueError("Y, mask and factors must all be on the host or all on the device")
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    cand = list(TUNE_CANDIDATES if candidates is None else candidates)
+    carr = (ctypes.c_int32 * len(cand))(*[int(c) for c in cand])
+    ms = (ctypes.c_double * len(cand))()
+    best = ctypes.c_int32(0)
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.fctn_autotune(ctypes.byref(params), py, pm, arr, where, carr if candidates is not None else None,
+                             len(cand), int(sweeps), sp, ctypes.byref(best), ms))
+    return best.value, {c: ms[i] for i, c in enumerate(cand)}
 
 
 def fctn_quality(h, truth):

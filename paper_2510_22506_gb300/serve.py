@@ -56,9 +56,45 @@ def mix_jobs(n_jobs, seed=5000, rate=20.0, shapes=MIX_SHAPES, contract=None):
     return jobs
 
 
-def job_params(job, precision):
-    return F.make_params(job["dims"], job["R"], lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO,
-                         precision=precision, reuse=True, order_policy="alternate")
+def job_params(job, precision, tuner=None):
+    p = F.make_params(job["dims"], job["R"], lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO,
+                      precision=precision, reuse=True, order_policy="alternate")
+    if tuner is not None:
+        p.rhs_ctas = tuner.get(job, p)
+    return p
+
+
+class TuneCache:
+    """Launch shapes (fctn_params.rhs_ctas) per job class (dims, ranks,
+    precision), chosen by libfctn's autotuner on the first job of the class
+    and reused for the rest; `fill` tunes every class of a job list up front,
+    as a server would load a stored cache before taking traffic."""
+
+    def __init__(self, sweeps=3, candidates=None):
+        self.sweeps, self.candidates, self.table, self.tune_s = sweeps, candidates, {}, 0.0
+
+    @staticmethod
+    def key(job, p):
+        N = len(job["dims"])
+        return (tuple(job["dims"]), tuple(int(job["R"][a][b]) for a in range(N) for b in range(a + 1, N)),
+                int(p.precision))
+
+    def get(self, job, p):
+        k = self.key(job, p)
+        if k not in self.table:
+            dt = F.elem_dtype(p)
+            t0 = time.perf_counter()
+            best, _ = F.fctn_autotune(p, np.ascontiguousarray(job["Y"].astype(dt)), job["mask"].astype(np.uint8),
+                                      [np.ascontiguousarray(a.astype(dt)) for a in job["init"]],
+                                      candidates=self.candidates, sweeps=self.sweeps)
+            self.tune_s += time.perf_counter() - t0
+            self.table[k] = best
+        return self.table[k]
+
+    def fill(self, jobs, precision):
+        for j in jobs:
+            job_params(j, precision, self)
+        return self
 
 
 def _pct(xs, q):
@@ -66,8 +102,9 @@ def _pct(xs, q):
 
 
 def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_budget_bytes=0,
-            keep_results=False, poll_sleep=2e-5, arrivals=True):
-    """Submit jobs at their arrival times, step the server until all finish."""
+            keep_results=False, poll_sleep=2e-5, arrivals=True, tuner=None):
+    """Submit jobs at their arrival times, step the server until all finish;
+    `tuner` (a TuneCache) supplies each job's launch shape."""
     srv = F.fctn_server_create(max_jobs=max_jobs, mem_budget_bytes=mem_budget_bytes)
     pending = sorted(jobs, key=lambda j: j["arrival"]) if arrivals else list(jobs)
     ids, t_arr, results, infos = {}, {}, {}, {}
@@ -78,7 +115,7 @@ def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_b
             now = time.perf_counter() - t0
             while nxt < len(pending) and (not arrivals or pending[nxt]["arrival"] <= now):
                 j = pending[nxt]
-                p = job_params(j, precision)
+                p = job_params(j, precision, tuner)
                 dt = F.elem_dtype(p)
                 jid = F.fctn_server_submit(srv, p, j["Y"].astype(dt), j["mask"], [a.astype(dt) for a in j["init"]],
                                            tol, max_sweeps)

@@ -61,6 +61,8 @@ def test_footprint_scales_with_size(F):
     dict(precision=9),
     dict(order_policy=5),
     dict(refine_steps=99),
+    dict(rhs_ctas=-1),
+    dict(rhs_ctas=5000),
 ])
 def test_invalid_params_rejected(F, bad):
     dims = bad.pop("dims", (30, 30, 10))
@@ -79,3 +81,13 @@ def test_reuse_beyond_order_four_is_planned(F):
     on = F.fctn_footprint_bytes(_params(F, (6, 5, 4, 5, 4), r=2, reuse=True))
     off = F.fctn_footprint_bytes(_params(F, (6, 5, 4, 5, 4), r=2, reuse=False))
     assert on > 0 and off > 0
+
+
+def test_rhs_ctas_sets_the_split(F):
+    """A larger right-hand-side CTA budget splits M_k's columns more finely:
+    more per-split partials, so a larger footprint; 0 is the built-in rule."""
+    small = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32", rhs_ctas=16))
+    rule = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32"))
+    large = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32", rhs_ctas=2432))
+    assert small < large
+    assert small <= rule <= large

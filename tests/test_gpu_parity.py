@@ -171,6 +171,23 @@ def test_fp32_factored_and_direct_gram(F):
             assert rel(a, b) <= 1e-4, (mode, k, rel(a, b))
 
 
+def test_fp32_autotuned_launch_shape(F):
+    """The autotuner times its candidates and returns one of them; every
+    launch shape of the right-hand-side kernel keeps parity with the oracle."""
+    d = inputs(None, dims=(48, 40, 9), r=4, p=0.2, idx=44, noise=0.0, cap=None, dtype=np.float32)
+    p = F.make_params(d["dims"], d["R"], precision="fp32")
+    best, ms = F.fctn_autotune(p, d["Y"], d["mask"].astype(np.uint8), d["init"], candidates=(8, 96, 600), sweeps=2)
+    assert best in (8, 96, 600)
+    assert all(v > 0 for v in ms.values()), ms
+    assert ms[best] == min(ms.values())
+    st, _ = oracle_run(d, 10)
+    for c in (8, 600):
+        g = gpu_run(F, d, 10, precision="fp32", rhs_ctas=c)
+        assert rel(g["X"], st.X) <= 1e-4, (c, rel(g["X"], st.X))
+        for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+            assert rel(a, b) <= 1e-4, (c, k, rel(a, b))
+
+
 # ---- FP32 path ------------------------------------------------------------
 def test_fp32_small_matches_oracle(F):
     d = inputs(None, dims=(48, 40, 9), r=4, p=0.2, idx=44, noise=0.0, cap=None, dtype=np.float32)
