@@ -336,6 +336,72 @@ __device__ __forceinline__ void sm_mm(float* __restrict__ out, int so, const flo
   }
 }
 
+// dst[r][j] (stride sd) <- src[r s + j] for r, j < m, zero outside s x s;
+// warp w takes rows w, w + warps, ... (at most 8: the eigensolver launches at
+// least m / 8 warps) and lane l columns l, l + 32, ... (m <= 128), with all of
+// a thread's loads (two batches of 16) in flight before its stores.  Returns the thread's sum of
+// squares of what it loaded.
+__device__ __forceinline__ float ej_load(float* __restrict__ dst, int sd, const float* __restrict__ src, int s,
+                                         int m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  float ss = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // two batches of 16 loads
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int r = warp + (h * 4 + (u >> 2)) * nwarp, j = lane + (u & 3) * 32;
+      v[u] = (r < s && j < s) ? src[r * s + j] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int r = warp + (h * 4 + (u >> 2)) * nwarp, j = lane + (u & 3) * 32;
+      if (r < m && j < m) dst[r * sd + j] = v[u];
+      ss = fmaf(v[u], v[u], ss);
+    }
+  }
+  return ss;
+}
+
+// out = X^T Y for a product known to be symmetric (m % 4 == 0, layouts as
+// sm_mm<true>): only the 4 x 4 tiles on and above the diagonal are formed,
+// and each is written to both triangles, so out is exactly symmetric.
+__device__ __forceinline__ void sm_mm_sym(float* __restrict__ out, int so, const float* __restrict__ X, int sx,
+                                          const float* __restrict__ Y, int sy, int m) {
+  const int mq = m / 4, ntile = mq * (mq + 1) / 2;
+  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+    int ti = 0, b = t;
+    while (b >= mq - ti) {
+      b -= mq - ti;
+      ++ti;
+    }
+    const int i0 = ti * 4, j0 = (ti + b) * 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < m; ++k) {
+      const float4 xv = *(const float4*)(X + k * sx + i0);
+      const float4 yv = *(const float4*)(Y + k * sy + j0);
+      const float x[4] = {xv.x, xv.y, xv.z, xv.w}, y[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(x[a], y[c], acc[a][c]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (b != 0 || a <= c) {
+          out[(i0 + a) * so + j0 + c] = acc[a][c];
+          out[(j0 + c) * so + i0 + a] = acc[a][c];
+        }
+  }
+}
+
 // Block-ordered two-sided Jacobi (FP32, s <= EIG3_MAX), one CTA: cyclic
 // Jacobi sweeps whose pairs are ordered so that one parallel step
 // touches only the index sets of disjoint 8 x 8 subproblems.  The m indices
@@ -460,49 +526,38 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
   __shared__ float red[32];
   __shared__ unsigned wrot[32], wmu[32];  // per warp: rotations and largest ratio of a sweep
   __shared__ int pq[16];                  // per subproblem: blocks P | Q << 16
-  float fr = 0.f;
-  for (int e = tid; e < s * s; e += nt) fr = fmaf(G[e], G[e], fr);
-  fr = warp_sum(fr);
-  if (lane == 0) red[warp] = fr;
-  // B in X1, V^T in X2 (both stride sp)
+  // B in X1, V^T in X2 (both stride sp); element loops run a warp per row
+  // and a lane per column
   if (warm) {
-    for (int e = tid; e < m * m; e += nt) {  // X1 <- V0 (row r, column j), zero padded
-      const int r = e / m, j = e % m;
-      X1[r * sp + j] = (r < s && j < s) ? Cio[r * s + j] : 0.f;
-    }
+    ej_load(X1, sp, Cio, s, m);  // X1 <- V0 (row r, column j)
     __syncthreads();
-    sm_mm<true>(X2, sp, X1, sp, X1, sp, m, 1.f, nullptr, 0, 0.f);  // S = V0^T V0
+    sm_mm_sym(X2, sp, X1, sp, X1, sp, m);  // S = V0^T V0
     __syncthreads();
     sm_mm<false>(X3, sp, X1, sp, X2, sp, m, -0.5f, X1, sp, 1.5f);  // V = 1.5 V0 - 0.5 V0 S
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {  // X1 <- G
-      const int r = e / m, j = e % m;
-      X1[r * sp + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
-    }
-    __syncthreads();
+  }
+  float fr = ej_load(X1, sp, G, s, m);  // X1 <- G; ||G||_F
+  if (!warm)
+    for (int r = warp; r < m; r += nwarp)
+      for (int j = lane; j < m; j += 32) X2[r * sp + j] = (r == j) ? 1.f : 0.f;
+  fr = warp_sum(fr);
+  if (lane == 0) red[warp] = fr;
+  __syncthreads();
+  if (warm) {
     sm_mm<true>(X2, sp, X1, sp, X3, sp, m, 1.f, nullptr, 0, 0.f);  // W = G V = G^T V (G symmetric)
     __syncthreads();
-    sm_mm<true>(X1, sp, X3, sp, X2, sp, m, 1.f, nullptr, 0, 0.f);  // B = V^T W
+    sm_mm_sym(X1, sp, X3, sp, X2, sp, m);  // B = V^T W, exactly symmetric
     __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {  // V^T
-      const int r = e / m, j = e % m;
-      X2[j * sp + r] = X3[r * sp + j];
-    }
+    for (int r = warp; r < m; r += nwarp)  // V^T
+      for (int j = lane; j < m; j += 32) X2[j * sp + r] = X3[r * sp + j];
   } else {
-    for (int e = tid; e < m * m; e += nt) {
-      const int r = e / m, j = e % m;
-      X1[r * sp + j] = (r < s && j < s) ? G[r * s + j] : 0.f;
-      X2[r * sp + j] = (r == j) ? 1.f : 0.f;
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < m * m; e += nt) {  // symmetrise B
-    const int r = e / m, j = e % m;
-    if (r < j) {
-      const float v = 0.5f * (X1[r * sp + j] + X1[j * sp + r]);
-      X1[r * sp + j] = v;
-      X1[j * sp + r] = v;
-    }
+    for (int r = warp; r < m; r += nwarp)  // symmetrise B = G
+      for (int j = lane; j < m; j += 32)
+        if (r < j) {
+          const float v = 0.5f * (X1[r * sp + j] + X1[j * sp + r]);
+          X1[r * sp + j] = v;
+          X1[j * sp + r] = v;
+        }
   }
   if (tid == 0) {
     float t = 0.f;
@@ -667,10 +722,8 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
     converged = (cn == 0) || (__uint_as_float(mx) < tol);
   }
   for (int j = tid; j < s; j += nt) Phi[j] = B[j * sp + j];
-  for (int e = tid; e < s * s; e += nt) {
-    const int r = e / s, j = e % s;
-    Cio[e] = Vt[j * sp + r];
-  }
+  for (int r = warp; r < s; r += nwarp)  // C[r][j] = V[r][j] = V^T[j][r]
+    for (int j = lane; j < s; j += 32) Cio[r * s + j] = Vt[j * sp + r];
   __syncthreads();
   if (tid == 0) {
     float mn = Phi[0];
