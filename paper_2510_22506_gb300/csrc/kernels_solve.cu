@@ -406,8 +406,8 @@ __device__ __forceinline__ void sm_mm_sym(float* __restrict__ out, int so, const
 // Jacobi sweeps whose pairs are ordered so that one parallel step
 // touches only the index sets of disjoint 8 x 8 subproblems.  The m indices
 // form nb = m / 4 blocks of four; outer round r pairs block P with block Q by
-// the round-robin schedule, and a warp rotates the submatrix B[S, S] of such
-// a pair (S = P u Q, local indices 0-3 and 4-7) in four rounds of cross pairs
+// the round-robin schedule, and half a warp rotates the submatrix B[S, S] of
+// such a pair (S = P u Q, local indices 0-3 and 4-7) in four rounds of cross pairs
 // (i, 4 + (i xor t)), preceded in the first outer round of a sweep by three
 // rounds of pairs within a block, accumulating the product U of its
 // rotations.  Every pair (p, q) is thus rotated once per sweep, as in a
@@ -416,8 +416,10 @@ __device__ __forceinline__ void sm_mm_sym(float* __restrict__ out, int so, const
 // and columns).  The CTA then applies J = diag(U) over the subproblems by
 // 8 x 8 products held in registers: B <- J^T B and V^T <- J^T V^T (rows,
 // 8 x 4 tiles), then B <- B J (columns, 4 x 8 tiles), the diagonal
-// superblocks taking the warp's rotated submatrix.  Inner rounds cost warp
-// synchronisations only; an outer round costs three block barriers.
+// superblocks taking the rotated submatrix.  Inner rounds cost warp
+// synchronisations only (a warp runs two subproblems in lockstep, so that
+// fewer warps contend for issue slots); an outer round costs three block
+// barriers.
 // Rotation test and stop test: rotate iff B_pq^2 > tol^2 |B_pp B_qq| +
 // floor^2 (tol = sqrt(s) eps, floor = eps ||G||_F / sqrt(s)); stop after a
 // sweep whose largest rotated B_pq^2 / |B_pp B_qq| was below tol (quadratic
@@ -465,16 +467,17 @@ __device__ __forceinline__ float ej_rot(float a, float b, float g, float tol2, f
   return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
 }
 
-// One inner round of a warp on its subproblem (S, U in shared memory), the
-// same instructions on every lane.  Lane L < 16 updates the 2 x 2 block
-// (L >> 2, L & 3) of the grid of this round's four pairs (rows rotated by
-// the first pair, columns by the second; a diagonal block keeps the exact
-// Jacobi update with zeroed off-diagonal), and every lane rotates row L >> 2
-// of U by pair L & 3.  Lanes 0, 5, 10, 15 count their pair's rotation.
+// One inner round of a half warp on its subproblem (S, U in shared memory),
+// the same instructions on every lane.  Lane L of the half updates the
+// 2 x 2 block (L >> 2, L & 3) of the grid of this round's four pairs (rows
+// rotated by the first pair, columns by the second; a diagonal block keeps
+// the exact Jacobi update with zeroed off-diagonal) and rotates rows L >> 2
+// and 4 + (L >> 2) of U by pair L & 3; lanes 0, 5, 10, 15 count their pair's
+// rotation.  The two halves of a warp run two subproblems in lockstep.
 template <bool W, int T>
-__device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restrict__ Uw, int lane, float tol2,
+__device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restrict__ Uw, int hl, float tol2,
                                          float floor2, unsigned& cnt, float& cmu) {
-  const int k = (lane >> 2) & 3, l = lane & 3, ui = lane >> 2;
+  const int k = hl >> 2, l = hl & 3;
   int pk, qk, pl, ql;
   ej_pair(W, T, k, pk, qk);
   ej_pair(W, T, l, pl, ql);
@@ -482,7 +485,8 @@ __device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restri
   const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
   const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
   const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
-  const float u0 = Uw[ui * 8 + pl], u1 = Uw[ui * 8 + ql];
+  const float u00 = Uw[k * 8 + pl], u01 = Uw[k * 8 + ql];
+  const float u10 = Uw[(k + 4) * 8 + pl], u11 = Uw[(k + 4) * 8 + ql];
   __syncwarp();  // every read of this round before any write
   float ck, sk, tk, cl, sl, tl;
   const float mu = ej_rot(ak, bk, gk, tol2, floor2, ck, sk, tk);
@@ -497,19 +501,17 @@ __device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restri
     z11 = fmaf(tk, gk, bk);
     z01 = 0.f;
     z10 = 0.f;
-  }
-  if (lane < 16) {
-    Sw[pk * 8 + pl] = z00;
-    Sw[pk * 8 + ql] = z01;
-    Sw[qk * 8 + pl] = z10;
-    Sw[qk * 8 + ql] = z11;
-  }
-  if (dg && lane < 16) {
     ++cnt;
     cmu = fmaxf(cmu, mu);
   }
-  Uw[ui * 8 + pl] = cl * u0 - sl * u1;
-  Uw[ui * 8 + ql] = sl * u0 + cl * u1;
+  Sw[pk * 8 + pl] = z00;
+  Sw[pk * 8 + ql] = z01;
+  Sw[qk * 8 + pl] = z10;
+  Sw[qk * 8 + ql] = z11;
+  Uw[k * 8 + pl] = cl * u00 - sl * u01;
+  Uw[k * 8 + ql] = sl * u00 + cl * u01;
+  Uw[(k + 4) * 8 + pl] = cl * u10 - sl * u11;
+  Uw[(k + 4) * 8 + ql] = sl * u10 + cl * u11;
   __syncwarp();
 }
 
@@ -517,14 +519,14 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
                                                 float* __restrict__ Phi, int s, int warm, int max_sweeps,
                                                 double tmin, int* status, int* sweeps_used) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int m = (s + 7) & ~7, sp = m + 4, nb = m / 4, nsub = m / 8;
+  const int m = (s + 7) & ~7, sp = m + 4, nb = m / 4, nsub = m / 8, nsub2 = (nsub + 1) / 2;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   float* X1 = (float*)sm;
   float* X2 = X1 + m * sp;
   float* X3 = X2 + m * sp;  // warm-start scratch
-  float* SC = X3 + m * sp;  // the subproblems
+  float* SC = X3 + m * sp;  // the subproblems and a spare slot
   __shared__ float red[32];
-  __shared__ unsigned wrot[32], wmu[32];  // per warp: rotations and largest ratio of a sweep
+  __shared__ unsigned wrot[32], wmu[32];  // per subproblem warp: rotations and largest ratio of a sweep
   __shared__ int pq[16];                  // per subproblem: blocks P | Q << 16
   // B in X1, V^T in X2 (both stride sp); element loops run a warp per row
   // and a lane per column
@@ -595,30 +597,34 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
   bool converged = (s <= 1);
   for (; sweep < max_sweeps && !converged; ++sweep) {
     for (int r = 0; r < nb - 1; ++r) {
-      for (int sub = warp; sub < nsub; sub += nwarp) {
-        float* Sw = SC + sub * EJ_SUB;
+      for (int sw = warp; sw < nsub2; sw += nwarp) {
+        const int sub = 2 * sw + (lane >> 4), hl = lane & 15;
+        const bool real = sub < nsub;  // else the spare slot, which never rotates
+        float* Sw = SC + (real ? sub : nsub) * EJ_SUB;
         float* Uw = Sw + 64;
-        int P, Q;
-        round_pair(nb, r, sub, P, Q);
-        if (lane == 0) pq[sub] = P | Q << 16;
-        for (int e = lane; e < 64; e += 32) {
+        int P = 0, Q = 0;
+        if (real) {
+          round_pair(nb, r, sub, P, Q);
+          if (hl == 0) pq[sub] = P | Q << 16;
+        }
+        for (int e = hl; e < 64; e += 16) {
           const int i = e >> 3, j = e & 7;
           const int gi = i < 4 ? 4 * P + i : 4 * Q + i - 4, gj = j < 4 ? 4 * P + j : 4 * Q + j - 4;
-          Sw[e] = B[gi * sp + gj];
+          Sw[e] = real ? B[gi * sp + gj] : 0.f;
           Uw[e] = (i == j) ? 1.f : 0.f;
         }
         __syncwarp();
         if (r == 0) {
-          ej_round<true, 0>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
-          ej_round<true, 1>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
-          ej_round<true, 2>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+          ej_round<true, 0>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+          ej_round<true, 1>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+          ej_round<true, 2>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
         }
-        ej_round<false, 0>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
-        ej_round<false, 1>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
-        ej_round<false, 2>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
-        ej_round<false, 3>(Sw, Uw, lane, tol2, floor2, cnt, cmu);
+        ej_round<false, 0>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+        ej_round<false, 1>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+        ej_round<false, 2>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+        ej_round<false, 3>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
       }
-      if (r == nb - 2 && warp < nsub) {  // this sweep's totals per warp
+      if (r == nb - 2 && warp < nsub2) {  // this sweep's totals per warp
         const unsigned cn = __reduce_add_sync(0xffffffffu, cnt);
         const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(cmu));  // cmu >= 0
         if (lane == 0) {
@@ -715,7 +721,7 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
       __syncthreads();
     }
     unsigned cn = 0, mx = 0;
-    for (int w = 0; w < min(nsub, nwarp); ++w) {
+    for (int w = 0; w < min(nsub2, nwarp); ++w) {
       cn += wrot[w];
       mx = max(mx, wmu[w]);
     }
@@ -735,7 +741,7 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
 
 size_t eig3_smem(int s) {
   const int m = (s + 7) & ~7, sp = m + 4;
-  return (size_t)(3 * m * sp + (m / 8) * EJ_SUB) * sizeof(float);
+  return (size_t)(3 * m * sp + (m / 8 + 1) * EJ_SUB) * sizeof(float);
 }
 
 
