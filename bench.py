@@ -44,7 +44,9 @@ DESC = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maximum SM clock
 # DRAM bytes (read + write) per launch of the dominant kernel class, from one
 # ncu capture of the current kernel (profiles/); None when not captured.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel class, from one
+# ncu capture of the current kernel (profiles/eig_block_jacobi_s64.md)
+TRAFFIC = {("eig", "fp32"): 112896}
 
 
 def dist_env():
