@@ -171,6 +171,19 @@ def test_fp32_factored_and_direct_gram(F):
             assert rel(a, b) <= 1e-4, (mode, k, rel(a, b))
 
 
+@pytest.mark.parametrize("r", [6, 11, 12])
+def test_fp32_eigensolver_sizes(F, r):
+    """Gram sizes s = r^2 across the FP32 eigensolver's configurations: 36
+    (an odd number of 8 x 8 subproblems, one half warp idle), 121 (the
+    largest block-ordered case, 16 subproblems) and 144 (one-sided Jacobi)."""
+    d = inputs(None, dims=(40, 36, 12), r=r, p=0.3, idx=46, noise=0.0, cap=None, dtype=np.float32)
+    st, _ = oracle_run(d, 10)
+    g = gpu_run(F, d, 10, precision="fp32")
+    assert rel(g["X"], st.X) <= 1e-4, rel(g["X"], st.X)
+    for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+        assert rel(a, b) <= 1e-4, (k, rel(a, b))
+
+
 def test_fp32_autotuned_launch_shape(F):
     """The autotuner times its candidates and returns one of them; every
     launch shape of the right-hand-side kernel keeps parity with the oracle."""

@@ -113,3 +113,32 @@ def test_failing_job_does_not_stop_the_others(mods):
         assert states[ids[0]]["state"] == F.FCTN_JOB_DONE and states[ids[2]]["state"] == F.FCTN_JOB_DONE
     finally:
         F.fctn_server_destroy(srv)
+
+
+def test_tuning_cache_per_job_class(mods):
+    """The per-class tuning cache tunes each (dims, ranks, precision) class
+    once, hands every job of a class the same launch shape, and a tuned mix
+    still matches each job run alone with that shape."""
+    F, S = mods
+    jobs = S.mix_jobs(6, seed=9, rate=1000.0, shapes=SMALL[:2], contract=_contract)
+    tuner = S.TuneCache(sweeps=1, candidates=(16, 152)).fill(jobs, "fp32")
+    classes = {S.TuneCache.key(j, S.job_params(j, "fp32")) for j in jobs}
+    assert set(tuner.table) == classes
+    assert all(v in (16, 152) for v in tuner.table.values())
+    for j in jobs:
+        assert S.job_params(j, "fp32", tuner).rhs_ctas == tuner.table[S.TuneCache.key(j, S.job_params(j, "fp32"))]
+    mix = S.run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=30, max_jobs=3, keep_results=True,
+                    arrivals=False, tuner=tuner)
+    assert mix["failed"] == 0
+    for j in jobs:
+        p = S.job_params(j, "fp32", tuner)
+        dt = F.elem_dtype(p)
+        h = F.fctn_create(p)
+        try:
+            F.fctn_set_data(h, np.ascontiguousarray(j["Y"].astype(dt)), j["mask"].astype(np.uint8))
+            F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(dt)) for a in j["init"]])
+            out = np.empty(j["dims"], dtype=dt)
+            F.fctn_complete(h, 1e-4, 30, out)
+        finally:
+            F.fctn_destroy(h)
+        np.testing.assert_array_equal(mix["results"][j["i"]], out)
