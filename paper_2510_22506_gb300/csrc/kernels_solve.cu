@@ -1,5 +1,6 @@
 // Factor solve of Eqs. 5-8: the symmetric eigendecomposition of the Gram
-// (one-sided Jacobi), the eigen-route solve with its FP64 refinement, and the
+// (block-ordered two-sided Jacobi for FP32 Grams up to 128 x 128, one-sided
+// Jacobi otherwise), the eigen-route solve with its FP64 refinement, and the
 // reductions of the objective (Eq. 2) and the stop test.
 #include <float.h>
 
