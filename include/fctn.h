@@ -192,12 +192,12 @@ int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, dou
 /* Autotuner of the launch shape (fctn_params.rhs_ctas).  For each candidate
  * value it creates a probe handle with *p and that rhs_ctas on cuda_stream,
  * copies in Y, mask and factors (as fctn_set_data / fctn_set_factors, host
- * or device per `where`), runs one untimed sweep (graph capture, warm
- * starts) and times `sweeps` sweeps with CUDA events; then destroys the
- * probe.  *best gets the fastest candidate; ms_out[i] (may be NULL) the mean
- * sweep time of candidate i in milliseconds.  cand = NULL takes the built-in
- * candidates {96, 152, 228, 304} (ncand is then ignored; ms_out needs 4
- * entries).  No existing handle changes.  Handles created with different
+ * or device per `where`), runs 2 * sweeps untimed sweeps (graph capture, and
+ * eigensolver warm starts closer to a running job's) and times `sweeps`
+ * sweeps with CUDA events; then destroys the probe.  *best gets the fastest
+ * candidate; ms_out[i] (may be NULL) the mean sweep time of candidate i in
+ * milliseconds.  cand = NULL takes the built-in candidates {96, 120, 152,
+ * 192, 228, 304} (ncand is then ignored; ms_out needs 6 entries).  No existing handle changes.  Handles created with different
  * rhs_ctas give results that agree within rounding (the split changes the
  * summation order of the Gram and right-hand side).  Needs the device
  * memory of one more handle with *p (fctn_footprint_bytes); synchronises

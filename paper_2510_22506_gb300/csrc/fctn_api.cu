@@ -1513,12 +1513,12 @@ int fctn_grow_ranks(fctn_handle* h, const int32_t ranks[FCTN_MAX_ORDER][FCTN_MAX
 
 int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors, int where,
                   const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best, double* ms_out) {
-  static const int32_t builtin[4] = {96, 152, 228, 304};
+  static const int32_t builtin[6] = {96, 120, 152, 192, 228, 304};
   if (!p || !Y || !mask || !factors || !best) return fail(FCTN_E_ARG, "NULL argument");
   if (sweeps < 1 || sweeps > 1000) return fail(FCTN_E_ARG, "sweeps %d outside [1, 1000]", sweeps);
   if (!cand) {
     cand = builtin;
-    ncand = 4;
+    ncand = 6;
   }
   if (ncand < 1 || ncand > 64) return fail(FCTN_E_ARG, "ncand %d outside [1, 64]", ncand);
   for (int i = 0; i < ncand; ++i)
@@ -1540,7 +1540,7 @@ int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, cons
     fctn_stats st{};
     float ms = 0.f;
     if (!(rc = fctn_set_data(h, Y, mask, where)) && !(rc = fctn_set_factors(h, factors, where)) &&
-        !(rc = fctn_pam_sweep(h, 1, nullptr))) {
+        !(rc = fctn_pam_sweep(h, 2 * sweeps, nullptr))) {
       cudaError_t ce = cudaEventRecord(e0, h->st);
       if (ce == cudaSuccess) rc = fctn_pam_sweep(h, sweeps, nullptr);
       if (ce == cudaSuccess && !rc) ce = cudaEventRecord(e1, h->st);

@@ -285,7 +285,7 @@ def fctn_grow_ranks(h, R, scale, seed):
     _check(lib.fctn_grow_ranks(h, ctypes.byref(r), float(scale), ctypes.c_uint64(int(seed) & (2 ** 64 - 1))))
 
 
-TUNE_CANDIDATES = (96, 152, 228, 304)
+TUNE_CANDIDATES = (96, 120, 152, 192, 228, 304)
 
 
 def fctn_autotune(params, Y, mask, factors, candidates=None, sweeps=3, stream=None):
