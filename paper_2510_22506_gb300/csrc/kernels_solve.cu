@@ -805,7 +805,7 @@ void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, dou
 // The operand that every block needs whole (R or W, I x s) is staged in
 // shared memory in chunks of NC rows by the bulk-copy engine; the sum over
 // the I rows is split over KS thread groups and combined in a fixed order.
-constexpr int SOLVE_NT = 256;
+constexpr int SOLVE_NT = 512;
 
 // One bulk copy global -> shared by the TMA engine (cp.async.bulk), completed
 // on an mbarrier by transaction bytes; thread 0 issues, every thread waits
@@ -955,22 +955,27 @@ __global__ void __launch_bounds__(SOLVE_NT) k_solve_fwd(const T* __restrict__ QT
   const T* Cp = stageC ? Cs : C;
   if (stageC)
     for (int e = tid; e < s * s; e += nt) Cs[(e / s) * cst + e % s] = C[e];
-  const int j = tid % s, kq = tid / s;
+  // column j of P in thread j mod cols (KS = threads / cols groups split
+  // the rows); more than one column group only when s exceeds the threads
+  const int cols = min(s, nt), jl = tid % cols, kq = tid / cols;
   const bool act = kq < KS;
-  T acc[TI];
-#pragma unroll
-  for (int t = 0; t < TI; ++t) acc[t] = 0;
   unsigned phase = 0;
-  for (int n0 = 0; n0 < I; n0 += NC) {
-    const int nc = min(NC, I - n0);
-    __syncthreads();  // previous chunk consumed; on the first pass, Qs and the barrier init visible
-    stage_rows(Rs, Rm, n0, nc, s, &bar, phase, status);
-    __syncthreads();
-    if (act) chunk_product<T, TI>(Qs, I, Rs, s, n0, nc, j, kq, KS, TI, acc);
-  }
-  if (act)
+  for (int jb = 0; jb < s; jb += cols) {
+    const int j = jb + jl;
+    T acc[TI];
 #pragma unroll
-    for (int t = 0; t < TI; ++t) part[(kq * TI + t) * s + j] = acc[t];
+    for (int t = 0; t < TI; ++t) acc[t] = 0;
+    for (int n0 = 0; n0 < I; n0 += NC) {
+      const int nc = min(NC, I - n0);
+      __syncthreads();  // previous chunk consumed; on the first pass, Qs and the barrier init visible
+      stage_rows(Rs, Rm, n0, nc, s, &bar, phase, status);
+      __syncthreads();
+      if (act && j < s) chunk_product<T, TI>(Qs, I, Rs, s, n0, nc, j, kq, KS, TI, acc);
+    }
+    if (act && j < s)
+#pragma unroll
+      for (int t = 0; t < TI; ++t) part[(kq * TI + t) * s + j] = acc[t];
+  }
   __syncthreads();
   for (int e = tid; e < TI * s; e += nt) {  // fixed-order combine of the KS partial sums
     T v = 0;
@@ -1039,23 +1044,26 @@ __global__ void __launch_bounds__(SOLVE_NT) k_solve_bwd(const T* __restrict__ Q,
     const int row = (i0 - off + t + I) % I;
     Qs[e] = Q[(int64_t)row * I + n];
   }
-  const int j = tid % s, kq = tid / s;
+  const int cols = min(s, nt), jl = tid % cols, kq = tid / cols;  // as in k_solve_fwd
   const bool act = kq < KS;
-  T acc[NRMAX];
-#pragma unroll
-  for (int t = 0; t < NRMAX; ++t) acc[t] = 0;
   unsigned phase = 0;
-  for (int n0 = 0; n0 < I; n0 += NC) {
-    const int nc = min(NC, I - n0);
-    __syncthreads();
-    stage_rows(Ws, Wm, n0, nc, s, &bar, phase, status);
-    __syncthreads();
-    if (act) chunk_product<T, NRMAX>(Qs, I, Ws, s, n0, nc, j, kq, KS, nr, acc);
-  }
-  if (act)
+  for (int jb = 0; jb < s; jb += cols) {
+    const int j = jb + jl;
+    T acc[NRMAX];
 #pragma unroll
-    for (int t = 0; t < NRMAX; ++t)
-      if (t < nr) part[(kq * NRMAX + t) * s + j] = acc[t];
+    for (int t = 0; t < NRMAX; ++t) acc[t] = 0;
+    for (int n0 = 0; n0 < I; n0 += NC) {
+      const int nc = min(NC, I - n0);
+      __syncthreads();
+      stage_rows(Ws, Wm, n0, nc, s, &bar, phase, status);
+      __syncthreads();
+      if (act && j < s) chunk_product<T, NRMAX>(Qs, I, Ws, s, n0, nc, j, kq, KS, nr, acc);
+    }
+    if (act && j < s)
+#pragma unroll
+      for (int t = 0; t < NRMAX; ++t)
+        if (t < nr) part[(kq * NRMAX + t) * s + j] = acc[t];
+  }
   __syncthreads();
   for (int e = tid; e < nr * s; e += nt) {
     const int t = e / s, jj = e % s;
@@ -1098,7 +1106,7 @@ struct SolveCfg {
 template <typename T>
 SolveCfg<T> solve_cfg(int I, int s, bool bwd, bool res) {
   SolveCfg<T> c;
-  c.TI = I <= 152 ? 1 : 2;
+  c.TI = 1;  // one factor row per CTA: measured faster than two; more CTAs outweigh the extra halo rows
   c.KS = std::max(1, SOLVE_NT / s);
   c.stageC = (!bwd && (size_t)s * (s + 1) * sizeof(T) <= 40 * 1024) ? 1 : 0;
   const size_t budget = 160 * 1024;
@@ -1119,16 +1127,11 @@ void solve_fwd(const T* QT, const T* R, const T* C, const double* LamL, const T*
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_solve_fwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_solve_fwd<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const int grid = (I + c.TI - 1) / c.TI;
-  if (c.TI == 1)
-    k_solve_fwd<T, 1><<<grid, SOLVE_NT, c.bytes, st>>>(QT, R, C, LamL, Phi, lam, rho, I, s, c.NC, c.KS, c.stageC, W,
-                                                        status);
-  else
-    k_solve_fwd<T, 2><<<grid, SOLVE_NT, c.bytes, st>>>(QT, R, C, LamL, Phi, lam, rho, I, s, c.NC, c.KS, c.stageC, W,
-                                                        status);
+  k_solve_fwd<T, 1><<<grid, SOLVE_NT, c.bytes, st>>>(QT, R, C, LamL, Phi, lam, rho, I, s, c.NC, c.KS, c.stageC, W,
+                                                      status);
 }
 
 template <typename T, typename Tc>
@@ -1139,16 +1142,11 @@ void solve_bwd(const T* Q, const T* W, int I, int s, int accumulate, double* A64
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_solve_bwd<T, Tc, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_solve_bwd<T, Tc, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const int grid = (I + c.TI - 1) / c.TI;
-  if (c.TI == 1)
-    k_solve_bwd<T, Tc, 1><<<grid, SOLVE_NT, c.bytes, st>>>(Q, W, I, s, c.NC, c.KS, accumulate, A64, Ac, Yd, Gd, lam,
-                                                            rho, c0, c1, Rout, status);
-  else
-    k_solve_bwd<T, Tc, 2><<<grid, SOLVE_NT, c.bytes, st>>>(Q, W, I, s, c.NC, c.KS, accumulate, A64, Ac, Yd, Gd, lam,
-                                                            rho, c0, c1, Rout, status);
+  k_solve_bwd<T, Tc, 1><<<grid, SOLVE_NT, c.bytes, st>>>(Q, W, I, s, c.NC, c.KS, accumulate, A64, Ac, Yd, Gd, lam,
+                                                          rho, c0, c1, Rout, status);
 }
 
 // FP64 residual of Eq. 5, one CTA per row: R = Y - lam L A - rho A - A G.

@@ -184,6 +184,22 @@ def test_fp32_eigensolver_sizes(F, r):
         assert rel(a, b) <= 1e-4, (k, rel(a, b))
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+def test_gram_wider_than_a_solve_block(F, precision, tol):
+    """s = 17^2 = 289 columns exceed the solve kernels' 256 threads: every
+    column group of Q^T R and Q W must be formed (and the eigensolver takes
+    its global-memory one-sided form).  P_k >= s for every k, so that the
+    Grams have full rank (with rank-deficient Grams and rho = 0.1 the FP32
+    Gram's rounding alone moves the solution by ~1e-3)."""
+    d = inputs(None, dims=(40, 36, 30), r=17, p=0.4, idx=47, noise=0.0, cap=None,
+               dtype=np.float64 if precision == "fp64" else np.float32)
+    st, _ = oracle_run(d, 5)
+    g = gpu_run(F, d, 5, precision=precision)
+    assert rel(g["X"], st.X) <= tol, rel(g["X"], st.X)
+    for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+        assert rel(a, b) <= tol, (k, rel(a, b))
+
+
 def test_fp32_autotuned_launch_shape(F):
     """The autotuner times its candidates and returns one of them; every
     launch shape of the right-hand-side kernel keeps parity with the oracle."""
