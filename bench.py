@@ -44,9 +44,11 @@ DESC = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maximum SM clock
 # DRAM bytes (read + write) per launch of the dominant kernel class, from one
 # ncu capture of the current kernel (profiles/); None when not captured.
-# DRAM bytes (read + write) per launch of the dominant kernel class, from one
-# ncu capture of the current kernel (profiles/eig_block_jacobi_s64.md)
-TRAFFIC = {("eig", "fp32"): 112896}
+# DRAM bytes (read + write) per launch of the dominant kernel class and the
+# kernel they were taken from, from one ncu capture of the current kernels
+# (profiles/eig_block_jacobi_s64.md, profiles/gram_fused_fp32_256x256x31.md)
+TRAFFIC = {("eig", "fp32"): (112896, "k_eig3"),
+           ("gram", "fp32"): (8304213, "k_gram_fused, mean of the three factors' launches at rhs_ctas 192")}
 
 
 def dist_env():
@@ -302,7 +304,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": {"kernel_class": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "peak_source": peak_note, "traffic": TRAFFIC.get((dom, precision)),
+                     "frac": achieved / peak, "peak_source": peak_note,
+                     "traffic": TRAFFIC[(dom, precision)][0] if (dom, precision) in TRAFFIC else None,
+                     "traffic_of": TRAFFIC[(dom, precision)][1] if (dom, precision) in TRAFFIC else None,
                      "avg_launch_us": avg_ms * 1e3, "launches": prof["launches"],
                      "measured": "CUDA events around each launch of the class, second timed pass of K eager sweeps",
                      "class_ms_2sweeps": {c: round(v["ms"], 4) for c, v in per_class.items()}},
