@@ -46,7 +46,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maxim
 # ncu capture of the current kernel (profiles/); None when not captured.
 # DRAM bytes (read + write) per launch of the dominant kernel class and the
 # kernel they were taken from, from one ncu capture of the current kernels
-# (profiles/eig_block_jacobi_s64.md, profiles/gram_fused_fp32_256x256x31.md)
+# (summarised under profiles/)
 TRAFFIC = {("eig", "fp32"): (112896, "k_eig3"),
            ("gram", "fp32"): (8304213, "k_gram_fused, mean of the three factors' launches at rhs_ctas 192")}
 

@@ -17,7 +17,7 @@
  * in closed form (Eq. 10).  Algorithm 2 adds intermediate-tensor reuse and a
  * permuted update order (Sec. 3.3): for N >= 4 the merged tensors of one
  * half of the modes (1..N/2 or N/2+1..N) share the contraction of the other
- * half (for N = 4 the pairs of Sec. 3.3; for N >= 5 this build's reading of
+ * half (for N = 4 the pairs of Sec. 3.3; for N >= 5 a reading of
  * Table 2), and the alternating order starts every even sweep with the
  * second half.
  *
@@ -59,7 +59,7 @@ enum {
   FCTN_E_TIMEOUT = 5,    /* a bounded device-side wait or iteration limit ran out       */
   FCTN_E_CUDA = 6,       /* a CUDA runtime call failed                                  */
   FCTN_E_STATE = 7,      /* call out of order (e.g. sweep before data was set)          */
-  FCTN_E_UNSUPPORTED = 8 /* valid request that this build does not implement            */
+  FCTN_E_UNSUPPORTED = 8 /* valid request that this library does not implement          */
 };
 
 /* arithmetic of the contractions (merged tensors, Gram, right-hand side, X update) */

@@ -22,7 +22,7 @@ Network") computes, step by step and in the paper's order and notation:
   counter per cost centre.
 * PSNR (Sec. 4).
 
-Readings of passages the paper leaves open (each is also listed in the design doc):
+Readings of passages the paper leaves open:
 
 * Laplacian sign: the printed matrix (diagonal -2-delta, neighbours +1) is
   negative definite, while the text says the term penalises second-order
@@ -375,7 +375,7 @@ def psnr(X, truth):
 
 # --------------------------------------------------------------------------
 # FCTN-rank growth (Algorithms 1-2 start from all-ones ranks and grow them to
-# the maximal FCTN-rank; the schedule below is this build's reading)
+# the maximal FCTN-rank; the schedule below is the reading taken here)
 # --------------------------------------------------------------------------
 _U64 = np.uint64
 

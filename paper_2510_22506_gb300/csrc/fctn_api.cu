@@ -928,7 +928,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   const int warm = h->cvalid[k] ? 1 : 0;
   const double e = (double)h->esz;
   const double part_elems = (double)g.ksplit * g.s * g.ncols;
-  // algorithmic traffic / work of each step ("kernels")
+  // algorithmic traffic / work of each step
   const double gram_bytes = (double)h->P * e + part_elems * e + (Mout ? (double)g.s * g.Pk * e : 0.0);
   const double gram_flops = 2.0 * (double)g.s * (double)g.ncols * (double)g.Pk;
   const FactGram& fg = h->fg[k];
