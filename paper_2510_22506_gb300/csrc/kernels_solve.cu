@@ -1080,7 +1080,39 @@ __global__ void __launch_bounds__(SOLVE_NT) k_solve_bwd(const T* __restrict__ Q,
   }
   if (!res) return;
   __syncthreads();
-  for (int e = tid; e < nv * s; e += nt) {
+  if (s <= nt && nv * KS * s * (int)sizeof(double) <= KS * NRMAX * s * (int)sizeof(T)) {
+    // (A G)[r][jj] split over the KS thread groups (q = g, g + KS, ...), the
+    // partial sums combined in group order; G staged in shared memory (in
+    // the W staging area, free now) when it fits there
+    const bool gsm = (size_t)s * s * sizeof(double) <= L.ad - L.ws;
+    double* Gs = (double*)(sm + L.ws);
+    if (gsm) {
+      for (int e = tid; e < s * s; e += nt) Gs[e] = Gd[e];
+      __syncthreads();
+    }
+    const double* Gp = gsm ? Gs : Gd;
+    double* pr = (double*)(sm + L.part);  // [KS][nv][s]
+    const int jj = tid % s, g = tid / s;
+    if (g < KS)
+      for (int r = 0; r < nv; ++r) {
+        const int t = r + 1;
+        double acc = 0.0;
+        for (int q = g; q < s; q += KS) acc = fma(Ad[t * s + q], Gp[(int64_t)q * s + jj], acc);
+        pr[(g * nv + r) * s + jj] = acc;
+      }
+    __syncthreads();
+    for (int e = tid; e < nv * s; e += nt) {
+      const int r = e / s, jc = e % s, t = r + 1;
+      const int64_t o = (int64_t)(i0 + r) * s + jc;
+      double ag = 0.0;
+      for (int gg = 0; gg < KS; ++gg) ag += pr[(gg * nv + r) * s + jc];
+      const double a = Ad[t * s + jc];
+      const double la = c0 * a + c1 * (Ad[(t - 1) * s + jc] + Ad[(t + 1) * s + jc]);
+      Rout[o] = (T)(Yd[o] - lam * la - rho * a - ag);
+    }
+    return;
+  }
+  for (int e = tid; e < nv * s; e += nt) {  // s above the block: one thread per output
     const int r = e / s, jj = e % s, t = r + 1;
     const int64_t o = (int64_t)(i0 + r) * s + jj;
     double g0 = 0.0, g1 = 0.0;
