@@ -91,3 +91,20 @@ def test_rhs_ctas_sets_the_split(F):
     large = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32", rhs_ctas=2432))
     assert small < large
     assert small <= rule <= large
+
+
+@pytest.mark.parametrize("bad", [dict(sweeps=0), dict(sweeps=1001), dict(candidates=(-1,)), dict(candidates=(5000,)),
+                                 dict(candidates=tuple(range(1, 66)))])
+def test_autotune_rejects_bad_arguments_before_any_launch(F, bad):
+    """fctn_autotune validates its arguments on the host (FCTN_E_ARG) before
+    it creates a probe handle, so these calls need no GPU."""
+    dims = (6, 5, 4)
+    p = _params(F, dims, r=2, precision="fp32")
+    Y = np.zeros(dims, dtype=np.float32)
+    mask = np.ones(dims, dtype=np.uint8)
+    facs = [np.zeros(F.factor_shapes(p)[k], dtype=np.float32) for k in range(3)]
+    kw = dict(candidates=(96,), sweeps=1)
+    kw.update(bad)
+    with pytest.raises(F.FctnError) as ei:
+        F.fctn_autotune(p, Y, mask, facs, **kw)
+    assert ei.value.code == F.FCTN_E_ARG
