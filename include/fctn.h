@@ -112,6 +112,9 @@ typedef struct fctn_params {
   int32_t rhs_ctas;     /* launch shape of the Gram / right-hand-side kernel: about this
                            many CTAs per factor update, the columns of M_k split among
                            them; 0 = built-in rule (see fctn_autotune), <= 2432        */
+  int32_t eig_max_sweeps; /* cap on the Jacobi sweeps of one Gram eigendecomposition
+                             (Eq. 7); 0 = 60.  Reaching it is reported in
+                             fctn_stats.eig_capped, not as an error                    */
 } fctn_params;
 
 typedef struct fctn_stats {
@@ -122,7 +125,10 @@ typedef struct fctn_stats {
   int32_t converged;  /* fctn_complete: 1 if rel_change <= tol was reached                    */
   int32_t status;     /* FCTN_OK or the error that stopped the run                             */
   int32_t eig_sweeps; /* Jacobi sweeps of the Gram eigensolver, max over the last sweep's k    */
-  int32_t reserved;
+  int32_t eig_capped; /* factors of the last sweep whose eigendecomposition stopped at the
+                         sweep cap (eig_max_sweeps) before its stop test held; the eigenbasis
+                         is then orthogonal but less exact, and the FP64 refinement of the
+                         solve (refine_steps) carries the rest                                  */
 } fctn_stats;
 
 typedef struct fctn_handle fctn_handle;
@@ -306,9 +312,13 @@ int fctn_server_destroy(fctn_server* s);
  * returns without synchronising.
  *
  * Errors: FCTN_E_ARG for bad arguments or when an intermediate would exceed
- * half the scratch (nothing is launched then); FCTN_E_CUDA if a launch fails.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
+ * half the scratch, FCTN_E_UNSUPPORTED when a chain intermediate would have
+ * more indices than the planner holds (nothing is launched in either case);
+ * FCTN_E_CUDA if a CUDA error from earlier work was already pending on the
+ * calling thread (reported and cleared before anything is queued) or if a
+ * launch fails.  Every call looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with the caller's device current; the first call on
+ * a device may also load the library's device code, so make that first call
  * before any stream capture.  Every call on a device shares the one scratch
  * array and it keeps the last call's contents (every element a call reads is
  * written by that call first, so nothing needs clearing); calls that overlap

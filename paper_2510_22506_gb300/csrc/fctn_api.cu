@@ -116,6 +116,7 @@ struct fctn_handle {
        *Rs = nullptr, *gwork = nullptr;
   int* status = nullptr;
   int* eig_used = nullptr;
+  int eig_cap = 60;  // Jacobi sweep cap per eigendecomposition (fctn_params.eig_max_sweeps)
   void* Ck[FCTN_MAX_ORDER] = {};
   bool cvalid[FCTN_MAX_ORDER] = {};
   double lam_min[FCTN_MAX_ORDER] = {};
@@ -216,13 +217,20 @@ int make_plan(const View& A, const View* B, const Lab* out, int nout, ContractPl
   return FCTN_OK;
 }
 
-// Labels of A x B when the result keeps every unshared index (A's first).
+// Labels of A x B when the result keeps every unshared index (A's first);
+// -1 (nothing written past out[FCTN_MAXD - 1]) if they would be more than FCTN_MAXD.
 int joint_order(const View& A, const View& B, Lab* out) {
   int n = 0;
   for (int i = 0; i < A.n; ++i)
-    if (B.find(A.lab[i]) < 0) out[n++] = A.lab[i];
+    if (B.find(A.lab[i]) < 0) {
+      if (n >= FCTN_MAXD) return -1;
+      out[n++] = A.lab[i];
+    }
   for (int i = 0; i < B.n; ++i)
-    if (A.find(B.lab[i]) < 0) out[n++] = B.lab[i];
+    if (A.find(B.lab[i]) < 0) {
+      if (n >= FCTN_MAXD) return -1;
+      out[n++] = B.lab[i];
+    }
   return n;
 }
 
@@ -314,6 +322,7 @@ int run_chain(fctn_handle* h, const int* ids, int nids, const Lab* final_order, 
       memcpy(ord, final_order, sizeof(Lab) * nfinal);
     } else {
       n = joint_order(cur, nx, ord);
+      if (n < 0) return fail(FCTN_E_UNSUPPORTED, "chain intermediate has more than %d indices", FCTN_MAXD);
     }
     ContractPlan p;
     View ov;
@@ -373,12 +382,17 @@ bool half_valid(const fctn_handle* h, int q) {
 // Sizes of every intermediate of the chains (for allocation).
 int64_t chain_need(const fctn_handle* h) {
   int64_t need = 0;
+  bool too_many = false;
   auto sim = [&](const int* ids, int nids) {
     View cur = factor_view(h, ids[0]);
     for (int i = 1; i < nids - 1; ++i) {
       View nx = factor_view(h, ids[i]);
       Lab ord[FCTN_MAXD];
       int n = joint_order(cur, nx, ord);
+      if (n < 0) {
+        too_many = true;
+        return;
+      }
       int64_t ext[FCTN_MAXD];
       for (int j = 0; j < n; ++j) {
         int ia = cur.find(ord[j]);
@@ -405,7 +419,7 @@ int64_t chain_need(const fctn_handle* h) {
     }
     for (int k = 0; k < h->N; ++k) sim(ids, own_others(h, k, ids));
   }
-  return need;
+  return too_many ? -1 : need;
 }
 
 // Pair intermediates of Algorithm 2 (N = 4): index 0 = (A_1, A_2), 1 = (A_3, A_4).
@@ -433,6 +447,7 @@ View chain_result_view(const fctn_handle* h, const int* ids, int nids, Lab* ord,
     View nx = factor_view(h, ids[i]);
     Lab o[FCTN_MAXD];
     int n = joint_order(cur, nx, o);
+    if (n < 0) n = 0;  // unreachable: check_params bounds every chain by FCTN_MAXD labels
     int64_t ext[FCTN_MAXD];
     for (int q = 0; q < n; ++q) {
       int ia = cur.find(o[q]);
@@ -663,6 +678,8 @@ int check_params(const fctn_params* p) {
     return fail(FCTN_E_ARG, "unknown gram mode %d", p->gram_mode);
   if (p->refine_steps < 0 || p->refine_steps > 8) return fail(FCTN_E_ARG, "refine_steps %d outside [0, 8]", p->refine_steps);
   if (p->rhs_ctas < 0 || p->rhs_ctas > 16 * 152) return fail(FCTN_E_ARG, "rhs_ctas %d outside [0, 2432]", p->rhs_ctas);
+  if (p->eig_max_sweeps < 0 || p->eig_max_sweeps > 1000)
+    return fail(FCTN_E_ARG, "eig_max_sweeps %d outside [0, 1000]", p->eig_max_sweeps);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
@@ -670,6 +687,10 @@ int check_params(const fctn_params* p) {
     for (int t = k + 1; t < p->order; ++t)
       if (p->ranks[k][t] < 1 || p->ranks[k][t] > 64) return fail(FCTN_E_ARG, "rank R[%d][%d] = %d out of range", k, t, p->ranks[k][t]);
   }
+  // every chain intermediate of m factors has m (N - m + 1) labels at most
+  for (int m = 1; m <= p->order; ++m)
+    if (m * (p->order - m + 1) > FCTN_MAXD)
+      return fail(FCTN_E_UNSUPPORTED, "order %d: chain intermediates exceed %d indices", p->order, FCTN_MAXD);
   return FCTN_OK;
 }
 
@@ -692,6 +713,7 @@ void fill_shapes(fctn_handle* h, const fctn_params* p) {
   h->f64 = (p->precision == FCTN_FP64);
   h->esz = h->f64 ? 8 : 4;
   h->tc = (p->precision == FCTN_TF32 || p->precision == FCTN_BF16);
+  h->eig_cap = p->eig_max_sweeps > 0 ? p->eig_max_sweeps : 60;
 }
 
 struct Sizes {
@@ -802,6 +824,7 @@ void plan_fact(const fctn_handle* h, int k, const PairPlan& pp, const std::vecto
 }
 
 int plan_all(fctn_handle* h, std::vector<int>* all, size_t* offs) {
+  if (chain_need(h) < 0) return fail(FCTN_E_UNSUPPORTED, "a chain intermediate has more than %d indices", FCTN_MAXD);
   for (int k = 0; k < h->N; ++k) {
     View L, R;
     pair_operands(h, k, &L, &R);
@@ -959,13 +982,13 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       if (h->f64) {
         LAUNCH_ON(3, launch_fact_gram_f64(fg, (const double*)L, (const double*)R, (double*)HL, (double*)HR, s, h->Gd,
                                           fst));
-        LAUNCH_ON(1, launch_eig_f64(h->Gd, (double*)h->Ck[k], (double*)h->Phi, (double*)h->gwork, s, warm, 60, tmin,
+        LAUNCH_ON(1, launch_eig_f64(h->Gd, (double*)h->Ck[k], (double*)h->Phi, (double*)h->gwork, s, warm, h->eig_cap, tmin,
                                     h->status, h->eig_used + k, fst));
       } else {
         LAUNCH_ON(3, launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
                                           (float*)h->Gs, fst));
         LAUNCH_ON(1, launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                    60, tmin, h->status, h->eig_used + k, fst));
+                                    h->eig_cap, tmin, h->status, h->eig_used + k, fst));
       }
       if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
     } else if (h->f64) {
@@ -989,7 +1012,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     if (!fork)
       LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-             launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, 60, tmin, h->status, h->eig_used + k, h->st));
+             launch_eig_f64(h->Gd, Ck, Phi, (double*)h->gwork, s, warm, h->eig_cap, tmin, h->status, h->eig_used + k, h->st));
     // Eq. 8, then refinement passes on the FP64 residual of Eq. 5 (the
     // first residual is fused into the first backward pass)
     const int nref = h->p.refine_steps;
@@ -1025,7 +1048,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     if (!fork)
       LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-             launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, 60, tmin, h->status,
+             launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
                             h->eig_used + k, h->st));
     const int nref = h->p.refine_steps;
     LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
@@ -1183,8 +1206,12 @@ int read_stats(fctn_handle* h, fctn_stats* out) {
   CK(cudaMemcpyAsync(&status, h->status, sizeof status, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(used, h->eig_used, sizeof(int) * h->N, cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
-  int umax = 0;
-  for (int k = 0; k < h->N; ++k) umax = used[k] > umax ? used[k] : umax;
+  int umax = 0, capped = 0;
+  for (int k = 0; k < h->N; ++k) {
+    const int u = used[k] < 0 ? -used[k] : used[k];  // negative: stopped at the sweep cap
+    umax = u > umax ? u : umax;
+    capped += used[k] < 0 ? 1 : 0;
+  }
   if (out) {
     out->t = h->t;
     out->rel_change = st[0];
@@ -1193,9 +1220,12 @@ int read_stats(fctn_handle* h, fctn_stats* out) {
     out->converged = 0;
     out->status = status;
     out->eig_sweeps = umax;
+    out->eig_capped = capped;
   }
   if (status == FCTN_E_SINGULAR) return fail(FCTN_E_SINGULAR, "min T <= 0: the Sylvester system of Eq. 5 is not positive definite");
-  if (status == FCTN_E_TIMEOUT) return fail(FCTN_E_TIMEOUT, "Gram eigensolver reached its sweep limit");
+  if (status == FCTN_E_TIMEOUT)
+    return fail(FCTN_E_TIMEOUT, "a bounded device wait gave up (a tensor-core pipeline or bulk-copy barrier of a "
+                                "sweep kernel); the sweep's results are not valid");
   if (st[3] != 0.0) {
     if (out) out->status = FCTN_E_NONFINITE;
     return fail(FCTN_E_NONFINITE, "non-finite value in the stop-test reductions");

@@ -7,7 +7,10 @@
 
 #include "fctn.h"
 
-#define FCTN_MAXD 16  // digits of a contraction plan's output index
+// Digits of a contraction plan's output index.  A chain intermediate of m of
+// the N factors keeps its m modes and the m (N - m) bonds to the rest, at most
+// m (N - m + 1) labels: 20 at N = 8 (m = 4 or 5), so 24 covers every order.
+#define FCTN_MAXD 24
 #define FCTN_MAXC 8   // digits of its contracted index
 #define FCTN_CON_TABLE 4096  // contracted-index offsets kept in shared memory
 

@@ -35,7 +35,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Warm start: V0 (the previous sweep's C for the same factor) is first
 // re-orthonormalised by one Newton-Schulz step V0 (3I - V0^T V0)/2.
 // Also checks min_j Phi_j + tmin > 0 (T of Eq. 8 positive) -> FCTN_E_SINGULAR.
-// The sweep limit is not an error: *sweeps_used then equals max_sweeps.
+// The sweep limit is not an error: *sweeps_used is then -max_sweeps (the
+// sign tells the host that the stop test did not hold).
 constexpr int EG = 16;  // lanes per pair
 
 // Sum over the EG lanes of one group.  The mask names only this group's lanes:
@@ -257,8 +258,8 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
     if (!((double)mn + tmin > 0.0)) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
     // not converged within max_sweeps: the eigenbasis is still orthogonal to
     // working precision; the refinement pass of the solve absorbs the rest.
-    // The sweep count is reported (== max_sweeps) rather than failing.
-    if (sweeps_used) *sweeps_used = converged ? sweep : max_sweeps;
+    // The cap is reported (-max_sweeps) rather than failing.
+    if (sweeps_used) *sweeps_used = converged ? sweep : -max_sweeps;
   }
 }
 
@@ -736,7 +737,7 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
     float mn = Phi[0];
     for (int j = 1; j < s; ++j) mn = fminf(mn, Phi[j]);
     if (!((double)mn + tmin > 0.0)) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
-    if (sweeps_used) *sweeps_used = converged ? sweep : max_sweeps;
+    if (sweeps_used) *sweeps_used = converged ? sweep : -max_sweeps;
   }
 }
 

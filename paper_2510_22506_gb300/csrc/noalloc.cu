@@ -2,11 +2,12 @@
 //
 // The two intermediates of the ascending contraction chain live in one
 // file-scope device array (FCTN_NOALLOC_SCRATCH_BYTES, split in two halves).
-// Host code cannot use the array's name as a device address: its address is
-// fetched once per device with cudaGetSymbolAddress, with that device
-// current, and passed to the kernels.
+// Host code cannot use the array's name as a device address: every call asks
+// for its address with cudaGetSymbolAddress, with the caller's device
+// current, and passes that address to the kernels.  The lookup is repeated
+// per call (it is cheap next to the launches) so that a device reset or a new
+// primary context, which can move the array, never leaves a stale address.
 #include <cstring>
-#include <mutex>
 
 #include "fctn_internal.cuh"
 
@@ -14,24 +15,15 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FCTN_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device.
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fctn_internal_fail(FCTN_E_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fctn_internal_fail(FCTN_E_UNSUPPORTED, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return fctn_internal_fail(FCTN_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();  // the failed lookup is reported here, not by a later call
+    return fctn_internal_fail(FCTN_E_CUDA, "cudaGetSymbolAddress of the scratch array failed");
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return FCTN_OK;
 }
 
@@ -137,15 +129,20 @@ extern "C" int fctn_contract_noalloc(int order, const int64_t* dims, const int32
     NView nx = factor_view(N, dims, ranks, i);
     NLab ord[FCTN_MAXD];
     int n = 0;
+    bool too_many = false;
+    auto push = [&](const NLab& l) {
+      if (n >= FCTN_MAXD) too_many = true;
+      else ord[n++] = l;
+    };
     if (i == N - 1) {
-      for (int t = 0; t < N; ++t) ord[n++] = NLab{0, t};
+      for (int t = 0; t < N; ++t) push(NLab{0, t});
     } else {
       for (int q = 0; q < cur.n; ++q)
-        if (nx.find(cur.lab[q]) < 0) ord[n++] = cur.lab[q];
+        if (nx.find(cur.lab[q]) < 0) push(cur.lab[q]);
       for (int q = 0; q < nx.n; ++q)
-        if (cur.find(nx.lab[q]) < 0) ord[n++] = nx.lab[q];
+        if (cur.find(nx.lab[q]) < 0) push(nx.lab[q]);
     }
-    if (n > FCTN_MAXD) return fctn_internal_fail(FCTN_E_UNSUPPORTED, "fctn_contract_noalloc: too many indices");
+    if (too_many) return fctn_internal_fail(FCTN_E_UNSUPPORTED, "fctn_contract_noalloc: too many indices");
     NView ov;
     int rc = plan(cur, nx, ord, n, &plans[i], &ov);
     if (rc) return rc;
@@ -155,6 +152,12 @@ extern "C" int fctn_contract_noalloc(int order, const int64_t* dims, const int32
                                 "(FCTN_NOALLOC_SCRATCH_BYTES / 2 per intermediate)");
     cur = ov;
   }
+  // an error left pending by earlier, unrelated work on this thread would be
+  // read back after the first launch below and abort the chain half-way; it
+  // is reported (and cleared) here instead, before anything is queued
+  cudaError_t pending = cudaGetLastError();
+  if (pending != cudaSuccess)
+    return fctn_internal_fail(FCTN_E_CUDA, "fctn_contract_noalloc: a CUDA error was pending before the call");
   void* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc) return rc;

@@ -46,6 +46,7 @@ class fctn_params(ctypes.Structure):
         ("extrap_beta", ctypes.c_double),
         ("gram_mode", ctypes.c_int32),
         ("rhs_ctas", ctypes.c_int32),
+        ("eig_max_sweeps", ctypes.c_int32),
     ]
 
 
@@ -58,7 +59,7 @@ class fctn_stats(ctypes.Structure):
         ("converged", ctypes.c_int32),
         ("status", ctypes.c_int32),
         ("eig_sweeps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("eig_capped", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -156,7 +157,8 @@ def fctn_version():
 
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
-                laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0):
+                laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
+                eig_max_sweeps=0):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -182,6 +184,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
         p.extrap_alpha, p.extrap_beta = float(extrapolation[0]), float(extrapolation[1])
     p.gram_mode = {"auto": 0, "direct": 1, "factored": 2}[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
     p.rhs_ctas = int(rhs_ctas)
+    p.eig_max_sweeps = int(eig_max_sweeps)
     return p
 
 

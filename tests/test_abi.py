@@ -108,3 +108,22 @@ def test_autotune_rejects_bad_arguments_before_any_launch(F, bad):
     with pytest.raises(F.FctnError) as ei:
         F.fctn_autotune(p, Y, mask, facs, **kw)
     assert ei.value.code == F.FCTN_E_ARG
+
+
+def test_order8_planning_stays_in_bounds(F):
+    """Order 8, every rank 1: chain intermediates carry up to 20 labels.  The
+    footprint planner and the no-allocation contraction plan them without
+    overrunning their label arrays and answer with status codes; the
+    no-allocation call is rejected by its scratch limit before it touches
+    the device (its pointers are never dereferenced)."""
+    import ctypes
+    dims = (16,) * 8
+    N = 8
+    R = np.ones((N, N), dtype=int)
+    assert F.fctn_footprint_bytes(F.make_params(dims, R, precision="fp32")) > 4 * 16 ** 8
+    d = (ctypes.c_int64 * N)(*dims)
+    r = (ctypes.c_int32 * (N * N))(*([1] * (N * N)))
+    fake = (ctypes.c_void_p * N)(*([ctypes.c_void_p(256)] * N))
+    rc = F.lib.fctn_contract_noalloc(N, d, r, F.FCTN_FP32, fake, ctypes.c_void_p(256), None)
+    assert rc == F.FCTN_E_ARG
+    assert "scratch" in F.fctn_last_error()

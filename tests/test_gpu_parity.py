@@ -291,3 +291,24 @@ def test_fp64_asymmetric_extrapolation_matches_oracle(F, dims, r, cap):
     assert rel(g["X"], st.X) <= 1e-9, rel(g["X"], st.X)
     for a, b in zip(g["factors"], st.factors):
         assert rel(a, b) <= 1e-9
+
+
+# ---- the eigensolver's sweep cap is reported, not hidden ------------------
+@pytest.mark.parametrize("precision,dims,r", [("fp32", (40, 36, 9), 5), ("fp32", (12, 10, 6, 5), 6),
+                                              ("fp64", (30, 30, 10), 3)])
+def test_eig_sweep_cap_is_reported(F, precision, dims, r):
+    """A cap of one Jacobi sweep on a cold Gram (first PAM sweep, no warm
+    start) cannot meet the stop test: every factor reports the cap in
+    fctn_stats.eig_capped while the sweep itself still completes (FCTN_OK,
+    finite values).  The default cap is not reached on the same inputs."""
+    dt = np.float64 if precision == "fp64" else np.float32
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=63, noise=0.0, cap=None, dtype=dt)
+    g = gpu_run(F, d, 1, precision=precision, eig_max_sweeps=1)
+    st = g["stats"]
+    assert st["status"] == 0
+    assert st["eig_capped"] == len(dims), st
+    assert st["eig_sweeps"] == 1
+    assert np.isfinite(g["X"]).all()
+    g2 = gpu_run(F, d, 1, precision=precision)
+    assert g2["stats"]["eig_capped"] == 0, g2["stats"]
+    assert g2["stats"]["eig_sweeps"] > 1

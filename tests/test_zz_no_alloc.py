@@ -67,3 +67,34 @@ def test_noalloc_rejects_oversized_intermediate():
         F.fctn_contract_noalloc(dims, R, "fp32", small, out)
     assert ei.value.code == F.FCTN_E_ARG
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_order5_unequal_ranks_twice():
+    """Order 5 with unequal bond ranks: the bond order of every factor view
+    (smaller mode index first) must match the handle-based contraction."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_22506_gb300 import fctn as F
+
+    dims = (5, 4, 3, 4, 3)
+    N = len(dims)
+    R = np.ones((N, N), dtype=int)
+    vals = iter([2, 3, 1, 2, 3, 2, 1, 2, 3, 2])
+    for a in range(N):
+        for b in range(a + 1, N):
+            R[a, b] = R[b, a] = next(vals)
+    p = F.make_params(dims, R, precision="fp64", reuse=False)
+    rng = np.random.default_rng(5)
+    fs = [np.ascontiguousarray(rng.standard_normal(shp)) for shp in F.factor_shapes(p)]
+    h = F.fctn_create(p)
+    try:
+        F.fctn_set_factors(h, fs)
+        ref = np.empty(dims)
+        F.fctn_contract(h, ref)
+    finally:
+        F.fctn_destroy(h)
+    dev = [torch.from_numpy(a).cuda() for a in fs]
+    for _ in range(2):
+        out = torch.full(dims, float("nan"), dtype=torch.float64, device="cuda")
+        F.fctn_contract_noalloc(dims, R, "fp64", dev, out)
+        torch.cuda.synchronize()
+        assert _rel(out.cpu().numpy(), ref) <= 1e-12
