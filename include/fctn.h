@@ -236,7 +236,8 @@ enum {
   FCTN_KC_SOLVE = 4,    /* Eq. 8 solve and its FP64 refinement                          */
   FCTN_KC_XUPDATE = 5,  /* X update of Eq. 10 fused with F = A_k(k) M_k and the sums    */
   FCTN_KC_MISC = 6,     /* trace terms, finalisation, staging                           */
-  FCTN_KC_COUNT = 7
+  FCTN_KC_ENV = 7,      /* Grams of the factors and their chains (Gram of M_k)          */
+  FCTN_KC_COUNT = 8
 };
 
 /* Time every launch of one kernel class with CUDA events recorded on the

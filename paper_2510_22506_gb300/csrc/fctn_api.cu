@@ -69,6 +69,45 @@ View dense_view(int n, const Lab* labs, const int64_t* ext) {
   return v;
 }
 
+// One table-driven contraction (kernels_sgemm.cu) of a plan: its shape, the
+// offset (in ints) of its six tables in the handle's table buffer, and whether
+// the operands are passed swapped (so that C's innermost index runs along n).
+struct SgPlanH {
+  SgShape sh{};
+  size_t tab = 0;
+  bool swap = false;
+};
+
+// Head-mode association of a sweep (order 1, ..., N; head = mode 1, index 0
+// here).  M_0, the merged tensor of every factor but the head, serves three
+// products: the head's right-hand side X_(0) M_0^T, the reconstruction
+// F = A_(0) M_0 of the X update (the merged tensor that Algorithm 2 keeps for
+// the X update, here the head's), and, through Z = X_(0)^T A_(0), the
+// right-hand sides of all other factors: X_(k) M_k^T is Z contracted with the
+// factors t != 0, k (the same products, associated differently).  The
+// Gram M_k M_k^T of every factor is the contraction of the factor Grams
+// H_t = A_(t)^T A_(t), t != k, over their shared bond pairs.
+struct HeadRoute {
+  bool on = false;
+  int64_t s0 = 0, P0 = 0;
+  SgPlanH m0[FCTN_MAX_ORDER];  // chain 1 .. N-1 building M_0 (nm0 steps)
+  int nm0 = 0;
+  SgPlanH y0, z;               // Y_0 raw = X_(0) M_0^T, Z = X_(0)^T A_(0)
+  SgPlanH ys[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k >= 1: Z (x) A_t for t in yfac[k]
+  int yfac[FCTN_MAX_ORDER][FCTN_MAX_ORDER] = {};
+  int nys[FCTN_MAX_ORDER] = {};
+  SgPlanH hg[FCTN_MAX_ORDER];  // H_t
+  SgPlanH env[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k: chain of H_t, t != k (ascending)
+  int nenv[FCTN_MAX_ORDER] = {};
+  int64_t u_elems = 0, e_elems = 0, part_main = 0, part_side = 0;
+  float *M0 = nullptr, *Zb = nullptr, *U[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr};
+  float* H[FCTN_MAX_ORDER] = {};
+  float *Yraw = nullptr, *pm = nullptr, *ps = nullptr;
+  int* tabs = nullptr;
+  bool m0_valid = false;
+  bool hvalid[FCTN_MAX_ORDER] = {};
+};
+
 }  // namespace
 
 struct fctn_handle {
@@ -148,6 +187,7 @@ struct fctn_handle {
   double prof_ms = 0.0, prof_bytes = 0.0, prof_flops = 0.0;
   double cls_bytes = 0.0, cls_flops = 0.0;  // algorithmic counts of the class, since fctn_profile()
   int64_t cls_launches = 0;
+  HeadRoute hr;  // head-mode association (FP32 / TF32 / BF16 with reuse and the plain order)
 };
 
 namespace {
@@ -837,14 +877,249 @@ int plan_all(fctn_handle* h, std::vector<int>* all, size_t* offs) {
     plan_fact(h, k, h->pp[k], tab, &h->fg[k], &ftab);
     if (offs) offs[FCTN_MAX_ORDER + k] = all->size();
     all->insert(all->end(), ftab.begin(), ftab.end());
-    h->mat[k] = h->p.reuse && materialise_ok(h, k);
-    if (h->tc) {
+    h->mat[k] = h->p.reuse && materialise_ok(h, k) && !h->hr.on;
+    if (h->tc && !h->hr.on) {
       h->tp[k].n_groups = 0;
       GramPlan g = gram_plan(h, k);
       rc = tc_plan(h->pp[k], g, h->p.precision, &h->tp[k]);
       if (rc) return fail(rc, "tensor-core Gram kernel does not cover factor %d (s_k = %lld)", k, (long long)h->s[k]);
     }
   }
+  return FCTN_OK;
+}
+
+// ---- head-mode association: planning ---------------------------------------
+// Second copy of a bond in a Gram H_t = A_(t)^T A_(t) (kind 2).
+Lab pbond_lab(int x, int y) { return Lab{2, x < y ? x : y, x < y ? y : x}; }
+
+// Mixed-radix offsets: for every index e over the digits (last fastest),
+// o1[e] = sum digit * s1, o2[e] = sum digit * s2.
+void radix_offsets(int nd, const int64_t* ext, const int64_t* s1, const int64_t* s2, int* o1, int* o2) {
+  int64_t total = 1;
+  for (int d = 0; d < nd; ++d) total *= ext[d];
+  for (int64_t e = 0; e < total; ++e) {
+    int64_t r = e, a = 0, b = 0;
+    for (int d = nd - 1; d >= 0; --d) {
+      const int64_t dig = r % ext[d];
+      r /= ext[d];
+      a += dig * s1[d];
+      b += dig * s2[d];
+    }
+    o1[e] = (int)a;
+    o2[e] = (int)b;
+  }
+}
+
+int64_t max_offset(const View& v) {
+  int64_t o = 0;
+  for (int i = 0; i < v.n; ++i) o += (v.ext[i] - 1) * v.str[i];
+  return o;
+}
+
+// Plan C = A (x) B (every shared label contracted) with C laid out as `C`.
+// The operand that holds C's innermost label plays B, so that consecutive
+// columns n are consecutive in C.
+int sg_plan(const View& A0, const View& B0, const View& C, SgPlanH* out, std::vector<int>* tabs) {
+  const bool swap = C.n > 0 && A0.find(C.lab[C.n - 1]) >= 0;
+  const View& A = swap ? B0 : A0;
+  const View& B = swap ? A0 : B0;
+  int64_t mext[FCTN_MAXD], ma[FCTN_MAXD], mc[FCTN_MAXD], next[FCTN_MAXD], nb[FCTN_MAXD], nc[FCTN_MAXD];
+  int64_t kext[FCTN_MAXD], ka[FCTN_MAXD], kbs[FCTN_MAXD];
+  int nm = 0, nn = 0, nk = 0;
+  int64_t M = 1, Nn = 1, K = 1;
+  for (int i = 0; i < C.n; ++i) {
+    const int ia = A.find(C.lab[i]), ib = B.find(C.lab[i]);
+    if ((ia >= 0) == (ib >= 0)) return fail(FCTN_E_STATE, "contraction plan: output index in both or neither operand");
+    if (ia >= 0) {
+      mext[nm] = C.ext[i], ma[nm] = A.str[ia], mc[nm++] = C.str[i];
+      M *= C.ext[i];
+    } else {
+      next[nn] = C.ext[i], nb[nn] = B.str[ib], nc[nn++] = C.str[i];
+      Nn *= C.ext[i];
+    }
+  }
+  for (int i = 0; i < A.n; ++i) {
+    if (C.find(A.lab[i]) >= 0) continue;
+    const int ib = B.find(A.lab[i]);
+    if (ib < 0) return fail(FCTN_E_STATE, "contraction plan: free index missing from the output");
+    kext[nk] = A.ext[i], ka[nk] = A.str[i], kbs[nk++] = B.str[ib];
+    K *= A.ext[i];
+  }
+  for (int i = 0; i < B.n; ++i)
+    if (C.find(B.lab[i]) < 0 && A.find(B.lab[i]) < 0)
+      return fail(FCTN_E_STATE, "contraction plan: free index missing from the output");
+  const int64_t lim = (int64_t)1 << 31;
+  if (M >= lim || Nn >= lim || K >= lim || max_offset(A) >= lim || max_offset(B) >= lim || max_offset(C) >= lim)
+    return fail(FCTN_E_UNSUPPORTED, "contraction plan: a tensor of the sweep exceeds 2^31 elements");
+  out->swap = swap;
+  out->tab = tabs->size();
+  tabs->resize(out->tab + (size_t)(2 * M + 2 * Nn + 2 * K));
+  int* am = tabs->data() + out->tab;
+  int* cm = am + M;
+  int* bn = cm + M;
+  int* cn = bn + Nn;
+  int* ak = cn + Nn;
+  int* bk = ak + K;
+  radix_offsets(nm, mext, ma, mc, am, cm);
+  radix_offsets(nn, next, nb, nc, bn, cn);
+  radix_offsets(nk, kext, ka, kbs, ak, bk);
+  sg_shape((int)M, (int)Nn, (int)K, &out->sh);
+  // loader lanes: along k when A's (B's) innermost contracted digit is
+  // contiguous, else along m (n) when that digit is
+  out->sh.a_mfast = (nk == 0 || ka[nk - 1] != 1) && nm > 0 && ma[nm - 1] == 1;
+  out->sh.b_nfast = (nk == 0 || kbs[nk - 1] != 1) && nn > 0 && nb[nn - 1] == 1;
+  return FCTN_OK;
+}
+
+View x_view(const fctn_handle* h) {
+  Lab l[FCTN_MAXD];
+  int64_t e[FCTN_MAXD];
+  for (int t = 0; t < h->N; ++t) l[t] = mode_lab(t), e[t] = h->I[t];
+  return dense_view(h->N, l, e);
+}
+// M_0 (s_0 x P_0): bonds (0, t) ascending, then modes 1 .. N-1.
+View m0_view(const fctn_handle* h) {
+  Lab l[FCTN_MAXD];
+  int64_t e[FCTN_MAXD];
+  int n = 0;
+  for (int t = 1; t < h->N; ++t) l[n] = bond_lab(0, t), e[n++] = rank_of(h, 0, t);
+  for (int t = 1; t < h->N; ++t) l[n] = mode_lab(t), e[n++] = h->I[t];
+  return dense_view(n, l, e);
+}
+// Z = X_(0)^T A_(0) (P_0 x s_0): modes 1 .. N-1, then bonds (0, t).
+View z_view(const fctn_handle* h) {
+  Lab l[FCTN_MAXD];
+  int64_t e[FCTN_MAXD];
+  int n = 0;
+  for (int t = 1; t < h->N; ++t) l[n] = mode_lab(t), e[n++] = h->I[t];
+  for (int t = 1; t < h->N; ++t) l[n] = bond_lab(0, t), e[n++] = rank_of(h, 0, t);
+  return dense_view(n, l, e);
+}
+// Gram of factor t's bonds (s_t x s_t): bonds (t, u) ascending, then their second copies.
+View hgram_view(const fctn_handle* h, int t) {
+  Lab l[FCTN_MAXD];
+  int64_t e[FCTN_MAXD];
+  int n = 0;
+  for (int u = 0; u < h->N; ++u)
+    if (u != t) l[n] = bond_lab(t, u), e[n++] = rank_of(h, t, u);
+  for (int u = 0; u < h->N; ++u)
+    if (u != t) l[n] = pbond_lab(t, u), e[n++] = rank_of(h, t, u);
+  return dense_view(n, l, e);
+}
+// Factor t with its bonds relabelled as second copies.
+View factor_primed_view(const fctn_handle* h, int t) {
+  View v = factor_view(h, t);
+  for (int i = 0; i < v.n; ++i)
+    if (v.lab[i].kind == 1) v.lab[i].kind = 2;
+  return v;
+}
+View joint_view(const View& a, const View& b, int* rc) {
+  Lab o[FCTN_MAXD];
+  int64_t e[FCTN_MAXD];
+  const int n = joint_order(a, b, o);
+  if (n < 0) {
+    *rc = FCTN_E_UNSUPPORTED;
+    return View{};
+  }
+  for (int q = 0; q < n; ++q) {
+    const int ia = a.find(o[q]);
+    e[q] = ia >= 0 ? a.ext[ia] : b.ext[b.find(o[q])];
+  }
+  return dense_view(n, o, e);
+}
+
+// Decide and plan the head-mode association (FP32 / TF32 / BF16 with reuse,
+// the plain order (N = 3 has only one order), N >= 3); the old route stays in
+// place otherwise.  Intermediates larger than 2^28 elements turn it off.
+int plan_route(fctn_handle* h, std::vector<int>* tabs) {
+  HeadRoute& r = h->hr;
+  r = HeadRoute{};
+  const int N = h->N;
+  r.on = !h->f64 && h->p.reuse && N >= 3 && (h->p.order_policy == FCTN_ORDER_PLAIN || N == 3);
+  if (!r.on) return FCTN_OK;
+  r.s0 = h->s[0];
+  r.P0 = h->Pk[0];
+  int rc = FCTN_OK;
+  std::vector<int> t0;  // tables of this plan (appended at the end, or dropped)
+  auto track = [](int64_t* mx, int64_t v) { *mx = v > *mx ? v : *mx; };
+  // M_0: factors 1 .. N-1 in ascending order
+  {
+    View cur = factor_view(h, 1);
+    for (int t = 2; t < N; ++t) {
+      View nx = factor_view(h, t);
+      View o = (t == N - 1) ? m0_view(h) : joint_view(cur, nx, &rc);
+      if (rc) return fail(rc, "head route: chain intermediate has too many indices");
+      if (t < N - 1) track(&r.u_elems, o.size());
+      if ((rc = sg_plan(cur, nx, o, &r.m0[r.nm0], &t0))) return rc;
+      track(&r.part_main, (int64_t)sg_part_elems(r.m0[r.nm0].sh));
+      r.nm0++;
+      cur = o;
+    }
+  }
+  if ((rc = sg_plan(x_view(h), m0_view(h), factor_view(h, 0), &r.y0, &t0))) return rc;
+  if ((rc = sg_plan(x_view(h), factor_view(h, 0), z_view(h), &r.z, &t0))) return rc;
+  track(&r.part_main, (int64_t)sg_part_elems(r.y0.sh));
+  track(&r.part_main, (int64_t)sg_part_elems(r.z.sh));
+  // right-hand sides of k >= 1: Z contracted with the factors t != 0, k,
+  // the largest mode first (it shrinks the intermediate most)
+  for (int k = 1; k < N; ++k) {
+    int ids[FCTN_MAX_ORDER], n = 0;
+    for (int t = 1; t < N; ++t)
+      if (t != k) ids[n++] = t;
+    for (int a = 0; a < n; ++a)
+      for (int b = a + 1; b < n; ++b)
+        if (h->I[ids[b]] > h->I[ids[a]]) std::swap(ids[a], ids[b]);
+    View cur = z_view(h);
+    for (int q = 0; q < n; ++q) {
+      View nx = factor_view(h, ids[q]);
+      View o = (q == n - 1) ? factor_view(h, k) : joint_view(cur, nx, &rc);
+      if (rc) return fail(rc, "head route: chain intermediate has too many indices");
+      if (q < n - 1) track(&r.u_elems, o.size());
+      if ((rc = sg_plan(cur, nx, o, &r.ys[k][q], &t0))) return rc;
+      track(&r.part_main, (int64_t)sg_part_elems(r.ys[k][q].sh));
+      r.yfac[k][q] = ids[q];
+      cur = o;
+    }
+    r.nys[k] = n;
+  }
+  // factor Grams and, per k, their chain over t != k (ascending)
+  for (int t = 0; t < N; ++t) {
+    if ((rc = sg_plan(factor_view(h, t), factor_primed_view(h, t), hgram_view(h, t), &r.hg[t], &t0))) return rc;
+    track(&r.part_side, (int64_t)sg_part_elems(r.hg[t].sh));
+  }
+  for (int k = 0; k < N; ++k) {
+    int ids[FCTN_MAX_ORDER], n = 0;
+    for (int t = 0; t < N; ++t)
+      if (t != k) ids[n++] = t;
+    View cur = hgram_view(h, ids[0]);
+    for (int q = 1; q < n; ++q) {
+      View nx = hgram_view(h, ids[q]);
+      View o = (q == n - 1) ? hgram_view(h, k) : joint_view(cur, nx, &rc);
+      if (rc) return fail(rc, "head route: Gram chain intermediate has too many indices");
+      if (q < n - 1) track(&r.e_elems, o.size());
+      if ((rc = sg_plan(cur, nx, o, &r.env[k][q - 1], &t0))) return rc;
+      track(&r.part_side, (int64_t)sg_part_elems(r.env[k][q - 1].sh));
+      cur = o;
+    }
+    r.nenv[k] = n - 1;
+  }
+  const int64_t cap = (int64_t)1 << 28;
+  if (r.u_elems > cap || r.e_elems > cap || r.part_main > cap || r.part_side > cap) {
+    r = HeadRoute{};
+    return FCTN_OK;
+  }
+  // table offsets are relative to this plan's block, which starts at tabs->size()
+  const size_t base = tabs->size();
+  auto rebase = [&](SgPlanH& q) { q.tab += base; };
+  for (int i = 0; i < r.nm0; ++i) rebase(r.m0[i]);
+  rebase(r.y0);
+  rebase(r.z);
+  for (int k = 1; k < N; ++k)
+    for (int q = 0; q < r.nys[k]; ++q) rebase(r.ys[k][q]);
+  for (int t = 0; t < N; ++t) rebase(r.hg[t]);
+  for (int k = 0; k < N; ++k)
+    for (int q = 0; q < r.nenv[k]; ++q) rebase(r.env[k][q]);
+  tabs->insert(tabs->end(), t0.begin(), t0.end());
   return FCTN_OK;
 }
 
@@ -868,6 +1143,11 @@ Sizes sizes_of(const fctn_handle* h) {
   z.maxfac = z.Is;
   z.chain = chain_need(h);
   z.lbuf = lbuf_need(h);
+  if (h->hr.on) {  // the head-mode route has buffers of its own (route_bytes); the
+    // chain buffers stay for fctn_contract
+    z.M = z.part = z.hbuf = z.lbuf = 0;
+    return z;
+  }
   if (reuse_pairs(h)) {
     for (int q = 0; q < 2; ++q) {
       Lab ord[FCTN_MAXD];
@@ -885,6 +1165,22 @@ void release_side(fctn_handle* h) {
   if (h->side) cudaStreamDestroy(h->side);
   h->side = nullptr;
   h->ev_fork = h->ev_join = nullptr;
+}
+
+// Device bytes of the head-mode route's own buffers.
+size_t route_bytes(const fctn_handle* h, size_t tab_ints) {
+  const HeadRoute& r = h->hr;
+  if (!r.on) return 0;
+  size_t b = 2 * (size_t)r.s0 * r.P0 * 4;            // M_0, Z
+  b += 2 * (size_t)r.u_elems * 4 + 2 * (size_t)r.e_elems * 4;
+  b += ((size_t)r.part_main + (size_t)r.part_side) * 4;
+  int64_t Is = 0;
+  for (int k = 0; k < h->N; ++k) {
+    b += (size_t)h->s[k] * h->s[k] * 4;                // H_k
+    Is = h->I[k] * h->s[k] > Is ? h->I[k] * h->s[k] : Is;
+  }
+  b += (size_t)Is * 4 + tab_ints * sizeof(int);
+  return b;
 }
 
 size_t footprint(const fctn_handle* h) {
@@ -1084,6 +1380,180 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
   return FCTN_OK;
 }
 
+// ---- head-mode association: one sweep ----------------------------------------
+SgTabs sg_tabs(const fctn_handle* h, const SgPlanH& q) {
+  const int* b = h->hr.tabs + q.tab;
+  const int M = q.sh.M, N = q.sh.N;
+  return SgTabs{b, b + M, b + 2 * M, b + 2 * M + N, b + 2 * M + 2 * N, b + 2 * M + 2 * N + q.sh.K};
+}
+
+// C = A (x) B by plan q on stream st (operands passed swapped when the plan says so).
+void run_sg(const fctn_handle* h, const SgPlanH& q, const float* A, const float* B, float* C, float* part,
+            cudaStream_t st) {
+  launch_sgemm(q.sh, sg_tabs(h, q), q.swap ? B : A, q.swap ? A : B, C, part, st);
+}
+double sg_flops(const SgPlanH& q) { return 2.0 * (double)q.sh.M * q.sh.N * q.sh.K; }
+int sg_launches(const SgPlanH& q) { return q.sh.ksplit > 1 ? 2 : 1; }
+
+// M_0 from the present factors 1 .. N-1 (ascending chain).
+int route_build_m0(fctn_handle* h) {
+  HeadRoute& r = h->hr;
+  const float* cur = (const float*)h->Ac[1];
+  for (int i = 0; i < r.nm0; ++i) {
+    float* o = (i == r.nm0 - 1) ? r.M0 : r.U[i % 2];
+    const SgPlanH& q = r.m0[i];
+    LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q), run_sg(h, q, cur, (const float*)h->Ac[i + 2], o, r.pm, h->st));
+    h->launches += sg_launches(q) - 1;
+    cur = o;
+  }
+  r.m0_valid = true;
+  return FCTN_OK;
+}
+
+// Eq. 8 solve with its FP64 refinement for factor k (FP32 operands), the
+// eigendecomposition first unless it already ran on the side stream.
+int route_solve(fctn_handle* h, int k, bool eig_done) {
+  const int I = (int)h->I[k], s = (int)h->s[k];
+  const double lam = h->p.lambda[k], rho = h->p.rho;
+  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
+  const double c0 = sgn * (2.0 + h->p.delta[k]), c1 = -sgn;
+  const double tmin = h->lam_min[k] + rho;
+  const int warm = h->cvalid[k] ? 1 : 0;
+  const double fwd_flops = 2.0 * ((double)I * I * s + 2.0 * (double)I * s * s);
+  const double bwd_flops = 2.0 * (double)I * I * s;
+  const double resid_flops = 2.0 * (double)I * s * s;
+  float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
+  if (!eig_done)
+    LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
+           launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
+                          h->eig_used + k, h->st));
+  const int nref = h->p.refine_steps;
+  LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+         launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
+                              h->st));
+  LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
+         launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
+                              nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
+  for (int r = 0; r < nref; ++r) {
+    if (r > 0)
+      LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
+             launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
+           launch_solve_fwd_f32(h->QT32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
+                                h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
+           launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
+                                c1, nullptr, h->status, h->st));
+  }
+  if (h->p.extrap_alpha != 0.0)
+    LAUNCH(FCTN_KC_SOLVE, 0.0, 0.0,
+           launch_extrap_f32(h->A64[k], h->Aprev, h->p.extrap_alpha, h->p.extrap_beta, (float*)h->Ac[k],
+                             (int64_t)I * s, h->st));
+  h->cvalid[k] = true;
+  h->ver[k]++;
+  return FCTN_OK;
+}
+
+// One sweep in the order 1, ..., N (Algorithm 1's order) by the head-mode
+// association; the Gram chain and the eigendecomposition of factor k run on
+// the side stream beside its right-hand side.
+int route_sweep(fctn_handle* h) {
+  HeadRoute& r = h->hr;
+  const int N = h->N;
+  const bool fork = h->side && h->prof_class < 0;
+  const double rho = h->p.rho;
+  const float* X = (const float*)h->X;
+  for (int t = 0; t < N; ++t)
+    if (!r.hvalid[t]) {
+      LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[t]),
+             run_sg(h, r.hg[t], (const float*)h->Ac[t], (const float*)h->Ac[t], r.H[t], r.pm, h->st));
+      h->launches += sg_launches(r.hg[t]) - 1;
+      r.hvalid[t] = true;
+    }
+  int rc;
+  if (!r.m0_valid && (rc = route_build_m0(h))) return rc;
+  for (int k = 0; k < N; ++k) {
+    const int I = (int)h->I[k], s = (int)h->s[k];
+    const int warm = h->cvalid[k] ? 1 : 0;
+    const double tmin = h->lam_min[k] + rho;
+    if (h->p.extrap_alpha != 0.0 && !h->dry)
+      CK(cudaMemcpyAsync(h->Aprev, h->A64[k], (size_t)I * s * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    // Gram of M_k: chain of the factor Grams H_t, t != k (side stream)
+    cudaStream_t gs = fork ? h->side : h->st;
+    if (fork && !h->dry) {
+      CK(cudaEventRecord(h->ev_fork, h->st));
+      CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    }
+    {
+      int ids[FCTN_MAX_ORDER], n = 0;
+      for (int t = 0; t < N; ++t)
+        if (t != k) ids[n++] = t;
+      const float* cur = r.H[ids[0]];
+      for (int q = 0; q < r.nenv[k]; ++q) {
+        float* o = (q == r.nenv[k] - 1) ? (float*)h->Gs : r.E[q % 2];
+        const SgPlanH& pl = r.env[k][q];
+        if (fork) {
+          LAUNCH_ON(sg_launches(pl), run_sg(h, pl, cur, r.H[ids[q + 1]], o, r.ps, gs));
+        } else {
+          LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(pl), run_sg(h, pl, cur, r.H[ids[q + 1]], o, r.ps, gs));
+          h->launches += sg_launches(pl) - 1;
+        }
+        cur = o;
+      }
+      if (fork) {
+        LAUNCH_ON(1, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
+        LAUNCH_ON(1, launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
+                                    h->eig_cap, tmin, h->status, h->eig_used + k, gs));
+        if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
+      } else {
+        LAUNCH(FCTN_KC_ENV, 0.0, 0.0, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
+      }
+    }
+    // right-hand side X_(k) M_k^T (main stream)
+    if (k == 0) {
+      LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.y0), run_sg(h, r.y0, X, r.M0, r.Yraw, r.pm, h->st));
+      h->launches += sg_launches(r.y0) - 1;
+    } else {
+      const float* cur = r.Zb;
+      for (int q = 0; q < r.nys[k]; ++q) {
+        float* o = (q == r.nys[k] - 1) ? r.Yraw : r.U[q % 2];
+        const SgPlanH& pl = r.ys[k][q];
+        LAUNCH(FCTN_KC_GRAM, 0.0, sg_flops(pl),
+               run_sg(h, pl, cur, (const float*)h->Ac[r.yfac[k][q]], o, r.pm, h->st));
+        h->launches += sg_launches(pl) - 1;
+        cur = o;
+      }
+    }
+    LAUNCH(FCTN_KC_REDUCE, 0.0, 0.0,
+           launch_finish_rhs(r.Yraw, h->A64[k], rho, h->Yd, (float*)h->Ys, (int64_t)I * s, h->st));
+    if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    if ((rc = route_solve(h, k, fork))) return rc;
+    // Gram of the new factor for the later Gram chains
+    LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[k]),
+           run_sg(h, r.hg[k], (const float*)h->Ac[k], (const float*)h->Ac[k], r.H[k], r.pm, h->st));
+    h->launches += sg_launches(r.hg[k]) - 1;
+    if (k == 0) {  // Z = X_(0)^T A_(0) with the new head factor
+      LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.z),
+             run_sg(h, r.z, X, (const float*)h->Ac[0], r.Zb, r.pm, h->st));
+      h->launches += sg_launches(r.z) - 1;
+    }
+  }
+  // M_0 of the new factors 1 .. N-1, then Eq. 10 with F = A_(0) M_0
+  if ((rc = route_build_m0(h))) return rc;
+  GramPlan g = gram_plan(h, 0);
+  const double xb = 2.0 * (double)h->P * 4.0 + (double)r.s0 * r.P0 * 4.0 + (double)h->P / 8.0;
+  LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0,
+         launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
+  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
+  for (int k = 0; k < N; ++k)
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
+           launch_trace_term(h->A64[k], h->I[k], h->s[k], sgn * (2.0 + h->p.delta[k]), -sgn, h->p.lambda[k],
+                             h->traces + 32 * k, h->st));
+  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, xupdate_blocks(g), h->traces, h->N, h->stats, h->st));
+  h->t++;
+  return FCTN_OK;
+}
+
 void sweep_order(const fctn_handle* h, int64_t t_next, int* order) {
   if (h->p.order_policy == FCTN_ORDER_ALTERNATE && h->N >= 4 && t_next % 2 == 0) {
     int m = 0;  // second half first: the first half's intermediate is still valid
@@ -1096,6 +1566,7 @@ void sweep_order(const fctn_handle* h, int64_t t_next, int* order) {
 
 // One sweep: every factor update in the current order, then the X update.
 int sweep_body(fctn_handle* h) {
+  if (h->hr.on) return route_sweep(h);
   int order[FCTN_MAX_ORDER];
   sweep_order(h, h->t + 1, order);
   const int last = order[h->N - 1];
@@ -1156,6 +1627,10 @@ uint64_t sweep_key(const fctn_handle* h) {
   for (int q = 0; q < 2; ++q) {
     bool v = reuse_pairs(h) && half_valid(h, q);
     key |= (uint64_t)(v ? 1 : 0) << (12 + q);
+  }
+  if (h->hr.on) {
+    key |= (uint64_t)(h->hr.m0_valid ? 1 : 0) << 14;
+    for (int k = 0; k < h->N; ++k) key |= (uint64_t)(h->hr.hvalid[k] ? 1 : 0) << (15 + k);
   }
   return key;
 }
@@ -1268,9 +1743,10 @@ int fctn_footprint_bytes(const fctn_params* p, size_t* out) {
   if (!out) return fail(FCTN_E_ARG, "out is NULL");
   fctn_handle tmp;
   fill_shapes(&tmp, p);
-  std::vector<int> tabs;
+  std::vector<int> tabs, rtabs;
+  if ((rc = plan_route(&tmp, &rtabs))) return rc;
   if ((rc = plan_all(&tmp, &tabs, nullptr))) return rc;
-  *out = footprint(&tmp) + tabs.size() * sizeof(int);
+  *out = footprint(&tmp) + tabs.size() * sizeof(int) + route_bytes(&tmp, rtabs.size());
   return FCTN_OK;
 }
 
@@ -1291,9 +1767,9 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     }
     h->own_stream = true;
   }
-  std::vector<int> all_tabs;
+  std::vector<int> all_tabs, route_tabs;
   size_t tab_offs[2 * FCTN_MAX_ORDER];  // pair tables, then FactGram tables
-  if ((rc = plan_all(h, &all_tabs, tab_offs))) {
+  if ((rc = plan_route(h, &route_tabs)) || (rc = plan_all(h, &all_tabs, tab_offs))) {
     if (h->own_stream) cudaStreamDestroy(h->st);
     delete h;
     return rc;
@@ -1349,6 +1825,27 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
   h->stage_bytes = (size_t)(h->P > z.maxfac ? h->P : z.maxfac) * e;
   A_(h->stage, h->stage_bytes);
   A_(h->stage_mask, h->P);
+  if (h->hr.on) {
+    HeadRoute& r = h->hr;
+    A_(r.M0, (size_t)r.s0 * r.P0 * 4);
+    A_(r.Zb, (size_t)r.s0 * r.P0 * 4);
+    A_(r.U[0], (size_t)r.u_elems * 4);
+    A_(r.U[1], (size_t)r.u_elems * 4);
+    A_(r.E[0], (size_t)r.e_elems * 4);
+    A_(r.E[1], (size_t)r.e_elems * 4);
+    A_(r.pm, (size_t)r.part_main * 4);
+    A_(r.ps, (size_t)r.part_side * 4);
+    for (int k = 0; k < h->N; ++k) A_(r.H[k], (size_t)h->s[k] * h->s[k] * 4);
+    A_(r.Yraw, (size_t)z.Is * 4);
+    A_(r.tabs, route_tabs.size() * sizeof(int));
+    cudaError_t ce = cudaMemcpy(r.tabs, route_tabs.data(), route_tabs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      free_all(h);
+      if (h->own_stream) cudaStreamDestroy(h->st);
+      delete h;
+      return fail(FCTN_E_CUDA, "fctn_create: %s", cudaGetErrorString(ce));
+    }
+  }
   {
     // index tables of the pair forms
     std::vector<int>& all = all_tabs;
@@ -1376,7 +1873,7 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     }
   }
 #undef A_
-  bool any_fact = false;
+  bool any_fact = h->hr.on;  // the route's Gram chains run on the side stream too
   for (int k = 0; k < h->N; ++k) any_fact = any_fact || h->fg[k].use;
   if (any_fact) {
     cudaError_t ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
@@ -1656,6 +2153,8 @@ int fctn_set_factors(fctn_handle* h, const void* const* factors, int where) {
   h->t = 0;
   h->Tvalid[0] = h->Tvalid[1] = false;
   for (int k = 0; k < h->N; ++k) h->cvalid[k] = false;
+  h->hr.m0_valid = false;
+  for (int k = 0; k < h->N; ++k) h->hr.hvalid[k] = false;
   return FCTN_OK;
 }
 

@@ -117,6 +117,36 @@ int fctn_internal_fail(int code, const char* msg);
 int fctn_internal_sweep_async(fctn_handle* h, double* pinned);
 cudaStream_t fctn_internal_stream(fctn_handle* h);
 
+// ---- kernels_sgemm.cu -------------------------------------------------------
+// Table-driven FP32 contraction C[cm[m] + cn[n]] = sum_k A[am[m] + ak[k]] B[bn[n] + bk[k]]
+// (offsets in elements, all < 2^31); a K split writes dense partials
+// (ksplit x M x N) that are summed in split order.
+struct SgShape {
+  int M, N, K, ksplit, kchunk;
+  int a_mfast, b_nfast;  // loader lanes run along m (n) when that digit is contiguous in A (B), else along k
+};
+struct SgTabs {
+  const int *am, *cm, *bn, *cn, *ak, *bk;
+};
+void sg_shape(int M, int N, int K, SgShape* sh);
+size_t sg_part_elems(const SgShape& sh);
+void launch_sgemm(const SgShape& sh, const SgTabs& t, const float* A, const float* B, float* C, float* part,
+                  cudaStream_t st);
+// Yd = Yraw + rho A_old, Ys = float(Yd) (n = I s); Gd = double(Gs) after symmetrising Gs.
+void launch_finish_rhs(const float* Yraw, const double* Aold, double rho, double* Yd, float* Ys, int64_t n,
+                       cudaStream_t st);
+void launch_finish_gram(float* Gs, double* Gd, int s, cudaStream_t st);
+// Transposed / padded copies (dst leading dimension ldd), optionally rounded
+// to TF32 or converted to BF16: operands of the tensor-core GEMMs.
+void launch_transpose_f32(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
+                          int round_tf32, cudaStream_t st);
+void launch_copy_f32(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
+                     int round_tf32, cudaStream_t st);
+void launch_transpose_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst,
+                           int64_t ldd, cudaStream_t st);
+void launch_copy_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst, int64_t ldd,
+                      cudaStream_t st);
+
 // ---- kernels_quality.cu ----------------------------------------------------
 // PSNR and SSIM (Sec. 4) of X against the truth Y, both (rows x ncol)
 // row-major with rows = I_1 I_2 (slice index = column); out = {psnr, ssim}.

@@ -85,10 +85,12 @@ def test_reuse_beyond_order_four_is_planned(F):
 
 def test_rhs_ctas_sets_the_split(F):
     """A larger right-hand-side CTA budget splits M_k's columns more finely:
-    more per-split partials, so a larger footprint; 0 is the built-in rule."""
-    small = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32", rhs_ctas=16))
-    rule = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32"))
-    large = F.fctn_footprint_bytes(_params(F, (256, 256, 31), r=8, precision="fp32", rhs_ctas=2432))
+    more per-split partials, so a larger footprint; 0 is the built-in rule.
+    (Merged tensors formed per factor: reuse off.)"""
+    kw = dict(r=8, precision="fp32", reuse=False)
+    small = F.fctn_footprint_bytes(_params(F, (256, 256, 31), rhs_ctas=16, **kw))
+    rule = F.fctn_footprint_bytes(_params(F, (256, 256, 31), **kw))
+    large = F.fctn_footprint_bytes(_params(F, (256, 256, 31), rhs_ctas=2432, **kw))
     assert small < large
     assert small <= rule <= large
 

@@ -1,0 +1,76 @@
+"""The head-mode association of a sweep (FP32 / TF32 / BF16 with reuse and
+the plain order 1..N) against the FP64 oracle and against the merged-tensor
+route of the same sweep order.
+
+The head route evaluates the products of Eq. 5 in another association: the
+merged tensor M_1 of every factor but the first serves the first factor's
+right-hand side and the reconstruction F of Eq. 10, Z = X_(1)^T A_(1) serves
+every other right-hand side, and every Gram M_k M_k^T comes from the Grams of
+the factors.  Exact arithmetic gives the oracle's iterates; FP32 stays within
+1e-4 (relative Frobenius error per result) after the fixed sweeps.
+"""
+import numpy as np
+import pytest
+
+from tests.util import gpu_run, inputs, oracle_run, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2510_22506_gb300 import fctn
+    return fctn
+
+
+CASES = [
+    ((48, 40, 9), 4, None, 10),          # N = 3, ragged against every tile
+    ((13, 7, 3, 5), 3, (3, 2), 8),       # N = 4, ragged, capped bonds of the size-3 mode
+    ((30, 24, 3, 7), 3, (3, 2), 8),
+    ((5, 4, 3, 4, 3), 2, None, 6),       # N = 5
+    ((64, 33, 17), 8, None, 6),          # s = 64, several K chunks
+]
+
+
+@pytest.mark.parametrize("dims,r,cap,sweeps", CASES)
+def test_head_route_fp32_matches_oracle(F, dims, r, cap, sweeps):
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=70, noise=0.0, cap=cap, dtype=np.float32)
+    st, hist = oracle_run(d, sweeps, reuse=True, policy="plain")
+    g = gpu_run(F, d, sweeps, precision="fp32", reuse=True, policy="plain")
+    e = rel(g["X"], st.X)
+    assert e <= 1e-4, e
+    for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
+        assert rel(a, b) <= 1e-4, (k, rel(a, b))
+    assert abs(g["stats"]["objective"] - hist[-1]["objective"]) <= 1e-4 * abs(hist[-1]["objective"])
+
+
+@pytest.mark.parametrize("dims,r,cap", [((30, 24, 3, 7), 3, (3, 2)), ((20, 16, 12), 5, None)])
+def test_head_route_agrees_with_merged_route(F, dims, r, cap):
+    """Same order, reuse on (head route) and off (merged tensors from scratch):
+    the two differ only by association."""
+    d = inputs(None, dims=dims, r=r, p=0.25, idx=71, noise=0.0, cap=cap, dtype=np.float32)
+    a = gpu_run(F, d, 6, precision="fp32", reuse=True, policy="plain")
+    b = gpu_run(F, d, 6, precision="fp32", reuse=False, policy="plain")
+    assert rel(a["X"], b["X"]) <= 1e-4
+    for x, y in zip(a["factors"], b["factors"]):
+        assert rel(x, y) <= 1e-4
+
+
+def test_head_route_graph_and_eager_identical(F):
+    """Graph-captured sweeps launch the same kernels as eager ones."""
+    d = inputs(None, dims=(30, 24, 3, 7), r=3, p=0.3, idx=72, noise=0.0, cap=(3, 2), dtype=np.float32)
+    p = F.make_params(d["dims"], d["R"], precision="fp32", reuse=True, order_policy="plain")
+    out = []
+    for graphs in (True, False):
+        h = F.fctn_create(p)
+        try:
+            F.fctn_set_graphs(h, graphs)
+            F.fctn_set_data(h, np.ascontiguousarray(d["Y"]), np.ascontiguousarray(d["mask"].astype(np.uint8)))
+            F.fctn_set_factors(h, [np.ascontiguousarray(a) for a in d["init"]])
+            F.fctn_pam_sweep(h, 5)
+            X = np.empty(d["dims"], dtype=np.float32)
+            F.fctn_get_X(h, X)
+            out.append(X)
+        finally:
+            F.fctn_destroy(h)
+    np.testing.assert_array_equal(out[0], out[1])
