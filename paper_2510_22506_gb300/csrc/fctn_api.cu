@@ -156,6 +156,7 @@ struct fctn_handle {
   int* status = nullptr;
   int* eig_used = nullptr;
   int eig_cap = 60;  // Jacobi sweep cap per eigendecomposition (fctn_params.eig_max_sweeps)
+  float* eig_rec = nullptr;  // rotation blocks of the large FP32 eigensolver (128 < s <= 224)
   void* Ck[FCTN_MAX_ORDER] = {};
   bool cvalid[FCTN_MAX_ORDER] = {};
   double lam_min[FCTN_MAX_ORDER] = {};
@@ -1196,7 +1197,12 @@ size_t footprint(const fctn_handle* h) {
   }
   b += 4 * z.Is * 8 + z.ss * 8;                           // Gd, Yd, Rd, previous factor
   size_t se = h->f64 ? 8 : 4;
-  b += (2 * z.ss + z.maxs + 5 * z.Is) * se + 3 * z.ss * se;  // solve buffers + eigensolver work
+  b += (2 * z.ss + z.maxs + 5 * z.Is) * se + 4 * z.ss * se;  // solve buffers + eigensolver work
+  if (!h->f64) {
+    size_t rec = 0;
+    for (int k = 0; k < h->N; ++k) rec = std::max(rec, eig_record_floats((int)h->s[k]));
+    b += rec * 4;  // rotation record of the large eigensolver
+  }
   for (int k = 0; k < h->N; ++k) b += h->s[k] * h->s[k] * se;  // warm-start eigenvectors
   b += (z.red_blocks * 3 + h->N * 32 + 8) * 8 + 16;
   int64_t stage = h->P > z.maxfac ? h->P : z.maxfac;
@@ -1283,8 +1289,9 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       } else {
         LAUNCH_ON(3, launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
                                           (float*)h->Gs, fst));
-        LAUNCH_ON(1, launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                    h->eig_cap, tmin, h->status, h->eig_used + k, fst));
+        LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
+                  launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
+                                 h->eig_cap, tmin, h->status, h->eig_used + k, fst, h->eig_rec));
       }
       if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
     } else if (h->f64) {
@@ -1345,7 +1352,8 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     if (!fork)
       LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
              launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
-                            h->eig_used + k, h->st));
+                            h->eig_used + k, h->st, h->eig_rec));
+    if (!fork) h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
     const int nref = h->p.refine_steps;
     LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
            launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
@@ -1423,10 +1431,12 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
   const double bwd_flops = 2.0 * (double)I * I * s;
   const double resid_flops = 2.0 * (double)I * s * s;
   float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
-  if (!eig_done)
+  if (!eig_done) {
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
-                          h->eig_used + k, h->st));
+                          h->eig_used + k, h->st, h->eig_rec));
+    h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
+  }
   const int nref = h->p.refine_steps;
   LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
          launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
@@ -1502,8 +1512,9 @@ int route_sweep(fctn_handle* h) {
       }
       if (fork) {
         LAUNCH_ON(1, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
-        LAUNCH_ON(1, launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                    h->eig_cap, tmin, h->status, h->eig_used + k, gs));
+        LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
+                  launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
+                                 h->eig_cap, tmin, h->status, h->eig_used + k, gs, h->eig_rec));
         if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
       } else {
         LAUNCH(FCTN_KC_ENV, 0.0, 0.0, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
@@ -1815,7 +1826,12 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
   A_(h->Z, z.Is * se);
   A_(h->W2, z.Is * se);
   A_(h->Rs, z.Is * 4);
-  A_(h->gwork, 3 * z.ss * se);
+  A_(h->gwork, 4 * z.ss * se);
+  if (!h->f64) {
+    size_t rec = 0;
+    for (int k = 0; k < h->N; ++k) rec = std::max(rec, eig_record_floats((int)h->s[k]));
+    if (rec) A_(h->eig_rec, rec * 4);
+  }
   A_(h->status, 16);
   A_(h->eig_used, FCTN_MAX_ORDER * sizeof(int));
   for (int k = 0; k < h->N; ++k) A_(h->Ck[k], h->s[k] * h->s[k] * se);

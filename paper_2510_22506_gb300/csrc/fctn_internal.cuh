@@ -186,9 +186,13 @@ void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint
 // C (s x s, column j = eigenvector j) is read as the warm start when warm != 0
 // and overwritten with the result; Phi gets the eigenvalues.  work: 3 s^2.
 // *status: FCTN_E_SINGULAR if min Phi + tmin <= 0; *used: sweeps taken
-// (max_sweeps if the sweep limit ran out, which is not an error).
+// (minus the sweeps taken if the sweep limit ran out, which is not an error).
+// With `rec` (eig_record_floats(s) floats) and 128 < s <= 224 the FP32 route
+// is the large block-ordered Jacobi (eig_launches kernels, work 4 s^2).
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                    double tmin, int* status, int* used, cudaStream_t st);
+                    double tmin, int* status, int* used, cudaStream_t st, float* rec = nullptr);
+size_t eig_record_floats(int s);
+int eig_launches(int s, int warm, int recorded);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
 // Eq. 8 by row blocks.  fwd: W = (((Q^T R) C) / T) C^T.  bwd: A = Q W into

@@ -741,6 +741,462 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
   }
 }
 
+// ------------------------------ block-ordered Jacobi, FP32, 128 < s <= 224 ----
+// The method of k_eig3 for Grams whose B and V^T do not fit on one SM
+// together.  B = V^T G V alone stays in shared memory (224 x 228 floats at
+// most); the warm-start products (one Newton-Schulz step V = V0 (3I -
+// V0^T V0) / 2, then B = V^T (G V)) run before it as multi-CTA products
+// (k_mm_small), and the rotation blocks U of every outer round are recorded
+// in global memory instead of being applied to V^T on chip.  k_eig_apply then
+// forms C = V J_1 J_2 ... row by row over many CTAs: a row of V meets every
+// round's 8 x 8 blocks in order, independently of the other rows.
+// Rotation test: rotate iff B_pq^2 > tol^2 (|B_pp| + t)(|B_qq| + t) + floor^2
+// with t = max(tmin, 0), the smallest shift lambda Lambda_i + rho of Eq. 8:
+// the solve divides by Phi_j + lambda Lambda_i + rho, so an off-diagonal B_pq
+// perturbs it by B_pq / sqrt((Phi_p + t)(Phi_q + t)) at most, and pairs of
+// eigenvalues far below the shift need no more accuracy than that.
+constexpr int EIG4_MAX = 224;
+constexpr int EJ4_NT = 512;          // 128 registers a thread: the 8 x 4 / 4 x 8 tiles stay unspilled
+constexpr int EJ4_TPT = 4;           // row / column tasks per thread: (224 / 8) (224 / 4) <= 4 * 512
+constexpr int EIG4_REC_SWEEPS = 16;  // sweeps whose rotation blocks fit the record
+
+// C = ca op(A) Bm + cb D for s x s row-major matrices (op(A) = A or A^T),
+// one 32 x 32 tile per CTA of 256 threads (2 x 2 outputs each).
+template <bool TA>
+__global__ void __launch_bounds__(256) k_mm_small(const float* __restrict__ A, const float* __restrict__ Bm,
+                                                  const float* __restrict__ D, float* __restrict__ C, int s, float ca,
+                                                  float cb) {
+  __shared__ float As[32][33], Bs[32][33];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k0 = 0; k0 < s; k0 += 32) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      // As[r][c] = op(A)[i0 + r][k0 + c]
+      const int ai = i0 + r, ak = k0 + c;
+      float av = 0.f;
+      if (ai < s && ak < s) av = TA ? A[(int64_t)ak * s + ai] : A[(int64_t)ai * s + ak];
+      As[r][c] = av;
+      const int bk = k0 + r, bj = j0 + c;
+      Bs[r][c] = (bk < s && bj < s) ? Bm[(int64_t)bk * s + bj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float a0 = As[ty * 2][k], a1 = As[ty * 2 + 1][k];
+      const float b0 = Bs[k][tx * 2], b1 = Bs[k][tx * 2 + 1];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ty * 2 + a, j = j0 + tx * 2 + b;
+      if (i < s && j < s) {
+        float v = ca * acc[a][b];
+        if (D) v = fmaf(cb, D[(int64_t)i * s + j], v);
+        C[(int64_t)i * s + j] = v;
+      }
+    }
+}
+
+__device__ __forceinline__ float ej_rot_shift(float a, float b, float g, float tol2, float floor2, float tsh,
+                                              float& c, float& sn, float& t) {
+  const float ab = (fabsf(a) + tsh) * (fabsf(b) + tsh), g2 = g * g;
+  const bool rot = g2 > tol2 * ab + floor2;
+  const float d = b - a, tg = 2.f * g;
+  const float h = fmaf(d, d, tg * tg);
+  const float hy = h * rsqrtf(h);
+  const float tt = __fdividef(d >= 0.f ? tg : -tg, fabsf(d) + hy);
+  const float x = fmaf(tt, tt, 1.f);
+  const float y = rsqrtf(x);
+  const float cc = y * fmaf(-0.5f * x * y, y, 1.5f);
+  c = rot ? cc : 1.f;
+  sn = rot ? cc * tt : 0.f;
+  t = rot ? tt : 0.f;
+  return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
+}
+
+// ej_round with the shifted rotation test (see k_eig4).
+template <bool W, int T>
+__device__ __forceinline__ void ej4_round(float* __restrict__ Sw, float* __restrict__ Uw, int hl, float tol2,
+                                          float floor2, float tsh, unsigned& cnt, float& cmu) {
+  const int k = hl >> 2, l = hl & 3;
+  int pk, qk, pl, ql;
+  ej_pair(W, T, k, pk, qk);
+  ej_pair(W, T, l, pl, ql);
+  const float ak = Sw[pk * 9], bk = Sw[qk * 9], gk = Sw[pk * 8 + qk];
+  const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
+  const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
+  const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
+  const float u00 = Uw[k * 8 + pl], u01 = Uw[k * 8 + ql];
+  const float u10 = Uw[(k + 4) * 8 + pl], u11 = Uw[(k + 4) * 8 + ql];
+  __syncwarp();
+  float ck, sk, tk, cl, sl, tl;
+  const float mu = ej_rot_shift(ak, bk, gk, tol2, floor2, tsh, ck, sk, tk);
+  ej_rot_shift(al, bl, gl, tol2, floor2, tsh, cl, sl, tl);
+  const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+  const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+  float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
+  float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
+  const bool dg = (k == l) && mu >= 0.f;
+  if (dg) {
+    z00 = fmaf(-tk, gk, ak);
+    z11 = fmaf(tk, gk, bk);
+    z01 = 0.f;
+    z10 = 0.f;
+    ++cnt;
+    cmu = fmaxf(cmu, mu);
+  }
+  Sw[pk * 8 + pl] = z00;
+  Sw[pk * 8 + ql] = z01;
+  Sw[qk * 8 + pl] = z10;
+  Sw[qk * 8 + ql] = z11;
+  Uw[k * 8 + pl] = cl * u00 - sl * u01;
+  Uw[k * 8 + ql] = sl * u00 + cl * u01;
+  Uw[(k + 4) * 8 + pl] = cl * u10 - sl * u11;
+  Uw[(k + 4) * 8 + ql] = sl * u10 + cl * u11;
+  __syncwarp();
+}
+
+// Jacobi sweeps on B (s x s in global memory, from the warm-start products
+// or G itself).  Records, for outer round n (counted over all sweeps), the
+// blocks U of the subproblems that rotated (entries RoundStart[n] ..
+// RoundStart[n + 1] - 1 of Urec, 64 floats each, and of PQrec, their block
+// pair); a subproblem without rotations has U = I and is neither recorded
+// nor applied to B.  *nrounds gets the number of rounds.
+__global__ void __launch_bounds__(EJ4_NT) k_eig4(const float* __restrict__ Bin, float* __restrict__ Phi, int s,
+                                                 int max_sweeps, double tmin, float* __restrict__ Urec,
+                                                 int* __restrict__ PQrec, int* __restrict__ RoundStart,
+                                                 int* __restrict__ nrounds, int* status, int* sweeps_used) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int m = (s + 7) & ~7, sp = m + 4, nb = m / 4, nsub = m / 8, nsub2 = (nsub + 1) / 2;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  float* B = (float*)sm;
+  float* SC = B + m * sp;
+  __shared__ float red[32];
+  __shared__ unsigned wrot[32], wmu[32];
+  __shared__ int pq[32];
+  __shared__ int rotf[32];   // subproblem rotated in this outer round
+  __shared__ int slot[32];   // its entry in the record, or -1
+  __shared__ int nrec_s;     // entries recorded so far
+  float fr = 0.f;
+  if (tid == 0) nrec_s = 0;
+  for (int r = warp; r < m; r += nwarp)
+    for (int j = lane; j < m; j += 32) {
+      float v = 0.f;
+      if (r < s && j < s) v = 0.5f * (Bin[(int64_t)r * s + j] + Bin[(int64_t)j * s + r]);
+      B[r * sp + j] = v;
+      fr = fmaf(v, v, fr);
+    }
+  fr = warp_sum(fr);
+  if (lane == 0) red[warp] = fr;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < nwarp; ++w) t += red[w];
+    red[0] = sqrtf(t);
+  }
+  __syncthreads();
+  const float eps = FLT_EPSILON;
+  const float tol = sqrtf((float)(s > 1 ? s : 1)) * eps;
+  const float tol2 = tol * tol;
+  const float floor_abs = eps * red[0] * rsqrtf((float)(s > 0 ? s : 1));
+  const float floor2 = floor_abs * floor_abs;
+  const float tsh = tmin > 0.0 ? (float)tmin : 0.f;
+  const int nq = m / 4, nr1 = nsub * nq;
+  int rt[EJ4_TPT], ct[EJ4_TPT];
+#pragma unroll
+  for (int i = 0; i < EJ4_TPT; ++i) {
+    const int t1 = tid + i * nt;
+    rt[i] = t1 < nr1 ? (t1 / nq) | (t1 % nq) << 8 : -1;
+    ct[i] = t1 < nr1 ? (t1 % nsub) | (t1 / nsub) << 8 : -1;
+  }
+  unsigned cnt = 0;
+  float cmu = 0.f;
+  int sweep = 0, nround = 0;
+  bool converged = (s <= 1);
+  const int sweep_cap = max_sweeps < EIG4_REC_SWEEPS ? max_sweeps : EIG4_REC_SWEEPS;
+  for (; sweep < sweep_cap && !converged; ++sweep) {
+    for (int r = 0; r < nb - 1; ++r, ++nround) {
+      for (int sw = warp; sw < nsub2; sw += nwarp) {
+        const int sub = 2 * sw + (lane >> 4), hl = lane & 15;
+        const bool real = sub < nsub;
+        float* Sw = SC + (real ? sub : nsub) * EJ_SUB;
+        float* Uw = Sw + 64;
+        int P = 0, Q = 0;
+        if (real) {
+          round_pair(nb, r, sub, P, Q);
+          if (hl == 0) pq[sub] = P | Q << 16;
+        }
+        for (int e = hl; e < 64; e += 16) {
+          const int i = e >> 3, j = e & 7;
+          const int gi = i < 4 ? 4 * P + i : 4 * Q + i - 4, gj = j < 4 ? 4 * P + j : 4 * Q + j - 4;
+          Sw[e] = real ? B[gi * sp + gj] : 0.f;
+          Uw[e] = (i == j) ? 1.f : 0.f;
+        }
+        __syncwarp();
+        const unsigned cnt0 = cnt;
+        if (r == 0) {
+          ej4_round<true, 0>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+          ej4_round<true, 1>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+          ej4_round<true, 2>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        }
+        ej4_round<false, 0>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 1>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 2>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 3>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        const unsigned any = __ballot_sync(0xffffffffu, cnt != cnt0);
+        if (real && hl == 0) rotf[sub] = ((any >> (lane & 16)) & 0xffffu) != 0u;
+      }
+      if (r == nb - 2 && warp < nsub2) {
+        const unsigned cn = __reduce_add_sync(0xffffffffu, cnt);
+        const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(cmu));
+        if (lane == 0) {
+          wrot[warp] = cn;
+          wmu[warp] = mx;
+        }
+        cnt = 0;
+        cmu = 0.f;
+      }
+      __syncthreads();
+      // record the blocks of the subproblems that rotated (k_eig_apply);
+      // round n's entries start at RoundStart[n]
+      if (warp == 0) {
+        const bool f = lane < nsub && rotf[lane];
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int base = nrec_s;
+        if (lane < nsub) slot[lane] = f ? base + __popc(bal & ((1u << lane) - 1u)) : -1;
+        if (lane == 0) {
+          RoundStart[nround] = base;
+          RoundStart[nround + 1] = base + __popc(bal);
+        }
+        __syncwarp();
+        if (lane == 0) nrec_s = base + __popc(bal);
+      }
+      __syncthreads();
+      for (int e = tid; e < nsub * 64; e += nt) {
+        const int a = e >> 6, q = slot[a];
+        if (q >= 0) Urec[(int64_t)q * 64 + (e & 63)] = SC[a * EJ_SUB + 64 + (e & 63)];
+      }
+      for (int a = tid; a < nsub; a += nt)
+        if (slot[a] >= 0) PQrec[slot[a]] = pq[a];
+      // rows: B[S_a, quad] <- U_a^T B[S_a, quad] outside S_a's own columns
+#pragma unroll
+      for (int i = 0; i < EJ4_TPT; ++i) {
+        if (rt[i] < 0) break;
+        const int a = rt[i] & 0xff, cq = rt[i] >> 8;
+        const int P = pq[a] & 0xffff, Q = pq[a] >> 16;
+        if (cq == P || cq == Q || !rotf[a]) continue;  // U_a = I: nothing to apply
+        float* Mx = B + 4 * cq;
+        const float* Ua = SC + a * EJ_SUB + 64;
+        float acc[8][4];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) acc[o][0] = acc[o][1] = acc[o][2] = acc[o][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const float4 x = *(const float4*)(Mx + (kk < 4 ? 4 * P + kk : 4 * Q + kk - 4) * sp);
+          const float4 ua = *(const float4*)(Ua + kk * 8), ub = *(const float4*)(Ua + kk * 8 + 4);
+          const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            acc[o][0] = fmaf(u[o], x.x, acc[o][0]);
+            acc[o][1] = fmaf(u[o], x.y, acc[o][1]);
+            acc[o][2] = fmaf(u[o], x.z, acc[o][2]);
+            acc[o][3] = fmaf(u[o], x.w, acc[o][3]);
+          }
+        }
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          *(float4*)(Mx + (o < 4 ? 4 * P + o : 4 * Q + o - 4) * sp) =
+              make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+      }
+      __syncthreads();
+      // columns: B[quad, S_b] <- B[quad, S_b] U_b; the superblock from its warp
+#pragma unroll
+      for (int i = 0; i < EJ4_TPT; ++i) {
+        if (ct[i] < 0) break;
+        const int b = ct[i] & 0xff, rq = ct[i] >> 8;
+        if (!rotf[b]) continue;  // U_b = I and the superblock is unchanged
+        const int P = pq[b] & 0xffff, Q = pq[b] >> 16;
+        const float* Sb = SC + b * EJ_SUB;
+        float* row0 = B + 4 * rq * sp;
+        if (rq == P || rq == Q) {
+          const int l0 = rq == P ? 0 : 4;
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            *(float4*)(row0 + ii * sp + 4 * P) = *(const float4*)(Sb + (l0 + ii) * 8);
+            *(float4*)(row0 + ii * sp + 4 * Q) = *(const float4*)(Sb + (l0 + ii) * 8 + 4);
+          }
+        } else {
+          float w[4][8];
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            const float4 w0 = *(const float4*)(row0 + ii * sp + 4 * P), w1 = *(const float4*)(row0 + ii * sp + 4 * Q);
+            w[ii][0] = w0.x;
+            w[ii][1] = w0.y;
+            w[ii][2] = w0.z;
+            w[ii][3] = w0.w;
+            w[ii][4] = w1.x;
+            w[ii][5] = w1.y;
+            w[ii][6] = w1.z;
+            w[ii][7] = w1.w;
+          }
+          const float* Ub = Sb + 64;
+          float o[4][8];
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o[ii][j] = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const float4 ua = *(const float4*)(Ub + kk * 8), uc = *(const float4*)(Ub + kk * 8 + 4);
+            const float u[8] = {ua.x, ua.y, ua.z, ua.w, uc.x, uc.y, uc.z, uc.w};
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) o[ii][j] = fmaf(w[ii][kk], u[j], o[ii][j]);
+          }
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            *(float4*)(row0 + ii * sp + 4 * P) = make_float4(o[ii][0], o[ii][1], o[ii][2], o[ii][3]);
+            *(float4*)(row0 + ii * sp + 4 * Q) = make_float4(o[ii][4], o[ii][5], o[ii][6], o[ii][7]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    unsigned cn = 0, mx = 0;
+    for (int w = 0; w < min(nsub2, nwarp); ++w) {
+      cn += wrot[w];
+      mx = max(mx, wmu[w]);
+    }
+    converged = (cn == 0) || (__uint_as_float(mx) < tol);
+  }
+  for (int j = tid; j < s; j += nt) Phi[j] = B[j * sp + j];
+  __syncthreads();
+  if (tid == 0) {
+    float mn = Phi[0];
+    for (int j = 1; j < s; ++j) mn = fminf(mn, Phi[j]);
+    if (!((double)mn + tmin > 0.0)) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
+    *nrounds = nround;
+    if (sweeps_used) *sweeps_used = converged ? sweep : -sweep;
+  }
+}
+
+// C = V J_1 J_2 ... J_n (n = *nrounds): row r of V (or of I when V is null)
+// meets every recorded round's blocks in order.  A warp holds one row in
+// shared memory and its lanes take the round's recorded blocks; the CTA
+// stages each round's blocks once for its eight rows, the next round's
+// blocks loaded into registers while the current round is applied.
+__global__ void __launch_bounds__(256) k_eig_apply(const float* __restrict__ V, const float* __restrict__ Urec,
+                                                   const int* __restrict__ PQrec, const int* __restrict__ RoundStart,
+                                                   const int* __restrict__ nrounds, float* __restrict__ C, int s) {
+  constexpr int MAXB = EIG4_MAX / 8;
+  __shared__ float row[8][EIG4_MAX + 4];
+  __shared__ float Us[2][MAXB][65];  // stride 65: lanes on different blocks hit different banks
+  __shared__ int pqs[2][MAXB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = (s + 7) & ~7;
+  const int r = blockIdx.x * 8 + warp;
+  for (int j = lane; j < m; j += 32)
+    row[warp][j] = (r < s && j < s) ? (V ? V[(int64_t)r * s + j] : (j == r ? 1.f : 0.f)) : 0.f;
+  const int n = *nrounds;
+  // register staging of one round: up to MAXB * 64 floats over 256 threads
+  constexpr int PER = (MAXB * 64 + 255) / 256;
+  float stage[PER];
+  int sp_cnt = 0, sp_pq = 0;
+  auto fetch = [&](int q) {
+    const int b = RoundStart[q], cnt = RoundStart[q + 1] - b;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + 256 * i;
+      stage[i] = e < cnt * 64 ? Urec[(int64_t)b * 64 + e] : 0.f;
+    }
+    sp_cnt = cnt;
+    sp_pq = threadIdx.x < cnt ? PQrec[b + threadIdx.x] : 0;
+  };
+  if (n > 0) fetch(0);
+  for (int q = 0; q < n; ++q) {
+    const int buf = q & 1, cnt = sp_cnt;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int e = threadIdx.x + 256 * i;
+      if (e < cnt * 64) Us[buf][e >> 6][e & 63] = stage[i];
+    }
+    if (threadIdx.x < cnt) pqs[buf][threadIdx.x] = sp_pq;
+    __syncthreads();
+    if (q + 1 < n) fetch(q + 1);  // in flight while this round is applied
+    for (int a = lane; a < cnt; a += 32) {
+      const int P = pqs[buf][a] & 0xffff, Q = pqs[buf][a] >> 16;
+      float x[8], y[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = row[warp][i < 4 ? 4 * P + i : 4 * Q + i - 4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc = fmaf(x[i], Us[buf][a][i * 8 + j], acc);
+        y[j] = acc;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) row[warp][j < 4 ? 4 * P + j : 4 * Q + j - 4] = y[j];
+    }
+    __syncwarp();
+  }
+  if (r < s)
+    for (int j = lane; j < s; j += 32) C[(int64_t)r * s + j] = row[warp][j];
+}
+
+// X = I + first-order eigenvector correction of a nearly diagonal symmetric B:
+// X_pq = B_pq / (B_qq - B_pp) for p != q when the gap exceeds 8 |B_pq|, else
+// 0.  V X holds columns v_q + sum_p X_pq v_p, which after re-orthonormalising
+// leave off-diagonal entries of order B_pq^2 / gap; close pairs are left to
+// Jacobi.  X is antisymmetric off the diagonal, so (V X)^T (V X) = I + X^T X;
+// when ||X||_F > 1/4 the step is dropped (X = I), since one Newton-Schulz
+// step then no longer restores orthonormality to working precision.  One CTA.
+__global__ void __launch_bounds__(1024) k_first_order(const float* __restrict__ B, float* __restrict__ X, int s) {
+  __shared__ float red[32];
+  const int64_t n = (int64_t)s * s;
+  float ss = 0.f;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const int p = (int)(e / s), q = (int)(e - (int64_t)p * s);
+    float v = 1.f;
+    if (p != q) {
+      const float bpq = 0.5f * (B[e] + B[(int64_t)q * s + p]);
+      const float gap = B[(int64_t)q * s + q] - B[(int64_t)p * s + p];
+      v = fabsf(gap) > 8.f * fabsf(bpq) ? bpq / gap : 0.f;
+      ss = fmaf(v, v, ss);
+    }
+    X[e] = v;
+  }
+  ss = warp_sum(ss);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  if (red[0] > 1.f / 16.f)
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const int p = (int)(e / s), q = (int)(e - (int64_t)p * s);
+      X[e] = p == q ? 1.f : 0.f;
+    }
+}
+
+size_t eig4_smem(int s) {
+  const int m = (s + 7) & ~7, sp = m + 4;
+  return (size_t)(m * sp + (m / 8 + 1) * EJ_SUB) * sizeof(float);
+}
+
 size_t eig3_smem(int s) {
   const int m = (s + 7) & ~7, sp = m + 4;
   return (size_t)(3 * m * sp + (m / 8 + 1) * EJ_SUB) * sizeof(float);
@@ -758,6 +1214,43 @@ EigCfg eig_cfg(int s, int elem) {
   if (2 * mat <= lim) return {1, 1, 2 * mat};
   if (mat <= lim) return {1, 0, mat};
   return {0, 0, 0};
+}
+
+// FP32 Grams with 128 < s <= 224: warm-start products (4 multi-CTA launches),
+// k_eig4, k_eig_apply.  work: 4 s^2 floats; rec: eig_record_floats(s) floats.
+void eig_big(const float* G, float* C, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+             double tmin, int* status, int* used, cudaStream_t st) {
+  const int m = (s + 7) & ~7, nsub = m / 8;
+  const int64_t ss = (int64_t)s * s;
+  float *W = work, *V = work + ss, *T = work + 2 * ss, *B = work + 3 * ss;
+  const int rounds = EIG4_REC_SWEEPS * (m / 4 - 1);
+  float* Urec = rec;
+  int* PQrec = (int*)(rec + (int64_t)rounds * nsub * 64);
+  int* RoundStart = PQrec + rounds * nsub;
+  int* nr = RoundStart + rounds + 1;
+  const dim3 g2((s + 31) / 32, (s + 31) / 32);
+  if (warm) {
+    k_mm_small<true><<<g2, 256, 0, st>>>(C, C, nullptr, W, s, 1.f, 0.f);    // W = V0^T V0
+    k_mm_small<false><<<g2, 256, 0, st>>>(C, W, C, V, s, -0.5f, 1.5f);      // V = 1.5 V0 - 0.5 V0 W
+    k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
+    k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
+    // first-order correction of the well-separated pairs, then once more
+    // one Newton-Schulz step and B = V^T G V
+    k_first_order<<<1, 1024, 0, st>>>(B, W, s);                               // X
+    k_mm_small<false><<<g2, 256, 0, st>>>(V, W, nullptr, T, s, 1.f, 0.f);   // V1 = V X
+    k_mm_small<true><<<g2, 256, 0, st>>>(T, T, nullptr, W, s, 1.f, 0.f);    // W = V1^T V1
+    k_mm_small<false><<<g2, 256, 0, st>>>(T, W, T, V, s, -0.5f, 1.5f);      // V = 1.5 V1 - 0.5 V1 W
+    k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
+    k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
+  }
+  static bool attr4 = false;
+  if (!attr4) {
+    cudaFuncSetAttribute(k_eig4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig4_smem(EIG4_MAX));
+    attr4 = true;
+  }
+  k_eig4<<<1, EJ4_NT, eig4_smem(s), st>>>(warm ? B : G, Phi, s, max_sweeps, tmin, Urec, PQrec, RoundStart, nr,
+                                           status, used);
+  k_eig_apply<<<(s + 7) / 8, 256, 0, st>>>(warm ? V : nullptr, Urec, PQrec, RoundStart, nr, C, s);
 }
 
 template <typename T>
@@ -1275,8 +1768,22 @@ __global__ void k_finalize(const double* __restrict__ red, int nblocks, const do
 }  // namespace
 
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                    double tmin, int* status, int* used, cudaStream_t st) {
+                    double tmin, int* status, int* used, cudaStream_t st, float* rec) {
+  if (rec && s > EIG3_MAX && s <= EIG4_MAX) {
+    eig_big(G, C, Phi, work, rec, s, warm, max_sweeps, tmin, status, used, st);
+    return;
+  }
   eig<float>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
+}
+
+size_t eig_record_floats(int s) {
+  if (s <= EIG3_MAX || s > EIG4_MAX) return 0;
+  const int m = (s + 7) & ~7, nsub = m / 8, rounds = EIG4_REC_SWEEPS * (m / 4 - 1);
+  return (size_t)rounds * nsub * 64 + (size_t)rounds * nsub + rounds + 18;  // blocks, pairs, round starts, count
+}
+int eig_launches(int s, int warm, int recorded) {
+  if (recorded && s > EIG3_MAX && s <= EIG4_MAX) return warm ? 12 : 2;
+  return 1;
 }
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st) {

@@ -171,11 +171,12 @@ def test_fp32_factored_and_direct_gram(F):
             assert rel(a, b) <= 1e-4, (mode, k, rel(a, b))
 
 
-@pytest.mark.parametrize("r", [6, 11, 12])
+@pytest.mark.parametrize("r", [6, 11, 12, 14])
 def test_fp32_eigensolver_sizes(F, r):
     """Gram sizes s = r^2 across the FP32 eigensolver's configurations: 36
     (an odd number of 8 x 8 subproblems, one half warp idle), 121 (the
-    largest block-ordered case, 16 subproblems) and 144 (one-sided Jacobi)."""
+    largest case with B and V^T on chip, 16 subproblems), 144 and 196 (B on
+    chip, rotation blocks recorded and applied to V by many CTAs)."""
     d = inputs(None, dims=(40, 36, 12), r=r, p=0.3, idx=46, noise=0.0, cap=None, dtype=np.float32)
     st, _ = oracle_run(d, 10)
     g = gpu_run(F, d, 10, precision="fp32")

@@ -29,6 +29,7 @@ CASES = [
     ((30, 24, 3, 7), 3, (3, 2), 8),
     ((5, 4, 3, 4, 3), 2, None, 6),       # N = 5
     ((64, 33, 17), 8, None, 6),          # s = 64, several K chunks
+    ((24, 20, 9, 8), 6, None, 6),        # N = 4, s = 216: the large eigensolver
 ]
 
 
