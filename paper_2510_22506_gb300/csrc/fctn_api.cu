@@ -106,6 +106,16 @@ struct HeadRoute {
   int* tabs = nullptr;
   bool m0_valid = false;
   bool hvalid[FCTN_MAX_ORDER] = {};
+  // tensor-core products (TF32 / BF16): Y_0 = X M_0^T, Z = X^T A_0 and
+  // F^T = M_0^T A_0^T with the X update, on TMA-fed tcgen05 GEMMs
+  bool tc = false, bf16 = false;
+  bool xt_valid = false;           // XT (and the BF16 copy of X) hold the present X
+  int64_t ldt = 0, ld0 = 0;        // leading dimensions of XT / A0T (I_0) and of M0T / A0p (s_0 padded)
+  TgArgs ty{}, tz{}, tf{};         // shapes of the three GEMMs
+  alignas(64) unsigned char maps[6][128];  // tensor maps: Y (A, B), Z (A, B), F (A, B)
+  void *M0T = nullptr, *XT = nullptr, *A0T = nullptr, *A0p = nullptr;  // operand copies (FP32 or BF16)
+  void *Xb = nullptr, *M0b = nullptr;  // BF16 copies of X and M_0
+  float* tpart = nullptr;              // K-split partials of Y_0
 };
 
 }  // namespace
@@ -1109,6 +1119,23 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
     r = HeadRoute{};
     return FCTN_OK;
   }
+  // tensor-core products: every operand row a multiple of 16 bytes (TMA)
+  if (h->tc) {
+    const int elem = h->p.precision == FCTN_BF16 ? 2 : 4, al = 16 / elem;
+    const int64_t I0 = h->I[0];
+    if (r.P0 % al == 0 && I0 % al == 0 && r.P0 < ((int64_t)1 << 31)) {
+      r.tc = true;
+      r.bf16 = elem == 2;
+      r.ldt = I0;
+      r.ld0 = (r.s0 + al - 1) / al * al;
+      tg_shape((int)I0, (int)r.s0, (int)r.P0, elem, 2 * 152, &r.ty);
+      tg_shape((int)r.P0, (int)r.s0, (int)I0, elem, 0, &r.tz);
+      tg_shape((int)r.P0, (int)I0, (int)r.s0, elem, 0, &r.tf);
+      r.ty.mode = TG_PARTIAL;
+      r.tz.mode = TG_STORE;
+      r.tf.mode = TG_XUPDATE;
+    }
+  }
   // table offsets are relative to this plan's block, which starts at tabs->size()
   const size_t base = tabs->size();
   auto rebase = [&](SgPlanH& q) { q.tab += base; };
@@ -1181,6 +1208,13 @@ size_t route_bytes(const fctn_handle* h, size_t tab_ints) {
     Is = h->I[k] * h->s[k] > Is ? h->I[k] * h->s[k] : Is;
   }
   b += (size_t)Is * 4 + tab_ints * sizeof(int);
+  if (r.tc) {
+    const size_t e = r.bf16 ? 2 : 4;
+    const int64_t I0 = h->I[0];
+    b += ((size_t)r.P0 * r.ld0 + (size_t)r.P0 * r.ldt + (size_t)r.s0 * r.ldt + (size_t)I0 * r.ld0) * e;
+    if (r.bf16) b += ((size_t)h->P + (size_t)r.s0 * r.P0) * 2;
+    b += (size_t)r.ty.ksplit * I0 * r.s0 * 4;
+  }
   return b;
 }
 
@@ -1414,7 +1448,35 @@ int route_build_m0(fctn_handle* h) {
     h->launches += sg_launches(q) - 1;
     cur = o;
   }
+  if (r.tc) {  // tensor-core operands: M_0 (Y_0's B) and M_0^T (F^T's A), rounded to TF32 or in BF16
+    const double mb = (double)r.s0 * r.P0 * 4.0;
+    if (r.bf16) {
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0,
+             launch_copy_bf16(r.M0, r.s0, r.P0, r.P0, (__nv_bfloat16*)r.M0b, r.P0, h->st));
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0,
+             launch_transpose_bf16(r.M0, r.s0, r.P0, r.P0, (__nv_bfloat16*)r.M0T, r.ld0, h->st));
+    } else {
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_copy_f32(r.M0, r.s0, r.P0, r.P0, r.M0, r.P0, 1, h->st));
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 1, h->st));
+    }
+  }
   r.m0_valid = true;
+  return FCTN_OK;
+}
+
+// Tensor-core copies of A_(0): A_0^T (Z's B operand) and A_0 padded to ld0
+// (F^T's B operand).
+int route_a0_copies(fctn_handle* h) {
+  HeadRoute& r = h->hr;
+  const int64_t I0 = h->I[0];
+  const float* A = (const float*)h->Ac[0];
+  if (r.bf16) {
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_transpose_bf16(A, I0, r.s0, r.s0, (__nv_bfloat16*)r.A0T, r.ldt, h->st));
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_bf16(A, I0, r.s0, r.s0, (__nv_bfloat16*)r.A0p, r.ld0, h->st));
+  } else {
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_transpose_f32(A, I0, r.s0, r.s0, (float*)r.A0T, r.ldt, 1, h->st));
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_f32(A, I0, r.s0, r.s0, (float*)r.A0p, r.ld0, 1, h->st));
+  }
   return FCTN_OK;
 }
 
@@ -1482,6 +1544,17 @@ int route_sweep(fctn_handle* h) {
     }
   int rc;
   if (!r.m0_valid && (rc = route_build_m0(h))) return rc;
+  if (r.tc && !r.xt_valid) {  // X^T (and the BF16 X) of the present X, after fctn_set_data
+    const int64_t I0 = h->I[0];
+    if (r.bf16) {
+      LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
+             launch_transpose_bf16(X, I0, r.P0, r.P0, (__nv_bfloat16*)r.XT, r.ldt, h->st));
+      LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_bf16(X, I0, r.P0, r.P0, (__nv_bfloat16*)r.Xb, r.P0, h->st));
+    } else {
+      LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_transpose_f32(X, I0, r.P0, r.P0, (float*)r.XT, r.ldt, 1, h->st));
+    }
+    r.xt_valid = true;
+  }
   for (int k = 0; k < N; ++k) {
     const int I = (int)h->I[k], s = (int)h->s[k];
     const int warm = h->cvalid[k] ? 1 : 0;
@@ -1521,7 +1594,16 @@ int route_sweep(fctn_handle* h) {
       }
     }
     // right-hand side X_(k) M_k^T (main stream)
-    if (k == 0) {
+    if (k == 0 && r.tc) {
+      TgArgs a = r.ty;
+      a.out = r.tpart;
+      a.status = h->status;
+      const double e = r.bf16 ? 2.0 : 4.0;
+      LAUNCH(FCTN_KC_GRAM, ((double)h->P + (double)r.s0 * r.P0) * e, 2.0 * (double)h->I[0] * r.s0 * r.P0,
+             launch_tg_gemm(r.maps[0], r.maps[1], a, r.bf16, h->st));
+      LAUNCH(FCTN_KC_REDUCE, 0.0, 0.0,
+             launch_tg_reduce(r.tpart, a.ksplit, (int64_t)h->I[0] * r.s0, r.Yraw, h->st));
+    } else if (k == 0) {
       LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.y0), run_sg(h, r.y0, X, r.M0, r.Yraw, r.pm, h->st));
       h->launches += sg_launches(r.y0) - 1;
     } else {
@@ -1543,7 +1625,16 @@ int route_sweep(fctn_handle* h) {
     LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[k]),
            run_sg(h, r.hg[k], (const float*)h->Ac[k], (const float*)h->Ac[k], r.H[k], r.pm, h->st));
     h->launches += sg_launches(r.hg[k]) - 1;
-    if (k == 0) {  // Z = X_(0)^T A_(0) with the new head factor
+    if (k == 0 && r.tc) {  // Z = X_(0)^T A_(0) with the new head factor (tensor cores)
+      if ((rc = route_a0_copies(h))) return rc;
+      TgArgs a = r.tz;
+      a.out = r.Zb;
+      a.ldo = r.s0;
+      a.status = h->status;
+      const double e = r.bf16 ? 2.0 : 4.0;
+      LAUNCH(FCTN_KC_GRAM, (double)h->P * e + (double)r.s0 * r.P0 * 4.0, 2.0 * (double)h->I[0] * r.s0 * r.P0,
+             launch_tg_gemm(r.maps[2], r.maps[3], a, r.bf16, h->st));
+    } else if (k == 0) {  // Z = X_(0)^T A_(0) with the new head factor
       LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.z),
              run_sg(h, r.z, X, (const float*)h->Ac[0], r.Zb, r.pm, h->st));
       h->launches += sg_launches(r.z) - 1;
@@ -1552,15 +1643,36 @@ int route_sweep(fctn_handle* h) {
   // M_0 of the new factors 1 .. N-1, then Eq. 10 with F = A_(0) M_0
   if ((rc = route_build_m0(h))) return rc;
   GramPlan g = gram_plan(h, 0);
-  const double xb = 2.0 * (double)h->P * 4.0 + (double)r.s0 * r.P0 * 4.0 + (double)h->P / 8.0;
-  LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0,
-         launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
+  int nred = xupdate_blocks(g);
+  if (r.tc) {  // F^T = M_0^T A_(0)^T with Eq. 10 in the epilogue (tensor cores)
+    TgArgs a = r.tf;
+    a.X = (float*)h->X;
+    a.bits = h->bits;
+    a.P0 = r.P0;
+    a.rho = rho;
+    a.XT = r.bf16 ? nullptr : (float*)r.XT;
+    a.XTb = r.bf16 ? (__nv_bfloat16*)r.XT : nullptr;
+    a.Xb = r.bf16 ? (__nv_bfloat16*)r.Xb : nullptr;
+    a.ldt = r.ldt;
+    a.round_tf32 = 1;
+    a.red = h->red;
+    a.status = h->status;
+    const double e = r.bf16 ? 2.0 : 4.0;
+    // X read and written, X^T written (and the BF16 X), mask bits, M_0^T read
+    const double xb = (double)h->P * (8.0 + e + (r.bf16 ? 2.0 : 0.0)) + (double)h->P / 8.0 + (double)r.s0 * r.P0 * e;
+    LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0, launch_tg_gemm(r.maps[4], r.maps[5], a, r.bf16, h->st));
+    nred = (int)(((r.P0 + 127) / 128) * ((h->I[0] + a.BN - 1) / a.BN));
+  } else {
+    const double xb = 2.0 * (double)h->P * 4.0 + (double)r.s0 * r.P0 * 4.0 + (double)h->P / 8.0;
+    LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0,
+           launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
+  }
   const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
   for (int k = 0; k < N; ++k)
     LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
            launch_trace_term(h->A64[k], h->I[k], h->s[k], sgn * (2.0 + h->p.delta[k]), -sgn, h->p.lambda[k],
                              h->traces + 32 * k, h->st));
-  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, xupdate_blocks(g), h->traces, h->N, h->stats, h->st));
+  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, nred, h->traces, h->N, h->stats, h->st));
   h->t++;
   return FCTN_OK;
 }
@@ -1641,6 +1753,7 @@ uint64_t sweep_key(const fctn_handle* h) {
   }
   if (h->hr.on) {
     key |= (uint64_t)(h->hr.m0_valid ? 1 : 0) << 14;
+    key |= (uint64_t)(h->hr.xt_valid ? 1 : 0) << 24;
     for (int k = 0; k < h->N; ++k) key |= (uint64_t)(h->hr.hvalid[k] ? 1 : 0) << (15 + k);
   }
   return key;
@@ -1854,6 +1967,27 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     for (int k = 0; k < h->N; ++k) A_(r.H[k], (size_t)h->s[k] * h->s[k] * 4);
     A_(r.Yraw, (size_t)z.Is * 4);
     A_(r.tabs, route_tabs.size() * sizeof(int));
+    if (r.tc) {
+      const size_t el = r.bf16 ? 2 : 4;
+      const int64_t I0 = h->I[0];
+      A_(r.M0T, (size_t)r.P0 * r.ld0 * el);
+      A_(r.XT, (size_t)r.P0 * r.ldt * el);
+      A_(r.A0T, (size_t)r.s0 * r.ldt * el);
+      A_(r.A0p, (size_t)I0 * r.ld0 * el);
+      if (r.bf16) {
+        A_(r.Xb, (size_t)h->P * 2);
+        A_(r.M0b, (size_t)r.s0 * r.P0 * 2);
+      }
+      A_(r.tpart, (size_t)r.ty.ksplit * I0 * r.s0 * 4);
+      const int e = (int)el;
+      int mrc = tg_make_map(r.maps[0], r.bf16 ? r.Xb : h->X, I0, r.P0, r.P0, e, 128);
+      if (!mrc) mrc = tg_make_map(r.maps[1], r.bf16 ? r.M0b : (void*)r.M0, r.s0, r.P0, r.P0, e, r.ty.BN);
+      if (!mrc) mrc = tg_make_map(r.maps[2], r.XT, r.P0, I0, r.ldt, e, 128);
+      if (!mrc) mrc = tg_make_map(r.maps[3], r.A0T, r.s0, I0, r.ldt, e, r.tz.BN);
+      if (!mrc) mrc = tg_make_map(r.maps[4], r.M0T, r.P0, r.s0, r.ld0, e, 128);
+      if (!mrc) mrc = tg_make_map(r.maps[5], r.A0p, I0, r.s0, r.ld0, e, r.tf.BN);
+      if (mrc) r.tc = false;  // no tensor maps here: the CUDA-core products serve instead
+    }
     cudaError_t ce = cudaMemcpy(r.tabs, route_tabs.data(), route_tabs.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
       free_all(h);
@@ -1950,6 +2084,7 @@ int fctn_set_data(fctn_handle* h, const void* Y, const uint8_t* mask, int where)
   h->t = 0;
   h->Tvalid[0] = h->Tvalid[1] = false;
   for (int k = 0; k < h->N; ++k) h->cvalid[k] = false;
+  h->hr.xt_valid = false;
   return FCTN_OK;
 }
 

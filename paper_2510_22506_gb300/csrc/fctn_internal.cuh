@@ -147,6 +147,47 @@ void launch_transpose_bf16(const float* src, int64_t rows, int64_t cols, int64_t
 void launch_copy_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst, int64_t ldd,
                       cudaStream_t st);
 
+// ---- kernels_tma.cu ---------------------------------------------------------
+// D[M x N] = A[M x K] B[N x K]^T on tcgen05 with TMA-fed operands (both
+// K-major); see kernels_tma.cu.  Epilogue modes:
+enum { TG_PARTIAL = 0,   // out[z][row][col] (dense M x N per K split z)
+       TG_STORE = 1,     // out[row * ldo + col]
+       TG_XUPDATE = 2 }; // rows j, columns i of F^T = (A_(1) M_1)^T: Eq. 10 on X_(1)[i, j]
+struct TgArgs {
+  int M, N, K;     // extents; K beyond the operands' tensor maps reads zeros
+  int BN, S;       // columns per CTA (multiple of 16, <= 256), pipeline stages
+  int kchunk;      // K per split (multiple of the 128-byte chunk)
+  int ksplit;
+  int mode;
+  float* out;
+  int64_t ldo;
+  // TG_XUPDATE: X (I_1 x P_1, row-major), observation bits, rho; transposed
+  // copy XT (P_1 x ldt, rounded to TF32 when round_tf32) and, for the BF16
+  // precision, BF16 copies Xb (I_1 x P_1) and XTb (P_1 x ldt); FP64 partial
+  // sums per CTA {||dX||^2, ||X_old||^2, ||X_new - F||^2} into red
+  float* X;
+  const uint32_t* bits;
+  int64_t P0;
+  double rho;
+  float* XT;
+  int64_t ldt;
+  __nv_bfloat16* Xb;
+  __nv_bfloat16* XTb;
+  int round_tf32;
+  double* red;
+  int* status;
+};
+// Tensor map of a row-major operand (rows x cols, leading dimension ld
+// elements, 16-byte multiple) for the GEMM: boxes of 128 bytes of K by
+// box_rows rows, 128-byte swizzle.  elem: 4 (FP32 / TF32) or 2 (BF16).
+int tg_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int elem, int box_rows);
+size_t tg_smem_bytes(int BN, int S);
+// Launch; bf16 selects the BF16 operands and MMA kind.
+void launch_tg_gemm(const void* mapA, const void* mapB, const TgArgs& a, int bf16, cudaStream_t st);
+void tg_shape(int M, int N, int K, int elem, int want_ctas, TgArgs* a);  // BN, S, kchunk, ksplit
+// out[e] = sum over the K split of part[z * MN + e] (split order, FP64), e < MN.
+void launch_tg_reduce(const float* part, int ksplit, int64_t MN, float* out, cudaStream_t st);
+
 // ---- kernels_quality.cu ----------------------------------------------------
 // PSNR and SSIM (Sec. 4) of X against the truth Y, both (rows x ncol)
 // row-major with rows = I_1 I_2 (slice index = column); out = {psnr, ssim}.

@@ -75,3 +75,34 @@ def test_head_route_graph_and_eager_identical(F):
         finally:
             F.fctn_destroy(h)
     np.testing.assert_array_equal(out[0], out[1])
+
+
+# ---- tensor-core products (TF32 / BF16) of the head route -----------------
+TC_CASES = [((48, 40, 9), 4, None), ((32, 24, 3, 7), 3, (3, 2)), ((24, 20, 9, 8), 6, None),
+            ((136, 40, 12), 5, None)]   # I_1 = 136: two row tiles of 128 in X_(1) M_1^T
+
+
+@pytest.mark.parametrize("dims,r,cap", TC_CASES)
+@pytest.mark.parametrize("precision,tol", [("tf32", 3e-3), ("bf16", 3e-2)])
+def test_head_route_tensor_core_one_sweep_close_to_fp32(F, dims, r, cap, precision, tol):
+    """One sweep: the TMA / tcgen05 products (X_(1) M_1^T, X_(1)^T A_(1),
+    M_1^T A_(1)^T with the X update) against the FP32 CUDA-core products."""
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=73, noise=0.0, cap=cap, dtype=np.float32)
+    a = gpu_run(F, d, 1, precision="fp32", policy="plain")
+    b = gpu_run(F, d, 1, precision=precision, policy="plain")
+    assert b["stats"]["status"] == 0
+    assert rel(b["X"], a["X"]) <= tol, rel(b["X"], a["X"])
+    for x, y in zip(b["factors"], a["factors"]):
+        assert rel(x, y) <= 10 * tol, rel(x, y)
+
+
+@pytest.mark.parametrize("dims,r,cap,sweeps", [((48, 40, 9), 4, None, 60), ((32, 24, 3, 7), 3, (3, 2), 50)])
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_head_route_tensor_core_psnr_within_005_db(F, dims, r, cap, sweeps, precision):
+    from oracle import fctn_oracle as O
+    d = inputs(None, dims=dims, r=r, p=0.3, idx=74, noise=0.0, cap=cap, dtype=np.float32)
+    st, _ = oracle_run(d, sweeps, policy="plain")
+    g = gpu_run(F, d, sweeps, precision=precision, policy="plain")
+    p_or, p_gpu = O.psnr(st.X, d["truth"]), O.psnr(g["X"], d["truth"])
+    print(f"{precision} {dims}: PSNR oracle {p_or:.4f} GPU {p_gpu:.4f}, X rel err {rel(g['X'], st.X):.2e}")
+    assert abs(p_gpu - p_or) <= 0.05
