@@ -67,8 +67,11 @@ enum {
   FCTN_FP64 = 0,  /* everything in double: the parity path                             */
   FCTN_FP32 = 1,  /* plain single precision on the CUDA cores                          */
   FCTN_TF32 = 2,  /* tcgen05 TF32 contractions, FP32 accumulation                      */
-  FCTN_BF16 = 3   /* tcgen05 BF16 contractions on split operands (v = hi + lo, three
-                     MMAs per product: hi.hi + hi.lo + lo.hi), FP32 accumulation     */
+  FCTN_BF16 = 3   /* tcgen05 BF16 contractions, FP32 accumulation.  With the head-mode
+                     route (reuse, plain order, N >= 3) the right-hand-side products
+                     take BF16 operands and the reconstruction F of Eq. 10 TF32;
+                     otherwise split operands (v = hi + lo, three MMAs per product:
+                     hi.hi + hi.lo + lo.hi)                                          */
 };
 
 /* update-order policy of Algorithm 2 ("unordered permutation" of the factors) */

@@ -1130,7 +1130,7 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
       r.ld0 = (r.s0 + al - 1) / al * al;
       tg_shape((int)I0, (int)r.s0, (int)r.P0, elem, 2 * 152, &r.ty);
       tg_shape((int)r.P0, (int)r.s0, (int)I0, elem, 0, &r.tz);
-      tg_shape((int)r.P0, (int)I0, (int)r.s0, elem, 0, &r.tf);
+      tg_shape((int)r.P0, (int)I0, (int)r.s0, 4, 0, &r.tf);  // the reconstruction stays TF32 (see route_build_m0)
       r.ty.mode = TG_PARTIAL;
       r.tz.mode = TG_STORE;
       r.tf.mode = TG_XUPDATE;
@@ -1211,7 +1211,7 @@ size_t route_bytes(const fctn_handle* h, size_t tab_ints) {
   if (r.tc) {
     const size_t e = r.bf16 ? 2 : 4;
     const int64_t I0 = h->I[0];
-    b += ((size_t)r.P0 * r.ld0 + (size_t)r.P0 * r.ldt + (size_t)r.s0 * r.ldt + (size_t)I0 * r.ld0) * e;
+    b += ((size_t)r.P0 * r.ldt + (size_t)r.s0 * r.ldt) * e + ((size_t)r.P0 * r.ld0 + (size_t)I0 * r.ld0) * 4;
     if (r.bf16) b += ((size_t)h->P + (size_t)r.s0 * r.P0) * 2;
     b += (size_t)r.ty.ksplit * I0 * r.s0 * 4;
   }
@@ -1448,13 +1448,16 @@ int route_build_m0(fctn_handle* h) {
     h->launches += sg_launches(q) - 1;
     cur = o;
   }
-  if (r.tc) {  // tensor-core operands: M_0 (Y_0's B) and M_0^T (F^T's A), rounded to TF32 or in BF16
+  if (r.tc) {
+    // tensor-core operands: M_0 (Y_0's B: TF32-rounded, or BF16) and M_0^T
+    // (F^T's A, TF32-rounded in both precisions: the reconstruction of Eq. 10
+    // sets the completed entries directly, and BF16 operands there moved the
+    // final PSNR by 0.11 dB on 48 x 40 x 9, beyond the 0.05 dB target)
     const double mb = (double)r.s0 * r.P0 * 4.0;
     if (r.bf16) {
       LAUNCH(FCTN_KC_MERGED, mb, 0.0,
              launch_copy_bf16(r.M0, r.s0, r.P0, r.P0, (__nv_bfloat16*)r.M0b, r.P0, h->st));
-      LAUNCH(FCTN_KC_MERGED, mb, 0.0,
-             launch_transpose_bf16(r.M0, r.s0, r.P0, r.P0, (__nv_bfloat16*)r.M0T, r.ld0, h->st));
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 1, h->st));
     } else {
       LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_copy_f32(r.M0, r.s0, r.P0, r.P0, r.M0, r.P0, 1, h->st));
       LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 1, h->st));
@@ -1472,7 +1475,7 @@ int route_a0_copies(fctn_handle* h) {
   const float* A = (const float*)h->Ac[0];
   if (r.bf16) {
     LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_transpose_bf16(A, I0, r.s0, r.s0, (__nv_bfloat16*)r.A0T, r.ldt, h->st));
-    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_bf16(A, I0, r.s0, r.s0, (__nv_bfloat16*)r.A0p, r.ld0, h->st));
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_f32(A, I0, r.s0, r.s0, (float*)r.A0p, r.ld0, 1, h->st));
   } else {
     LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_transpose_f32(A, I0, r.s0, r.s0, (float*)r.A0T, r.ldt, 1, h->st));
     LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_copy_f32(A, I0, r.s0, r.s0, (float*)r.A0p, r.ld0, 1, h->st));
@@ -1659,8 +1662,8 @@ int route_sweep(fctn_handle* h) {
     a.status = h->status;
     const double e = r.bf16 ? 2.0 : 4.0;
     // X read and written, X^T written (and the BF16 X), mask bits, M_0^T read
-    const double xb = (double)h->P * (8.0 + e + (r.bf16 ? 2.0 : 0.0)) + (double)h->P / 8.0 + (double)r.s0 * r.P0 * e;
-    LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0, launch_tg_gemm(r.maps[4], r.maps[5], a, r.bf16, h->st));
+    const double xb = (double)h->P * (8.0 + e + (r.bf16 ? 2.0 : 0.0)) + (double)h->P / 8.0 + (double)r.s0 * r.P0 * 4.0;
+    LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0, launch_tg_gemm(r.maps[4], r.maps[5], a, 0, h->st));
     nred = (int)(((r.P0 + 127) / 128) * ((h->I[0] + a.BN - 1) / a.BN));
   } else {
     const double xb = 2.0 * (double)h->P * 4.0 + (double)r.s0 * r.P0 * 4.0 + (double)h->P / 8.0;
@@ -1970,10 +1973,10 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     if (r.tc) {
       const size_t el = r.bf16 ? 2 : 4;
       const int64_t I0 = h->I[0];
-      A_(r.M0T, (size_t)r.P0 * r.ld0 * el);
+      A_(r.M0T, (size_t)r.P0 * r.ld0 * 4);
       A_(r.XT, (size_t)r.P0 * r.ldt * el);
       A_(r.A0T, (size_t)r.s0 * r.ldt * el);
-      A_(r.A0p, (size_t)I0 * r.ld0 * el);
+      A_(r.A0p, (size_t)I0 * r.ld0 * 4);
       if (r.bf16) {
         A_(r.Xb, (size_t)h->P * 2);
         A_(r.M0b, (size_t)r.s0 * r.P0 * 2);
@@ -1984,8 +1987,8 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
       if (!mrc) mrc = tg_make_map(r.maps[1], r.bf16 ? r.M0b : (void*)r.M0, r.s0, r.P0, r.P0, e, r.ty.BN);
       if (!mrc) mrc = tg_make_map(r.maps[2], r.XT, r.P0, I0, r.ldt, e, 128);
       if (!mrc) mrc = tg_make_map(r.maps[3], r.A0T, r.s0, I0, r.ldt, e, r.tz.BN);
-      if (!mrc) mrc = tg_make_map(r.maps[4], r.M0T, r.P0, r.s0, r.ld0, e, 128);
-      if (!mrc) mrc = tg_make_map(r.maps[5], r.A0p, I0, r.s0, r.ld0, e, r.tf.BN);
+      if (!mrc) mrc = tg_make_map(r.maps[4], r.M0T, r.P0, r.s0, r.ld0, 4, 128);
+      if (!mrc) mrc = tg_make_map(r.maps[5], r.A0p, I0, r.s0, r.ld0, 4, r.tf.BN);
       if (mrc) r.tc = false;  // no tensor maps here: the CUDA-core products serve instead
     }
     cudaError_t ce = cudaMemcpy(r.tabs, route_tabs.data(), route_tabs.size() * sizeof(int), cudaMemcpyHostToDevice);

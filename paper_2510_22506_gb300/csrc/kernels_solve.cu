@@ -422,10 +422,12 @@ __device__ __forceinline__ void sm_mm_sym(float* __restrict__ out, int so, const
 // synchronisations only (a warp runs two subproblems in lockstep, so that
 // fewer warps contend for issue slots); an outer round costs three block
 // barriers.
-// Rotation test and stop test: rotate iff B_pq^2 > tol^2 |B_pp B_qq| +
-// floor^2 (tol = sqrt(s) eps, floor = eps ||G||_F / sqrt(s)); stop after a
-// sweep whose largest rotated B_pq^2 / |B_pp B_qq| was below tol (quadratic
-// convergence: the next sweep would rotate nothing).
+// Rotation test and stop test: rotate iff B_pq^2 > tol^2 (|B_pp| + t)
+// (|B_qq| + t) + floor^2 (tol = sqrt(s) eps, floor = eps ||G||_F / sqrt(s),
+// t = max(tmin, 0), the smallest shift of Eq. 8: see k_eig4); stop after a
+// sweep whose largest rotated ratio was below tol (quadratic convergence: the
+// next sweep would rotate nothing), or before a sweep in which no pair would
+// rotate (one scan of the upper triangle).
 constexpr int EIG3_MAX = 128;
 constexpr int EJ_SUB = 132;  // floats per subproblem: S (8 x 8), U (8 x 8), 4 against bank conflicts
 constexpr int EJ_NT = 512;   // most threads
@@ -493,6 +495,67 @@ __device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restri
   float ck, sk, tk, cl, sl, tl;
   const float mu = ej_rot(ak, bk, gk, tol2, floor2, ck, sk, tk);
   ej_rot(al, bl, gl, tol2, floor2, cl, sl, tl);
+  const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+  const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+  float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
+  float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
+  const bool dg = (k == l) && mu >= 0.f;
+  if (dg) {
+    z00 = fmaf(-tk, gk, ak);
+    z11 = fmaf(tk, gk, bk);
+    z01 = 0.f;
+    z10 = 0.f;
+    ++cnt;
+    cmu = fmaxf(cmu, mu);
+  }
+  Sw[pk * 8 + pl] = z00;
+  Sw[pk * 8 + ql] = z01;
+  Sw[qk * 8 + pl] = z10;
+  Sw[qk * 8 + ql] = z11;
+  Uw[k * 8 + pl] = cl * u00 - sl * u01;
+  Uw[k * 8 + ql] = sl * u00 + cl * u01;
+  Uw[(k + 4) * 8 + pl] = cl * u10 - sl * u11;
+  Uw[(k + 4) * 8 + ql] = sl * u10 + cl * u11;
+  __syncwarp();
+}
+
+// Rotation test relative to the shifted diagonal (see k_eig4): rotate iff
+// B_pq^2 > tol^2 (|B_pp| + t)(|B_qq| + t) + floor^2, t = max(tmin, 0).
+__device__ __forceinline__ float ej_rot_shift(float a, float b, float g, float tol2, float floor2, float tsh,
+                                              float& c, float& sn, float& t) {
+  const float ab = (fabsf(a) + tsh) * (fabsf(b) + tsh), g2 = g * g;
+  const bool rot = g2 > tol2 * ab + floor2;
+  const float d = b - a, tg = 2.f * g;
+  const float h = fmaf(d, d, tg * tg);
+  const float hy = h * rsqrtf(h);
+  const float tt = __fdividef(d >= 0.f ? tg : -tg, fabsf(d) + hy);
+  const float x = fmaf(tt, tt, 1.f);
+  const float y = rsqrtf(x);
+  const float cc = y * fmaf(-0.5f * x * y, y, 1.5f);
+  c = rot ? cc : 1.f;
+  sn = rot ? cc * tt : 0.f;
+  t = rot ? tt : 0.f;
+  return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
+}
+
+// ej_round with the shifted rotation test (see k_eig4).
+template <bool W, int T>
+__device__ __forceinline__ void ej4_round(float* __restrict__ Sw, float* __restrict__ Uw, int hl, float tol2,
+                                          float floor2, float tsh, unsigned& cnt, float& cmu) {
+  const int k = hl >> 2, l = hl & 3;
+  int pk, qk, pl, ql;
+  ej_pair(W, T, k, pk, qk);
+  ej_pair(W, T, l, pl, ql);
+  const float ak = Sw[pk * 9], bk = Sw[qk * 9], gk = Sw[pk * 8 + qk];
+  const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
+  const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
+  const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
+  const float u00 = Uw[k * 8 + pl], u01 = Uw[k * 8 + ql];
+  const float u10 = Uw[(k + 4) * 8 + pl], u11 = Uw[(k + 4) * 8 + ql];
+  __syncwarp();
+  float ck, sk, tk, cl, sl, tl;
+  const float mu = ej_rot_shift(ak, bk, gk, tol2, floor2, tsh, ck, sk, tk);
+  ej_rot_shift(al, bl, gl, tol2, floor2, tsh, cl, sl, tl);
   const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
   const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
   float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
@@ -597,7 +660,28 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
   float cmu = 0.f;
   int sweep = 0;
   bool converged = (s <= 1);
+  const float tsh = tmin > 0.0 ? (float)tmin : 0.f;
+  __shared__ int any_rot;
   for (; sweep < max_sweeps && !converged; ++sweep) {
+    // a sweep in which no pair would pass the rotation test changes nothing:
+    // scan the upper triangle once and stop without running it
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    {
+      bool want = false;
+      for (int e = tid; e < s * s && !want; e += nt) {
+        const int p = e / s, q = e - p * s;
+        if (q <= p) continue;
+        const float a = B[p * sp + p], b = B[q * sp + q], g = B[p * sp + q];
+        want = g * g > tol2 * (fabsf(a) + tsh) * (fabsf(b) + tsh) + floor2;
+      }
+      if (__any_sync(0xffffffffu, want) && lane == 0) any_rot = 1;
+    }
+    __syncthreads();
+    if (!any_rot) {
+      converged = true;
+      break;
+    }
     for (int r = 0; r < nb - 1; ++r) {
       for (int sw = warp; sw < nsub2; sw += nwarp) {
         const int sub = 2 * sw + (lane >> 4), hl = lane & 15;
@@ -617,14 +701,14 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
         }
         __syncwarp();
         if (r == 0) {
-          ej_round<true, 0>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
-          ej_round<true, 1>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
-          ej_round<true, 2>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+          ej4_round<true, 0>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+          ej4_round<true, 1>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+          ej4_round<true, 2>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
         }
-        ej_round<false, 0>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
-        ej_round<false, 1>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
-        ej_round<false, 2>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
-        ej_round<false, 3>(Sw, Uw, hl, tol2, floor2, cnt, cmu);
+        ej4_round<false, 0>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 1>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 2>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
+        ej4_round<false, 3>(Sw, Uw, hl, tol2, floor2, tsh, cnt, cmu);
       }
       if (r == nb - 2 && warp < nsub2) {  // this sweep's totals per warp
         const unsigned cn = __reduce_add_sync(0xffffffffu, cnt);
@@ -806,65 +890,6 @@ __global__ void __launch_bounds__(256) k_mm_small(const float* __restrict__ A, c
     }
 }
 
-__device__ __forceinline__ float ej_rot_shift(float a, float b, float g, float tol2, float floor2, float tsh,
-                                              float& c, float& sn, float& t) {
-  const float ab = (fabsf(a) + tsh) * (fabsf(b) + tsh), g2 = g * g;
-  const bool rot = g2 > tol2 * ab + floor2;
-  const float d = b - a, tg = 2.f * g;
-  const float h = fmaf(d, d, tg * tg);
-  const float hy = h * rsqrtf(h);
-  const float tt = __fdividef(d >= 0.f ? tg : -tg, fabsf(d) + hy);
-  const float x = fmaf(tt, tt, 1.f);
-  const float y = rsqrtf(x);
-  const float cc = y * fmaf(-0.5f * x * y, y, 1.5f);
-  c = rot ? cc : 1.f;
-  sn = rot ? cc * tt : 0.f;
-  t = rot ? tt : 0.f;
-  return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
-}
-
-// ej_round with the shifted rotation test (see k_eig4).
-template <bool W, int T>
-__device__ __forceinline__ void ej4_round(float* __restrict__ Sw, float* __restrict__ Uw, int hl, float tol2,
-                                          float floor2, float tsh, unsigned& cnt, float& cmu) {
-  const int k = hl >> 2, l = hl & 3;
-  int pk, qk, pl, ql;
-  ej_pair(W, T, k, pk, qk);
-  ej_pair(W, T, l, pl, ql);
-  const float ak = Sw[pk * 9], bk = Sw[qk * 9], gk = Sw[pk * 8 + qk];
-  const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
-  const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
-  const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
-  const float u00 = Uw[k * 8 + pl], u01 = Uw[k * 8 + ql];
-  const float u10 = Uw[(k + 4) * 8 + pl], u11 = Uw[(k + 4) * 8 + ql];
-  __syncwarp();
-  float ck, sk, tk, cl, sl, tl;
-  const float mu = ej_rot_shift(ak, bk, gk, tol2, floor2, tsh, ck, sk, tk);
-  ej_rot_shift(al, bl, gl, tol2, floor2, tsh, cl, sl, tl);
-  const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
-  const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
-  float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
-  float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
-  const bool dg = (k == l) && mu >= 0.f;
-  if (dg) {
-    z00 = fmaf(-tk, gk, ak);
-    z11 = fmaf(tk, gk, bk);
-    z01 = 0.f;
-    z10 = 0.f;
-    ++cnt;
-    cmu = fmaxf(cmu, mu);
-  }
-  Sw[pk * 8 + pl] = z00;
-  Sw[pk * 8 + ql] = z01;
-  Sw[qk * 8 + pl] = z10;
-  Sw[qk * 8 + ql] = z11;
-  Uw[k * 8 + pl] = cl * u00 - sl * u01;
-  Uw[k * 8 + ql] = sl * u00 + cl * u01;
-  Uw[(k + 4) * 8 + pl] = cl * u10 - sl * u11;
-  Uw[(k + 4) * 8 + ql] = sl * u10 + cl * u11;
-  __syncwarp();
-}
-
 // Jacobi sweeps on B (s x s in global memory, from the warm-start products
 // or G itself).  Records, for outer round n (counted over all sweeps), the
 // blocks U of the subproblems that rotated (entries RoundStart[n] ..
@@ -923,7 +948,27 @@ __global__ void __launch_bounds__(EJ4_NT) k_eig4(const float* __restrict__ Bin, 
   int sweep = 0, nround = 0;
   bool converged = (s <= 1);
   const int sweep_cap = max_sweeps < EIG4_REC_SWEEPS ? max_sweeps : EIG4_REC_SWEEPS;
+  __shared__ int any_rot;
   for (; sweep < sweep_cap && !converged; ++sweep) {
+    // a sweep in which no pair would pass the rotation test changes nothing:
+    // scan the upper triangle once and stop without running it
+    if (tid == 0) any_rot = 0;
+    __syncthreads();
+    {
+      bool want = false;
+      for (int e = tid; e < s * s && !want; e += nt) {
+        const int p = e / s, q = e - p * s;
+        if (q <= p) continue;
+        const float a = B[p * sp + p], b = B[q * sp + q], g = B[p * sp + q];
+        want = g * g > tol2 * (fabsf(a) + tsh) * (fabsf(b) + tsh) + floor2;
+      }
+      if (__any_sync(0xffffffffu, want) && lane == 0) any_rot = 1;
+    }
+    __syncthreads();
+    if (!any_rot) {
+      converged = true;
+      break;
+    }
     for (int r = 0; r < nb - 1; ++r, ++nround) {
       for (int sw = warp; sw < nsub2; sw += nwarp) {
         const int sub = 2 * sw + (lane >> 4), hl = lane & 15;

@@ -115,7 +115,7 @@ __device__ __forceinline__ float tf32_round(float v) {
 namespace {
 
 template <class Op>
-__global__ void __launch_bounds__(TG_THREADS, 1) k_tg_gemm(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB, TgArgs a) {
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tg_gemm(const __grid_constant
     if (!ok) abort_flag = 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int row = m0 + 32 * q + lane;
-    double d2 = 0.0, x2 = 0.0, r2 = 0.0;
+    float d2 = 0.f, x2 = 0.f, r2 = 0.f;  // per-thread sums in FP32, combined in FP64 below
     if (ok) {
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
@@ -240,16 +240,24 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tg_gemm(const __grid_constant
             a.X[e] = xn;
             if (a.Xb) a.Xb[e] = __float2bfloat16_rn(xn);
             const float d = xn - xo, qq = xn - f;
-            d2 = fma((double)d, (double)d, d2);
-            x2 = fma((double)xo, (double)xo, x2);
-            r2 = fma((double)qq, (double)qq, r2);
+            d2 = fmaf(d, d, d2);
+            x2 = fmaf(xo, xo, x2);
+            r2 = fmaf(qq, qq, r2);
             xt[jj] = xn;
           }
-          if (a.XT) {
+          if (a.XT) {  // 16 consecutive columns of row j: four 16-byte stores when the row is whole
             float* o = a.XT + (int64_t)row * a.ldt + n0 + c0;
+            if (a.round_tf32)
 #pragma unroll
-            for (int jj = 0; jj < 16; ++jj)
-              if (n0 + c0 + jj < a.N) o[jj] = a.round_tf32 ? tf32_round(xt[jj]) : xt[jj];
+              for (int jj = 0; jj < 16; ++jj) xt[jj] = tf32_round(xt[jj]);
+            if (n0 + c0 + 16 <= a.N) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                *(float4*)(o + 4 * u) = make_float4(xt[4 * u], xt[4 * u + 1], xt[4 * u + 2], xt[4 * u + 3]);
+            } else {
+              for (int jj = 0; jj < 16; ++jj)
+                if (n0 + c0 + jj < a.N) o[jj] = xt[jj];
+            }
           }
           if (a.XTb) {
             __nv_bfloat16* o = a.XTb + (int64_t)row * a.ldt + n0 + c0;
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1) k_tg_gemm(const __grid_constant
       }
     }
     if (a.mode == TG_XUPDATE) {
-      double t[3] = {d2, x2, r2};
+      double t[3] = {(double)d2, (double)x2, (double)r2};
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         for (int o = 16; o > 0; o >>= 1) t[u] += __shfl_xor_sync(0xffffffffu, t[u], o);
@@ -343,11 +351,13 @@ void tg_shape(int M, int N, int K, int elem, int want_ctas, TgArgs* a) {
   a->N = N;
   a->K = K;
   a->BN = N <= 256 ? (N + 15) / 16 * 16 : 256;
-  int S = 8;
-  while (S > 2 && tg_smem_bytes(a->BN, S) > 200 * 1024) --S;
-  a->S = S;
   const int kel = 128 / elem;
   const int chunks = (K + kel - 1) / kel;
+  // a long K loop gets a deep ring; a short one (K <= 8 chunks) two stages,
+  // so that two CTAs (and their epilogues) share an SM
+  int S = chunks > 8 ? 8 : 2;
+  while (S > 2 && tg_smem_bytes(a->BN, S) > 200 * 1024) --S;
+  a->S = S;
   const int tiles = ((M + 127) / 128) * ((N + a->BN - 1) / a->BN);
   int ks = tiles >= want_ctas ? 1 : (want_ctas + tiles - 1) / tiles;
   const int maxks = chunks / 4 > 0 ? chunks / 4 : 1;
