@@ -240,7 +240,10 @@ enum {
   FCTN_KC_XUPDATE = 5,  /* X update of Eq. 10 fused with F = A_k(k) M_k and the sums    */
   FCTN_KC_MISC = 6,     /* trace terms, finalisation, staging                           */
   FCTN_KC_ENV = 7,      /* Grams of the factors and their chains (Gram of M_k)          */
-  FCTN_KC_COUNT = 8
+  FCTN_KC_RHS2 = 8,     /* right-hand sides of factors 2..N from Z (chain contractions) */
+  FCTN_KC_EIGAUX = 9,   /* warm-start products and rotation application of the large
+                           eigensolver (the Jacobi kernel itself is FCTN_KC_EIG)        */
+  FCTN_KC_COUNT = 10
 };
 
 /* Time every launch of one kernel class with CUDA events recorded on the

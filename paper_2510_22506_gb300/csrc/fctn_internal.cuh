@@ -234,6 +234,15 @@ void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, in
                     double tmin, int* status, int* used, cudaStream_t st, float* rec = nullptr);
 size_t eig_record_floats(int s);
 int eig_launches(int s, int warm, int recorded);
+// The three stages of the large FP32 eigensolver (128 < s <= 224), for
+// callers that time them apart: warm-start products (eig_big_prep_launches
+// kernels), the one-CTA Jacobi kernel, the rotation application.
+bool eig_is_big(int s);
+void launch_eig_big_prep(const float* G, const float* C, float* work, int s, cudaStream_t st);
+int eig_big_prep_launches();
+void launch_eig_big_jacobi(const float* G, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+                           double tmin, int* status, int* used, cudaStream_t st);
+void launch_eig_big_apply(float* C, const float* work, float* rec, int s, int warm, cudaStream_t st);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
 // Eq. 8 by row blocks.  fwd: W = (((Q^T R) C) / T) C^T.  bwd: A = Q W into

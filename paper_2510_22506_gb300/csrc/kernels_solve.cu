@@ -1263,39 +1263,71 @@ EigCfg eig_cfg(int s, int elem) {
 
 // FP32 Grams with 128 < s <= 224: warm-start products (4 multi-CTA launches),
 // k_eig4, k_eig_apply.  work: 4 s^2 floats; rec: eig_record_floats(s) floats.
-void eig_big(const float* G, float* C, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
-             double tmin, int* status, int* used, cudaStream_t st) {
-  const int m = (s + 7) & ~7, nsub = m / 8;
+struct BigRec {
+  float* Urec;
+  int *PQrec, *RoundStart, *nr;
+};
+BigRec big_rec(float* rec, int s) {
+  const int m = (s + 7) & ~7, nsub = m / 8, rounds = EIG4_REC_SWEEPS * (m / 4 - 1);
+  BigRec b;
+  b.Urec = rec;
+  b.PQrec = (int*)(rec + (int64_t)rounds * nsub * 64);
+  b.RoundStart = b.PQrec + rounds * nsub;
+  b.nr = b.RoundStart + rounds + 1;
+  return b;
+}
+
+}  // namespace
+
+// Warm-start products of the large eigensolver (work: W, V, T, B of s^2 each).
+void launch_eig_big_prep(const float* G, const float* C, float* work, int s, cudaStream_t st) {
   const int64_t ss = (int64_t)s * s;
   float *W = work, *V = work + ss, *T = work + 2 * ss, *B = work + 3 * ss;
-  const int rounds = EIG4_REC_SWEEPS * (m / 4 - 1);
-  float* Urec = rec;
-  int* PQrec = (int*)(rec + (int64_t)rounds * nsub * 64);
-  int* RoundStart = PQrec + rounds * nsub;
-  int* nr = RoundStart + rounds + 1;
   const dim3 g2((s + 31) / 32, (s + 31) / 32);
-  if (warm) {
-    k_mm_small<true><<<g2, 256, 0, st>>>(C, C, nullptr, W, s, 1.f, 0.f);    // W = V0^T V0
-    k_mm_small<false><<<g2, 256, 0, st>>>(C, W, C, V, s, -0.5f, 1.5f);      // V = 1.5 V0 - 0.5 V0 W
-    k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
-    k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
-    // first-order correction of the well-separated pairs, then once more
-    // one Newton-Schulz step and B = V^T G V
-    k_first_order<<<1, 1024, 0, st>>>(B, W, s);                               // X
-    k_mm_small<false><<<g2, 256, 0, st>>>(V, W, nullptr, T, s, 1.f, 0.f);   // V1 = V X
-    k_mm_small<true><<<g2, 256, 0, st>>>(T, T, nullptr, W, s, 1.f, 0.f);    // W = V1^T V1
-    k_mm_small<false><<<g2, 256, 0, st>>>(T, W, T, V, s, -0.5f, 1.5f);      // V = 1.5 V1 - 0.5 V1 W
-    k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
-    k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
-  }
+  k_mm_small<true><<<g2, 256, 0, st>>>(C, C, nullptr, W, s, 1.f, 0.f);    // W = V0^T V0
+  k_mm_small<false><<<g2, 256, 0, st>>>(C, W, C, V, s, -0.5f, 1.5f);      // V = 1.5 V0 - 0.5 V0 W
+  k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
+  k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
+  // first-order correction of the well-separated pairs, then once more one
+  // Newton-Schulz step and B = V^T G V
+  k_first_order<<<1, 1024, 0, st>>>(B, W, s);                               // X
+  k_mm_small<false><<<g2, 256, 0, st>>>(V, W, nullptr, T, s, 1.f, 0.f);   // V1 = V X
+  k_mm_small<true><<<g2, 256, 0, st>>>(T, T, nullptr, W, s, 1.f, 0.f);    // W = V1^T V1
+  k_mm_small<false><<<g2, 256, 0, st>>>(T, W, T, V, s, -0.5f, 1.5f);      // V = 1.5 V1 - 0.5 V1 W
+  k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
+  k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
+}
+int eig_big_prep_launches() { return 10; }
+
+// The Jacobi kernel (one CTA): B from the warm-start products, or G cold.
+void launch_eig_big_jacobi(const float* G, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+                           double tmin, int* status, int* used, cudaStream_t st) {
+  const int64_t ss = (int64_t)s * s;
+  const BigRec b = big_rec(rec, s);
   static bool attr4 = false;
   if (!attr4) {
     cudaFuncSetAttribute(k_eig4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig4_smem(EIG4_MAX));
     attr4 = true;
   }
-  k_eig4<<<1, EJ4_NT, eig4_smem(s), st>>>(warm ? B : G, Phi, s, max_sweeps, tmin, Urec, PQrec, RoundStart, nr,
-                                           status, used);
-  k_eig_apply<<<(s + 7) / 8, 256, 0, st>>>(warm ? V : nullptr, Urec, PQrec, RoundStart, nr, C, s);
+  k_eig4<<<1, EJ4_NT, eig4_smem(s), st>>>(warm ? work + 3 * ss : G, Phi, s, max_sweeps, tmin, b.Urec, b.PQrec,
+                                           b.RoundStart, b.nr, status, used);
+}
+
+// C = V (warm) or I (cold) times the recorded rotation blocks.
+void launch_eig_big_apply(float* C, const float* work, float* rec, int s, int warm, cudaStream_t st) {
+  const int64_t ss = (int64_t)s * s;
+  const BigRec b = big_rec(rec, s);
+  k_eig_apply<<<(s + 7) / 8, 256, 0, st>>>(warm ? work + ss : nullptr, b.Urec, b.PQrec, b.RoundStart, b.nr, C, s);
+}
+bool eig_is_big(int s) { return s > EIG3_MAX && s <= EIG4_MAX; }
+
+namespace {
+
+void eig_big(const float* G, float* C, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+             double tmin, int* status, int* used, cudaStream_t st) {
+  if (warm) launch_eig_big_prep(G, C, work, s, st);
+  launch_eig_big_jacobi(G, Phi, work, rec, s, warm, max_sweeps, tmin, status, used, st);
+  launch_eig_big_apply(C, work, rec, s, warm, st);
 }
 
 template <typename T>
@@ -1827,7 +1859,7 @@ size_t eig_record_floats(int s) {
   return (size_t)rounds * nsub * 64 + (size_t)rounds * nsub + rounds + 18;  // blocks, pairs, round starts, count
 }
 int eig_launches(int s, int warm, int recorded) {
-  if (recorded && s > EIG3_MAX && s <= EIG4_MAX) return warm ? 12 : 2;
+  if (recorded && s > EIG3_MAX && s <= EIG4_MAX) return warm ? 12 : 2;  // prep (10), Jacobi, apply
   return 1;
 }
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,

@@ -102,7 +102,8 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
             "fctn_server_finished", "fctn_quality", "fctn_grow_ranks", "fctn_autotune")
-KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6, "env": 7}
+KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6, "env": 7, "rhs2": 8,
+      "eigaux": 9}
 
 
 class fctn_server_config(ctypes.Structure):
