@@ -1496,17 +1496,16 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
   const double bwd_flops = 2.0 * (double)I * I * s;
   const double resid_flops = 2.0 * (double)I * s * s;
   float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
-  if (!eig_done && h->eig_rec && eig_is_big(s)) {  // the three stages timed apart
+  if (!eig_done && eig_is_big(s)) {  // the two stages timed apart
     const double ss = (double)s * s;
     if (warm) {
-      LAUNCH(FCTN_KC_EIGAUX, 0.0, 12.0 * ss * s,
+      LAUNCH(FCTN_KC_EIGAUX, 0.0, 8.0 * ss * s,
              launch_eig_big_prep((const float*)h->Gs, Ck, (float*)h->gwork, s, h->st));
       h->launches += eig_big_prep_launches() - 1;
     }
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-           launch_eig_big_jacobi((const float*)h->Gs, Phi, (float*)h->gwork, h->eig_rec, s, warm, h->eig_cap, tmin,
+           launch_eig_big_jacobi((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin,
                                  h->status, h->eig_used + k, h->st));
-    LAUNCH(FCTN_KC_EIGAUX, 0.0, 0.0, launch_eig_big_apply(Ck, (float*)h->gwork, h->eig_rec, s, warm, h->st));
   } else if (!eig_done) {
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,

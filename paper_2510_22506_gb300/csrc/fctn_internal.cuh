@@ -234,15 +234,20 @@ void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, in
                     double tmin, int* status, int* used, cudaStream_t st, float* rec = nullptr);
 size_t eig_record_floats(int s);
 int eig_launches(int s, int warm, int recorded);
-// The three stages of the large FP32 eigensolver (128 < s <= 224), for
-// callers that time them apart: warm-start products (eig_big_prep_launches
-// kernels), the one-CTA Jacobi kernel, the rotation application.
+// The two stages of the cluster eigensolver for FP32 Grams with 64 < s <= 256
+// (eig_is_big), for callers that time them apart: the warm-start products
+// (eig_big_prep_launches kernels; work: 4 s^2 floats) and the Jacobi sweeps on
+// one cluster of 8 CTAs (kernels_eigc.cu), which write Phi and C.
 bool eig_is_big(int s);
 void launch_eig_big_prep(const float* G, const float* C, float* work, int s, cudaStream_t st);
 int eig_big_prep_launches();
-void launch_eig_big_jacobi(const float* G, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+void launch_eig_big_jacobi(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
                            double tmin, int* status, int* used, cudaStream_t st);
-void launch_eig_big_apply(float* C, const float* work, float* rec, int s, int warm, cudaStream_t st);
+// ---- kernels_eigc.cu: B (s x s) and, warm, V (s x s, column j = eigenvector
+// guess j; null = identity) -> Phi, C; *used as in launch_eig_f32.
+size_t eigc_smem_bytes(int s);
+void launch_eigc(const float* Bin, const float* Vin, float* Phi, float* C, int s, int max_sweeps, double tmin,
+                 int* status, int* used, cudaStream_t st);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
 // Eq. 8 by row blocks.  fwd: W = (((Q^T R) C) / T) C^T.  bwd: A = Q W into

@@ -7,8 +7,10 @@
 #include <algorithm>
 
 #include "fctn_internal.cuh"
+#include "fctn_jacobi.cuh"
 
 namespace {
+using namespace fctn_jacobi;
 
 // ------------------------------------------------------- eigensolver ----
 template <typename T> struct Eps;
@@ -272,24 +274,6 @@ __global__ void __launch_bounds__(1024) k_eig1(const T* __restrict__ G, T* __res
 // sweep's C), B = V^T (G V).  The index set is padded to m = s rounded up to
 // 8 (the padding rows and columns of B are zero and never rotate).
 
-// Pair idx of round `round` of the round-robin schedule over m indices.
-__device__ __forceinline__ void round_pair(int m, int round, int idx, int& p, int& q) {
-  if (idx == 0) {
-    p = m - 1;
-    q = round;
-  } else {
-    p = round + idx;
-    if (p >= m - 1) p -= m - 1;
-    q = round - idx;
-    if (q < 0) q += m - 1;
-  }
-  if (p > q) {
-    int t = p;
-    p = q;
-    q = t;
-  }
-}
-
 // out[i][j] = ca * sum_k op(X)[i][k] Y[k][j] (+ cb * Add[i][j]) for i, j < m,
 // op(X) = X or X^T; m % 4 == 0; X, Y rows 16-byte aligned with strides that
 // are multiples of 4.  Each thread owns a 4 x 4 tile; the Y rows are read as
@@ -429,25 +413,9 @@ __device__ __forceinline__ void sm_mm_sym(float* __restrict__ out, int so, const
 // next sweep would rotate nothing), or before a sweep in which no pair would
 // rotate (one scan of the upper triangle).
 constexpr int EIG3_MAX = 128;
-constexpr int EJ_SUB = 132;  // floats per subproblem: S (8 x 8), U (8 x 8), 4 against bank conflicts
+constexpr int EIGC_MIN = 64, EIGC_MAX = 256;  // FP32 Grams with EIGC_MIN < s <= EIGC_MAX: cluster Jacobi
 constexpr int EJ_NT = 512;   // most threads
 constexpr int EJ_TPT = 2;    // row tasks per thread: 128 * 128 / 16 <= 2 * 512
-
-// Pair k (0-3) of inner round t: within-block rounds t = 0-2 pair (0,1)(2,3),
-// (0,2)(1,3), (0,3)(1,2) inside block P (k = 0, 1) and block Q (k = 2, 3);
-// cross rounds pair (k, 4 + (k xor t)).
-__device__ __forceinline__ void ej_pair(bool within, int t, int k, int& p, int& q) {
-  if (within) {
-    constexpr unsigned code = 4u | 14u << 4 | 8u << 8 | 13u << 12 | 12u << 16 | 9u << 20;  // a | b << 2 per (t, k & 1)
-    const unsigned v = (code >> ((t * 2 + (k & 1)) * 4)) & 15u;
-    const int base = (k & 2) << 1;
-    p = base + (int)(v & 3u);
-    q = base + (int)(v >> 2);
-  } else {
-    p = k;
-    q = 4 + (k ^ t);
-  }
-}
 
 // Rotation of a pair from its 2 x 2 block [a g; g b] without a branch:
 // t = sgn(d) 2g / (|d| + hypot(d, 2g)), d = b - a (the smaller root of
@@ -495,67 +463,6 @@ __device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restri
   float ck, sk, tk, cl, sl, tl;
   const float mu = ej_rot(ak, bk, gk, tol2, floor2, ck, sk, tk);
   ej_rot(al, bl, gl, tol2, floor2, cl, sl, tl);
-  const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
-  const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
-  float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
-  float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
-  const bool dg = (k == l) && mu >= 0.f;
-  if (dg) {
-    z00 = fmaf(-tk, gk, ak);
-    z11 = fmaf(tk, gk, bk);
-    z01 = 0.f;
-    z10 = 0.f;
-    ++cnt;
-    cmu = fmaxf(cmu, mu);
-  }
-  Sw[pk * 8 + pl] = z00;
-  Sw[pk * 8 + ql] = z01;
-  Sw[qk * 8 + pl] = z10;
-  Sw[qk * 8 + ql] = z11;
-  Uw[k * 8 + pl] = cl * u00 - sl * u01;
-  Uw[k * 8 + ql] = sl * u00 + cl * u01;
-  Uw[(k + 4) * 8 + pl] = cl * u10 - sl * u11;
-  Uw[(k + 4) * 8 + ql] = sl * u10 + cl * u11;
-  __syncwarp();
-}
-
-// Rotation test relative to the shifted diagonal (see k_eig4): rotate iff
-// B_pq^2 > tol^2 (|B_pp| + t)(|B_qq| + t) + floor^2, t = max(tmin, 0).
-__device__ __forceinline__ float ej_rot_shift(float a, float b, float g, float tol2, float floor2, float tsh,
-                                              float& c, float& sn, float& t) {
-  const float ab = (fabsf(a) + tsh) * (fabsf(b) + tsh), g2 = g * g;
-  const bool rot = g2 > tol2 * ab + floor2;
-  const float d = b - a, tg = 2.f * g;
-  const float h = fmaf(d, d, tg * tg);
-  const float hy = h * rsqrtf(h);
-  const float tt = __fdividef(d >= 0.f ? tg : -tg, fabsf(d) + hy);
-  const float x = fmaf(tt, tt, 1.f);
-  const float y = rsqrtf(x);
-  const float cc = y * fmaf(-0.5f * x * y, y, 1.5f);
-  c = rot ? cc : 1.f;
-  sn = rot ? cc * tt : 0.f;
-  t = rot ? tt : 0.f;
-  return rot ? __fdividef(g2, fmaxf(ab, FLT_MIN)) : -1.f;
-}
-
-// ej_round with the shifted rotation test (see k_eig4).
-template <bool W, int T>
-__device__ __forceinline__ void ej4_round(float* __restrict__ Sw, float* __restrict__ Uw, int hl, float tol2,
-                                          float floor2, float tsh, unsigned& cnt, float& cmu) {
-  const int k = hl >> 2, l = hl & 3;
-  int pk, qk, pl, ql;
-  ej_pair(W, T, k, pk, qk);
-  ej_pair(W, T, l, pl, ql);
-  const float ak = Sw[pk * 9], bk = Sw[qk * 9], gk = Sw[pk * 8 + qk];
-  const float al = Sw[pl * 9], bl = Sw[ql * 9], gl = Sw[pl * 8 + ql];
-  const float x00 = Sw[pk * 8 + pl], x01 = Sw[pk * 8 + ql];
-  const float x10 = Sw[qk * 8 + pl], x11 = Sw[qk * 8 + ql];
-  const float u00 = Uw[k * 8 + pl], u01 = Uw[k * 8 + ql];
-  const float u10 = Uw[(k + 4) * 8 + pl], u11 = Uw[(k + 4) * 8 + ql];
-  __syncwarp();
-  float ck, sk, tk, cl, sl, tl;
-  const float mu = ej_rot_shift(ak, bk, gk, tol2, floor2, tsh, ck, sk, tk);
-  ej_rot_shift(al, bl, gl, tol2, floor2, tsh, cl, sl, tl);
   const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
   const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
   float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
@@ -1288,46 +1195,25 @@ void launch_eig_big_prep(const float* G, const float* C, float* work, int s, cud
   k_mm_small<false><<<g2, 256, 0, st>>>(C, W, C, V, s, -0.5f, 1.5f);      // V = 1.5 V0 - 0.5 V0 W
   k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
   k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
-  // first-order correction of the well-separated pairs, then once more one
-  // Newton-Schulz step and B = V^T G V
-  k_first_order<<<1, 1024, 0, st>>>(B, W, s);                               // X
-  k_mm_small<false><<<g2, 256, 0, st>>>(V, W, nullptr, T, s, 1.f, 0.f);   // V1 = V X
-  k_mm_small<true><<<g2, 256, 0, st>>>(T, T, nullptr, W, s, 1.f, 0.f);    // W = V1^T V1
-  k_mm_small<false><<<g2, 256, 0, st>>>(T, W, T, V, s, -0.5f, 1.5f);      // V = 1.5 V1 - 0.5 V1 W
-  k_mm_small<false><<<g2, 256, 0, st>>>(G, V, nullptr, T, s, 1.f, 0.f);   // T = G V
-  k_mm_small<true><<<g2, 256, 0, st>>>(V, T, nullptr, B, s, 1.f, 0.f);    // B = V^T T
 }
-int eig_big_prep_launches() { return 10; }
+int eig_big_prep_launches() { return 4; }
 
-// The Jacobi kernel (one CTA): B from the warm-start products, or G cold.
-void launch_eig_big_jacobi(const float* G, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
+// The Jacobi sweeps on one cluster of 8 CTAs (kernels_eigc.cu): B from the
+// warm-start products (V among them), or G and the identity cold.
+void launch_eig_big_jacobi(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
                            double tmin, int* status, int* used, cudaStream_t st) {
   const int64_t ss = (int64_t)s * s;
-  const BigRec b = big_rec(rec, s);
-  static bool attr4 = false;
-  if (!attr4) {
-    cudaFuncSetAttribute(k_eig4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig4_smem(EIG4_MAX));
-    attr4 = true;
-  }
-  k_eig4<<<1, EJ4_NT, eig4_smem(s), st>>>(warm ? work + 3 * ss : G, Phi, s, max_sweeps, tmin, b.Urec, b.PQrec,
-                                           b.RoundStart, b.nr, status, used);
+  launch_eigc(warm ? work + 3 * ss : G, warm ? work + ss : nullptr, Phi, C, s, max_sweeps, tmin, status, used, st);
 }
 
-// C = V (warm) or I (cold) times the recorded rotation blocks.
-void launch_eig_big_apply(float* C, const float* work, float* rec, int s, int warm, cudaStream_t st) {
-  const int64_t ss = (int64_t)s * s;
-  const BigRec b = big_rec(rec, s);
-  k_eig_apply<<<(s + 7) / 8, 256, 0, st>>>(warm ? work + ss : nullptr, b.Urec, b.PQrec, b.RoundStart, b.nr, C, s);
-}
-bool eig_is_big(int s) { return s > EIG3_MAX && s <= EIG4_MAX; }
+bool eig_is_big(int s) { return s > EIGC_MIN && s <= EIGC_MAX; }
 
 namespace {
 
-void eig_big(const float* G, float* C, float* Phi, float* work, float* rec, int s, int warm, int max_sweeps,
-             double tmin, int* status, int* used, cudaStream_t st) {
+void eig_big(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps, double tmin,
+             int* status, int* used, cudaStream_t st) {
   if (warm) launch_eig_big_prep(G, C, work, s, st);
-  launch_eig_big_jacobi(G, Phi, work, rec, s, warm, max_sweeps, tmin, status, used, st);
-  launch_eig_big_apply(C, work, rec, s, warm, st);
+  launch_eig_big_jacobi(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
 }
 
 template <typename T>
@@ -1846,20 +1732,22 @@ __global__ void k_finalize(const double* __restrict__ red, int nblocks, const do
 
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st, float* rec) {
-  if (rec && s > EIG3_MAX && s <= EIG4_MAX) {
-    eig_big(G, C, Phi, work, rec, s, warm, max_sweeps, tmin, status, used, st);
+  (void)rec;
+  if (eig_is_big(s)) {
+    eig_big(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
     return;
   }
   eig<float>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
 }
 
 size_t eig_record_floats(int s) {
-  if (s <= EIG3_MAX || s > EIG4_MAX) return 0;
+  if (eig_is_big(s) || s <= EIG3_MAX || s > EIG4_MAX) return 0;  // the cluster Jacobi keeps V on chip
   const int m = (s + 7) & ~7, nsub = m / 8, rounds = EIG4_REC_SWEEPS * (m / 4 - 1);
   return (size_t)rounds * nsub * 64 + (size_t)rounds * nsub + rounds + 18;  // blocks, pairs, round starts, count
 }
 int eig_launches(int s, int warm, int recorded) {
-  if (recorded && s > EIG3_MAX && s <= EIG4_MAX) return warm ? 12 : 2;  // prep (10), Jacobi, apply
+  (void)recorded;
+  if (eig_is_big(s)) return warm ? 5 : 1;  // warm-start products (4), cluster Jacobi
   return 1;
 }
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
