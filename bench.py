@@ -45,11 +45,25 @@ DESC = {
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # CUDA-core FP32 at the maximum SM clock
 SM_FP32_TFLOPS = 128 * 2 * 2.07e9 / 1e12           # one SM (single-CTA kernels)
+
+
+def eig_sms(s):
+    """SMs of the FP32 Gram eigensolver: one CTA up to s = 64, else a cluster of
+    4-8 CTAs with T tables each, m = 8 CL T >= s padded least (as the library)."""
+    if s <= 64:
+        return 1, "k_eig3 (one CTA)"
+    need = (s + 7) // 8
+    best = None
+    for cl in range(8, 3, -1):
+        t = -(-need // cl)
+        if best is None or 8 * cl * t < best[0]:
+            best = (8 * cl * t, cl)
+    return best[1], f"k_eigc (cluster of {best[1]} CTAs, m = {best[0]})"
 # Kernel behind each profiler class of the head-mode route, and its bound.
 CLASS_KERNEL = {
     "gram": ("k_tg_gemm (X_(1) M_1^T, X_(1)^T A_(1))", "hbm"),
     "xupdate": ("k_tg_gemm (F^T = M_1^T A_(1)^T, Eq. 10 epilogue)", "hbm"),
-    "eig": ("k_eig4 (s > 128) / k_eig3 (one CTA)", "alu1"),
+    "eig": ("k_eigc (cluster) / k_eig3 (one CTA)", "alu1"),
     "env": ("k_sgemm (factor Grams and their chains)", "alu"),
     "rhs2": ("k_sgemm (right-hand sides 2..N from Z)", "alu"),
     "merged": ("k_sgemm (M_1) + operand copies", "alu"),
@@ -174,11 +188,13 @@ def class_roofline(cls, prof, peaks, peak_src, precision, svals, eig_sweeps):
     kernel, bound = CLASS_KERNEL.get(cls, (cls, "hbm"))
     n = max(prof["launches"], 1)
     avg_s = prof["ms"] / n / 1e3
-    if bound == "alu1":  # one CTA: one SM's FP32 rate; two-sided Jacobi on B, 6 s^3 flops per sweep
-        flops = float(np.mean([6.0 * sv ** 3 for sv in svals])) * max(eig_sweeps, 1)
+    if bound == "alu1":  # the SMs the eigensolver runs on; two-sided Jacobi on B and V^T, 9 s^3 flops per sweep
+        flops = float(np.mean([9.0 * sv ** 3 for sv in svals])) * max(eig_sweeps, 1)
+        sms, kname = eig_sms(max(svals))
         ach = flops / avg_s / 1e12
-        return dict(kernel=kernel, bound="alu", achieved=ach, peak=SM_FP32_TFLOPS, unit="TFLOP/s",
-                    frac=ach / SM_FP32_TFLOPS, peak_source="derived: one SM, 128 FP32 lanes x 2 x 2.07 GHz",
+        peak = sms * SM_FP32_TFLOPS
+        return dict(kernel=kname, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_source=f"derived: {sms} SM(s) x 128 FP32 lanes x 2 x 2.07 GHz",
                     flops_per_launch=flops)
     if bound == "alu":
         ach = prof["flops"] / n / avg_s / 1e12

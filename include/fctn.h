@@ -118,6 +118,12 @@ typedef struct fctn_params {
   int32_t eig_max_sweeps; /* cap on the Jacobi sweeps of one Gram eigendecomposition
                              (Eq. 7); 0 = 60.  Reaching it is reported in
                              fctn_stats.eig_capped, not as an error                    */
+  double eig_tol;         /* FP32 Gram eigensolver: a pair (p, q) is rotated while
+                             B_pq^2 > tol^2 (|B_pp| + t)(|B_qq| + t), t the smallest
+                             shift of Eq. 8.  0 = matched to refine_steps (the FP64
+                             refinement of the solve removes what the eigenbasis
+                             leaves): 2e-4 with two or more steps, 2e-5 with one,
+                             sqrt(s) FLT_EPSILON with none                              */
 } fctn_params;
 
 typedef struct fctn_stats {

@@ -731,6 +731,7 @@ int check_params(const fctn_params* p) {
   if (p->rhs_ctas < 0 || p->rhs_ctas > 16 * 152) return fail(FCTN_E_ARG, "rhs_ctas %d outside [0, 2432]", p->rhs_ctas);
   if (p->eig_max_sweeps < 0 || p->eig_max_sweeps > 1000)
     return fail(FCTN_E_ARG, "eig_max_sweeps %d outside [0, 1000]", p->eig_max_sweeps);
+  if (!(p->eig_tol >= 0.0 && p->eig_tol < 1.0)) return fail(FCTN_E_ARG, "eig_tol must lie in [0, 1)");
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
@@ -1275,6 +1276,17 @@ int copy_out(fctn_handle* h, void* dst, const void* src, size_t bytes, int where
 }
 
 
+// Rotation threshold of the FP32 Gram eigensolver: the caller's, else one
+// matched to the FP64 refinement of the solve, which removes what the
+// eigenbasis leaves: two refinement steps tolerate off-diagonal ratios of
+// 2e-4 (one Jacobi sweep from a warm start), one step 2e-5; without
+// refinement the kernels' own sqrt(s) FLT_EPSILON (0 here).
+double eig_tol_eff(const fctn_handle* h) {
+  if (h->p.eig_tol > 0.0) return h->p.eig_tol;
+  if (h->f64) return 0.0;
+  return h->p.refine_steps >= 2 ? 2e-4 : h->p.refine_steps == 1 ? 2e-5 : 0.0;
+}
+
 // Eqs. 5-9 for factor k; M_k is formed on chip from its pair operands L, R
 // (and written to Mout when that is non-null).
 int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mout) {
@@ -1325,7 +1337,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
                                           (float*)h->Gs, fst));
         LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
                   launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                 h->eig_cap, tmin, h->status, h->eig_used + k, fst, h->eig_rec));
+                                 h->eig_cap, tmin, h->status, h->eig_used + k, fst, h->eig_rec, eig_tol_eff(h)));
       }
       if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
     } else if (h->f64) {
@@ -1386,7 +1398,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
     if (!fork)
       LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
              launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
-                            h->eig_used + k, h->st, h->eig_rec));
+                            h->eig_used + k, h->st, h->eig_rec, eig_tol_eff(h)));
     if (!fork) h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
     const int nref = h->p.refine_steps;
     LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
@@ -1505,11 +1517,11 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
     }
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_big_jacobi((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin,
-                                 h->status, h->eig_used + k, h->st));
+                                 eig_tol_eff(h), h->status, h->eig_used + k, h->st));
   } else if (!eig_done) {
     LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
            launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
-                          h->eig_used + k, h->st, h->eig_rec));
+                          h->eig_used + k, h->st, h->eig_rec, eig_tol_eff(h)));
     h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
   }
   const int nref = h->p.refine_steps;
@@ -1600,7 +1612,7 @@ int route_sweep(fctn_handle* h) {
         LAUNCH_ON(1, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
         LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
                   launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                 h->eig_cap, tmin, h->status, h->eig_used + k, gs, h->eig_rec));
+                                 h->eig_cap, tmin, h->status, h->eig_used + k, gs, h->eig_rec, eig_tol_eff(h)));
         if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
       } else {
         LAUNCH(FCTN_KC_ENV, 0.0, 0.0, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));

@@ -231,7 +231,7 @@ void launch_xupdate_f64(const double* Ak, const double* M, double* X, const uint
 // With `rec` (eig_record_floats(s) floats) and 128 < s <= 224 the FP32 route
 // is the large block-ordered Jacobi (eig_launches kernels, work 4 s^2).
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                    double tmin, int* status, int* used, cudaStream_t st, float* rec = nullptr);
+                    double tmin, int* status, int* used, cudaStream_t st, float* rec = nullptr, double tol = 0.0);
 size_t eig_record_floats(int s);
 int eig_launches(int s, int warm, int recorded);
 // The two stages of the cluster eigensolver for FP32 Grams with 64 < s <= 256
@@ -242,12 +242,12 @@ bool eig_is_big(int s);
 void launch_eig_big_prep(const float* G, const float* C, float* work, int s, cudaStream_t st);
 int eig_big_prep_launches();
 void launch_eig_big_jacobi(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                           double tmin, int* status, int* used, cudaStream_t st);
+                           double tmin, double tol, int* status, int* used, cudaStream_t st);
 // ---- kernels_eigc.cu: B (s x s) and, warm, V (s x s, column j = eigenvector
 // guess j; null = identity) -> Phi, C; *used as in launch_eig_f32.
 size_t eigc_smem_bytes(int s);
 void launch_eigc(const float* Bin, const float* Vin, float* Phi, float* C, int s, int max_sweeps, double tmin,
-                 int* status, int* used, cudaStream_t st);
+                 double tol, int* status, int* used, cudaStream_t st);
 void launch_eig_f64(const double* G, double* C, double* Phi, double* work, int s, int warm, int max_sweeps,
                     double tmin, int* status, int* used, cudaStream_t st);
 // Eq. 8 by row blocks.  fwd: W = (((Q^T R) C) / T) C^T.  bwd: A = Q W into

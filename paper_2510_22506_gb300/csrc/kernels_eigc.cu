@@ -73,7 +73,8 @@ __host__ __device__ inline size_t ec_smem_floats(int s) {
 
 __global__ void __launch_bounds__(EC_NT)
     k_eigc(const float* __restrict__ Bin, const float* __restrict__ Vin, float* __restrict__ Phi,
-           float* __restrict__ C, int s, int max_sweeps, double tmin, int* status, int* sweeps_used) {
+           float* __restrict__ C, int s, int max_sweeps, double tmin, double tol_in, int* status,
+           int* sweeps_used) {
   cg::cluster_group cluster = cg::this_cluster();
   const int cr = (int)cluster.block_rank();
   const EcDims D = ec_dims(s);
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(EC_NT)
   __shared__ float pub_fr;                 // published: share of ||B||_F^2
   __shared__ unsigned pub_cnt, pub_mx;     // published: rotations and largest ratio of a sweep
   __shared__ int pub_scan;                 // published: some own pair would rotate
-  __shared__ float red[8];
+  __shared__ float red[EC_NT / 32];
   __shared__ float gnorm;
   __shared__ int g_any;
   __shared__ unsigned g_cnt, g_mx;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(EC_NT)
   }
   __syncthreads();
   const float eps = FLT_EPSILON;
-  const float tol = sqrtf((float)(s > 1 ? s : 1)) * eps, tol2 = tol * tol;
+  const float tol = tol_in > 0.0 ? (float)tol_in : sqrtf((float)(s > 1 ? s : 1)) * eps, tol2 = tol * tol;
   const float floor_abs = eps * gnorm * rsqrtf((float)(s > 0 ? s : 1)), floor2 = floor_abs * floor_abs;
   const float tsh = tmin > 0.0 ? (float)tmin : 0.f;
 
@@ -288,46 +289,42 @@ __global__ void __launch_bounds__(EC_NT)
         float* dst = cluster.map_shared_rank(Bb[nxt], ta / T) + ((ta % T) * 8 + th * 4) * sp;
         const float* src = Bb[cur] + (al * 8 + half * 4) * sp;
         const int P = pq[b] & 0xffff, Q = pq[b] >> 16;
-        float w[4][8];
         if (b == a) {  // own superblock: the rotated subproblem
-          const float* Sb = SC + al * EJ_SUB;
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) w[i][j] = Sb[(half * 4 + i) * 8 + j];
-        } else {
+          const float* Sb = SC + al * EJ_SUB + half * 32;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
+            *(float4*)(dst + i * sp + 4 * P) = *(const float4*)(Sb + i * 8);
+            *(float4*)(dst + i * sp + 4 * Q) = *(const float4*)(Sb + i * 8 + 4);
+          }
+        } else if (Uall[b * EC_UP + 64] == 0.f) {  // U_b = I: the rows move unchanged
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            *(float4*)(dst + i * sp + 4 * P) = *(const float4*)(src + i * sp + 4 * P);
+            *(float4*)(dst + i * sp + 4 * Q) = *(const float4*)(src + i * sp + 4 * Q);
+          }
+        } else {
+          const float* Ub = Uall + b * EC_UP;
+          float u[64];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float4 t4 = *(const float4*)(Ub + 4 * e);
+            u[4 * e] = t4.x, u[4 * e + 1] = t4.y, u[4 * e + 2] = t4.z, u[4 * e + 3] = t4.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {  // one row at a time: out_j = sum_k w_k U[k][j]
             const float4 w0 = *(const float4*)(src + i * sp + 4 * P), w1 = *(const float4*)(src + i * sp + 4 * Q);
-            w[i][0] = w0.x, w[i][1] = w0.y, w[i][2] = w0.z, w[i][3] = w0.w;
-            w[i][4] = w1.x, w[i][5] = w1.y, w[i][6] = w1.z, w[i][7] = w1.w;
-          }
-          if (Uall[b * EC_UP + 64] != 0.f) {
-            const float* Ub = Uall + b * EC_UP;
-            float o[4][8];
+            const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float o[8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int jj = 0; jj < 8; ++jj) {
+              float acc = 0.f;
 #pragma unroll
-              for (int j = 0; j < 8; ++j) o[i][j] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              const float4 ua = *(const float4*)(Ub + kk * 8), uc = *(const float4*)(Ub + kk * 8 + 4);
-              const float u[8] = {ua.x, ua.y, ua.z, ua.w, uc.x, uc.y, uc.z, uc.w};
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) o[i][j] = fmaf(w[i][kk], u[j], o[i][j]);
+              for (int kk = 0; kk < 8; ++kk) acc = fmaf(w[kk], u[kk * 8 + jj], acc);
+              o[jj] = acc;
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 8; ++j) w[i][j] = o[i][j];
+            *(float4*)(dst + i * sp + 4 * P) = make_float4(o[0], o[1], o[2], o[3]);
+            *(float4*)(dst + i * sp + 4 * Q) = make_float4(o[4], o[5], o[6], o[7]);
           }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          *(float4*)(dst + i * sp + 4 * P) = make_float4(w[i][0], w[i][1], w[i][2], w[i][3]);
-          *(float4*)(dst + i * sp + 4 * Q) = make_float4(w[i][4], w[i][5], w[i][6], w[i][7]);
         }
       }
       // V^T rows move with their block
@@ -398,7 +395,7 @@ __global__ void __launch_bounds__(EC_NT)
 size_t eigc_smem_bytes(int s) { return ec_smem_floats(s) * sizeof(float); }
 
 void launch_eigc(const float* Bin, const float* Vin, float* Phi, float* C, int s, int max_sweeps, double tmin,
-                 int* status, int* used, cudaStream_t st) {
+                 double tol, int* status, int* used, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_eigc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -417,5 +414,5 @@ void launch_eigc(const float* Bin, const float* Vin, float* Phi, float* C, int s
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_eigc, Bin, Vin, Phi, C, s, max_sweeps, tmin, status, used);
+  cudaLaunchKernelEx(&cfg, k_eigc, Bin, Vin, Phi, C, s, max_sweeps, tmin, tol, status, used);
 }

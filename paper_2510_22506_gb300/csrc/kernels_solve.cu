@@ -489,7 +489,7 @@ __device__ __forceinline__ void ej_round(float* __restrict__ Sw, float* __restri
 
 __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, float* __restrict__ Cio,
                                                 float* __restrict__ Phi, int s, int warm, int max_sweeps,
-                                                double tmin, int* status, int* sweeps_used) {
+                                                double tmin, double tol_in, int* status, int* sweeps_used) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int m = (s + 7) & ~7, sp = m + 4, nb = m / 4, nsub = m / 8, nsub2 = (nsub + 1) / 2;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(EJ_NT) k_eig3(const float* __restrict__ G, flo
   }
   __syncthreads();
   const float eps = FLT_EPSILON;
-  const float tol = sqrtf((float)(s > 1 ? s : 1)) * eps;
+  const float tol = tol_in > 0.0 ? (float)tol_in : sqrtf((float)(s > 1 ? s : 1)) * eps;
   const float tol2 = tol * tol;
   const float floor_abs = eps * red[0] * rsqrtf((float)(s > 0 ? s : 1));
   const float floor2 = floor_abs * floor_abs;
@@ -1201,9 +1201,10 @@ int eig_big_prep_launches() { return 4; }
 // The Jacobi sweeps on one cluster of 8 CTAs (kernels_eigc.cu): B from the
 // warm-start products (V among them), or G and the identity cold.
 void launch_eig_big_jacobi(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                           double tmin, int* status, int* used, cudaStream_t st) {
+                           double tmin, double tol, int* status, int* used, cudaStream_t st) {
   const int64_t ss = (int64_t)s * s;
-  launch_eigc(warm ? work + 3 * ss : G, warm ? work + ss : nullptr, Phi, C, s, max_sweeps, tmin, status, used, st);
+  launch_eigc(warm ? work + 3 * ss : G, warm ? work + ss : nullptr, Phi, C, s, max_sweeps, tmin, tol, status, used,
+              st);
 }
 
 bool eig_is_big(int s) { return s > EIGC_MIN && s <= EIGC_MAX; }
@@ -1211,14 +1212,14 @@ bool eig_is_big(int s) { return s > EIGC_MIN && s <= EIGC_MAX; }
 namespace {
 
 void eig_big(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps, double tmin,
-             int* status, int* used, cudaStream_t st) {
+             double tol, int* status, int* used, cudaStream_t st) {
   if (warm) launch_eig_big_prep(G, C, work, s, st);
-  launch_eig_big_jacobi(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
+  launch_eig_big_jacobi(G, C, Phi, work, s, warm, max_sweeps, tmin, tol, status, used, st);
 }
 
 template <typename T>
 void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, double tmin, int* status, int* used,
-         cudaStream_t st) {
+         cudaStream_t st, double tol = 0.0) {
   if (sizeof(T) == 4 && s <= EIG3_MAX) {
     const int m = (s + 7) & ~7, nsub = m / 8;
     // one warp per subproblem; one thread per row task up to EJ_NT
@@ -1229,7 +1230,7 @@ void eig(const T* G, T* C, T* Phi, T* work, int s, int warm, int max_sweeps, dou
       cudaFuncSetAttribute(k_eig3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eig3_smem(EIG3_MAX));
       attr3 = true;
     }
-    k_eig3<<<1, threads, bytes, st>>>((const float*)G, (float*)C, (float*)Phi, s, warm, max_sweeps, tmin, status,
+    k_eig3<<<1, threads, bytes, st>>>((const float*)G, (float*)C, (float*)Phi, s, warm, max_sweeps, tmin, tol, status,
                                        used);
     return;
   }
@@ -1731,13 +1732,13 @@ __global__ void k_finalize(const double* __restrict__ red, int nblocks, const do
 }  // namespace
 
 void launch_eig_f32(const float* G, float* C, float* Phi, float* work, int s, int warm, int max_sweeps,
-                    double tmin, int* status, int* used, cudaStream_t st, float* rec) {
+                    double tmin, int* status, int* used, cudaStream_t st, float* rec, double tol) {
   (void)rec;
   if (eig_is_big(s)) {
-    eig_big(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
+    eig_big(G, C, Phi, work, s, warm, max_sweeps, tmin, tol, status, used, st);
     return;
   }
-  eig<float>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st);
+  eig<float>(G, C, Phi, work, s, warm, max_sweeps, tmin, status, used, st, tol);
 }
 
 size_t eig_record_floats(int s) {

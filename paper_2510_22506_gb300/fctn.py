@@ -47,6 +47,7 @@ class fctn_params(ctypes.Structure):
         ("gram_mode", ctypes.c_int32),
         ("rhs_ctas", ctypes.c_int32),
         ("eig_max_sweeps", ctypes.c_int32),
+        ("eig_tol", ctypes.c_double),
     ]
 
 
@@ -159,7 +160,7 @@ def fctn_version():
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
                 laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
-                eig_max_sweeps=0):
+                eig_max_sweeps=0, eig_tol=0.0):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -186,6 +187,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     p.gram_mode = {"auto": 0, "direct": 1, "factored": 2}[gram_mode] if isinstance(gram_mode, str) else int(gram_mode)
     p.rhs_ctas = int(rhs_ctas)
     p.eig_max_sweeps = int(eig_max_sweeps)
+    p.eig_tol = float(eig_tol)
     return p
 
 
