@@ -355,7 +355,7 @@ def run_ours(args):
         if name != "c2":
             line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), args.steps, quality_sweeps=0)
         line["rank_growth"] = rank_growth_run(F, "c2", *gpu_inputs(F, "c2"))
-        line["serving"] = serving_mix(args.serve_jobs, tune=not args.no_tune)
+        line["serving"] = serving_mix(args.serve_jobs, tune=False)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -376,8 +376,10 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100,
     Y32, M8 = np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8)
     init32 = [np.ascontiguousarray(a.astype(np.float32)) for a in init]
     for prec in ("fp32", "tf32", "bf16"):
+        # the reduced precisions finish in FP32 once rel_change <= 1e-3: the
+        # tensor-core products' rounding alone keeps it near 4e-4 on 256x256x31x8
         p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=prec,
-                          order_policy="plain")
+                          order_policy="plain", finish_fp32_at=1e-3 if prec != "fp32" else 0.0)
         st = torch.cuda.Stream()
         h = F.fctn_create(p, st)
         try:
@@ -411,7 +413,8 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100,
                              "converged": bool(r["converged"]), "psnr_db": ps, "ssim": ss}
         finally:
             F.fctn_destroy(h)
-    res = {"unit": UNIT, "sweeps_per_s": out, "workload": name, "order_policy": "plain"}
+    res = {"unit": UNIT, "sweeps_per_s": out, "workload": name, "order_policy": "plain",
+           "finish_fp32_at": 1e-3}
     if quality_sweeps > 0:
         res.update({"quality_after_sweeps": max(quality_sweeps, steps + 3), "quality": quality,
                     "time_to_tol": {"tol": tol, "max_sweeps": max_sweeps, **ttt}})
@@ -457,24 +460,28 @@ def rank_growth_run(F, name, truth, Y, mask, init, R, grow_every=5, tol=1e-4, ma
     return out
 
 
-def serving_mix(n_jobs, tune=True):
-    """Serving mix (Poisson 20 jobs/s; shapes 64x64x16, 128x128x31, 144x176x3x20,
-    256x256x31; ranks {3,4,6}; SR {0.05,0.1,0.2}; to rel < 1e-4, cap 500):
-    served concurrently in TF32 vs the same jobs one by one in plain FP32."""
+def serving_mix(n_jobs, tune=True, precision="tf32"):
+    """Serving mix (Poisson 20 jobs/s, seeded; shapes 64x64x16, 128x128x31,
+    144x176x3x20, 256x256x31; ranks {3,4,6}; SR {0.05,0.1,0.2}; to rel < 1e-4,
+    cap 500): served (continuous batching, same-shape sweeps grouped into one
+    graph per class) in the mixed precision vs the same arrivals served one
+    job at a time in plain FP32; latency (arrival -> result) and time to
+    tolerance p50 / p99, jobs/s, and the mean final PSNR of each arm."""
     from paper_2510_22506_gb300 import serve as S
     jobs = S.mix_jobs(n_jobs, seed=5000, rate=20.0)
-    # launch shapes of every job class from the autotuner, before traffic
-    # (a server's stored tuning cache), outside the timed mix
-    tuner = S.TuneCache().fill(jobs, "tf32") if tune else None
-    served = S.run_mix(jobs, precision="tf32", tol=1e-4, max_sweeps=500, max_jobs=32, tuner=tuner)
+    tuner = S.TuneCache().fill(jobs, precision) if tune else None
+    served = S.run_mix(jobs, precision=precision, tol=1e-4, max_sweeps=500, max_jobs=64, tuner=tuner, group=True)
     seq = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500)
     keys = ("jobs", "failed", "wall_s", "jobs_per_s", "sweeps", "sweeps_per_s", "latency_p50_s", "latency_p99_s",
-            "ttt_p50_s", "ttt_p99_s")
-    return {"served_tf32": {k: served.get(k) for k in keys},
+            "ttt_p50_s", "ttt_p99_s", "psnr_mean_db", "group_launches", "group_captures")
+    arrival_rate = n_jobs / max(j["arrival"] for j in jobs)
+    return {f"served_{precision}": {k: served.get(k) for k in keys},
             "sequential_fp32": {k: seq.get(k) for k in keys if k in seq},
             "jobs_per_s_ratio": served["jobs_per_s"] / seq["jobs_per_s"],
+            "arrival_rate_jobs_per_s": arrival_rate,
+            "served_sustains_arrivals": served["jobs_per_s"] >= 0.95 * arrival_rate,
             "autotune": ({"classes": len(tuner.table), "tune_s": round(tuner.tune_s, 3),
-                          "rhs_ctas": sorted(set(tuner.table.values()))} if tuner else "off")}
+                          "choices": sorted(set(tuner.table.values()))} if tuner else "off")}
 
 
 def oracle_setup(name):
@@ -539,7 +546,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision and serving comparisons")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shape instead of the autotuner's")
-    ap.add_argument("--serve-jobs", type=int, default=48)
+    ap.add_argument("--serve-jobs", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -124,6 +124,12 @@ typedef struct fctn_params {
                              refinement of the solve removes what the eigenbasis
                              leaves): 2e-4 with two or more steps, 2e-5 with one,
                              sqrt(s) FLT_EPSILON with none                              */
+  double finish_fp32_at;  /* TF32 / BF16 with the head-mode route: once a sweep's
+                             rel_change <= this, or rel_change has not reached a new
+                             low (1 % below the lowest) for ten sweeps (the tensor-
+                             core products' rounding floor), later sweeps (fctn_complete,
+                             the server) use the FP32 CUDA-core products, so that
+                             rel_change can reach smaller tolerances; 0 = never         */
 } fctn_params;
 
 typedef struct fctn_stats {
@@ -269,14 +275,20 @@ int fctn_destroy(fctn_handle* h);
  * while a slot is free and the job's fctn_footprint_bytes fits the memory
  * budget.  An admitted job keeps its factors, X and mask on the device; each
  * of its sweeps is one CUDA-graph launch on the job's own stream, so sweeps
- * of different jobs overlap on the GPU.  A job runs until rel_change <= tol
- * or max_sweeps sweeps, then waits (X resident) until fctn_server_result.
- * The caller drives the scheduler with fctn_server_step (non-blocking). */
+ * of different jobs overlap on the GPU.  With FCTN_SERVER_GROUP the ready
+ * jobs of one shape class (identical fctn_params) sweep together: their
+ * sweeps are captured into one CUDA graph (each job's kernels on its own
+ * stream, joined to the group's), launched again as one graph while the
+ * members and their sweep signatures stay the same, and captured anew when
+ * they change.  A job runs until rel_change <= tol or max_sweeps sweeps, then
+ * waits (X resident) until fctn_server_result.  The caller drives the
+ * scheduler with fctn_server_step (non-blocking). */
 enum { FCTN_JOB_QUEUED = 0, FCTN_JOB_RUNNING = 1, FCTN_JOB_DONE = 2, FCTN_JOB_FAILED = 3 };
+enum { FCTN_SERVER_GROUP = 1 };
 
 typedef struct fctn_server_config {
   int32_t max_jobs;         /* concurrent jobs (slots), 1..1024                          */
-  int32_t reserved;
+  int32_t flags;            /* FCTN_SERVER_GROUP: grouped sweeps of same-shape jobs      */
   size_t mem_budget_bytes;  /* device bytes for admitted jobs; 0 = 80 % of free memory  */
 } fctn_server_config;
 
@@ -304,6 +316,8 @@ int fctn_server_result(fctn_server* s, uint64_t job_id, void* out_X, int where);
  * *n gets the count. */
 int fctn_server_finished(fctn_server* s, uint64_t* ids, int cap, int* n);
 int fctn_server_stats(fctn_server* s, int64_t* sweeps_launched, size_t* bytes_in_use);
+/* Grouped sweeps so far: group-graph launches and (re)captures. */
+int fctn_server_group_stats(fctn_server* s, int64_t* group_launches, int64_t* group_captures);
 int fctn_server_destroy(fctn_server* s);
 
 /* ---- FCTN contraction without device allocation --------------------------

@@ -109,6 +109,9 @@ struct HeadRoute {
   // tensor-core products (TF32 / BF16): Y_0 = X M_0^T, Z = X^T A_0 and
   // F^T = M_0^T A_0^T with the X update, on TMA-fed tcgen05 GEMMs
   bool tc = false, bf16 = false;
+  bool fp32_now = false;           // the CUDA-core FP32 products serve (finish_fp32_at reached)
+  double prev_rel = 0.0;           // lowest rel_change so far and the sweeps since it fell
+  int stall = 0;
   bool xt_valid = false;           // XT (and the BF16 copy of X) hold the present X
   int64_t ldt = 0, ld0 = 0;        // leading dimensions of XT / A0T (I_0) and of M0T / A0p (s_0 padded)
   TgArgs ty{}, tz{}, tf{};         // shapes of the three GEMMs
@@ -732,6 +735,7 @@ int check_params(const fctn_params* p) {
   if (p->eig_max_sweeps < 0 || p->eig_max_sweeps > 1000)
     return fail(FCTN_E_ARG, "eig_max_sweeps %d outside [0, 1000]", p->eig_max_sweeps);
   if (!(p->eig_tol >= 0.0 && p->eig_tol < 1.0)) return fail(FCTN_E_ARG, "eig_tol must lie in [0, 1)");
+  if (!(p->finish_fp32_at >= 0.0)) return fail(FCTN_E_ARG, "finish_fp32_at must be >= 0");
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
@@ -1460,7 +1464,7 @@ int route_build_m0(fctn_handle* h) {
     h->launches += sg_launches(q) - 1;
     cur = o;
   }
-  if (r.tc) {
+  if (r.tc && !r.fp32_now) {
     // tensor-core operands: M_0 (Y_0's B: TF32-rounded, or BF16) and M_0^T
     // (F^T's A, TF32-rounded in both precisions: the reconstruction of Eq. 10
     // sets the completed entries directly, and BF16 operands there moved the
@@ -1569,7 +1573,8 @@ int route_sweep(fctn_handle* h) {
     }
   int rc;
   if (!r.m0_valid && (rc = route_build_m0(h))) return rc;
-  if (r.tc && !r.xt_valid) {  // X^T (and the BF16 X) of the present X, after fctn_set_data
+  const bool tcp = r.tc && !r.fp32_now;  // tensor-core products this sweep
+  if (tcp && !r.xt_valid) {  // X^T (and the BF16 X) of the present X, after fctn_set_data
     const int64_t I0 = h->I[0];
     if (r.bf16) {
       LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
@@ -1619,7 +1624,7 @@ int route_sweep(fctn_handle* h) {
       }
     }
     // right-hand side X_(k) M_k^T (main stream)
-    if (k == 0 && r.tc) {
+    if (k == 0 && tcp) {
       TgArgs a = r.ty;
       a.out = r.tpart;
       a.status = h->status;
@@ -1650,7 +1655,7 @@ int route_sweep(fctn_handle* h) {
     LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[k]),
            run_sg(h, r.hg[k], (const float*)h->Ac[k], (const float*)h->Ac[k], r.H[k], r.pm, h->st));
     h->launches += sg_launches(r.hg[k]) - 1;
-    if (k == 0 && r.tc) {  // Z = X_(0)^T A_(0) with the new head factor (tensor cores)
+    if (k == 0 && tcp) {  // Z = X_(0)^T A_(0) with the new head factor (tensor cores)
       if ((rc = route_a0_copies(h))) return rc;
       TgArgs a = r.tz;
       a.out = r.Zb;
@@ -1669,7 +1674,7 @@ int route_sweep(fctn_handle* h) {
   if ((rc = route_build_m0(h))) return rc;
   GramPlan g = gram_plan(h, 0);
   int nred = xupdate_blocks(g);
-  if (r.tc) {  // F^T = M_0^T A_(0)^T with Eq. 10 in the epilogue (tensor cores)
+  if (tcp) {  // F^T = M_0^T A_(0)^T with Eq. 10 in the epilogue (tensor cores)
     TgArgs a = r.tf;
     a.X = (float*)h->X;
     a.bits = h->bits;
@@ -1691,6 +1696,7 @@ int route_sweep(fctn_handle* h) {
     const double xb = 2.0 * (double)h->P * 4.0 + (double)r.s0 * r.P0 * 4.0 + (double)h->P / 8.0;
     LAUNCH(FCTN_KC_XUPDATE, xb, 2.0 * (double)h->P * r.s0,
            launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
+    r.xt_valid = false;  // X moved without its transposed copy
   }
   const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
   for (int k = 0; k < N; ++k)
@@ -1770,7 +1776,9 @@ int sweep_body(fctn_handle* h) {
 // arguments) and is not fixed by the handle: the order parity, the warm-start
 // state of every factor and the validity of the cached pair intermediates.
 uint64_t sweep_key(const fctn_handle* h) {
-  uint64_t key = (uint64_t)((h->t + 1) % 2);
+  // the order parity matters only to the alternating order of the merged-tensor route
+  const bool par = h->p.order_policy == FCTN_ORDER_ALTERNATE && h->N >= 4 && !h->hr.on;
+  uint64_t key = par ? (uint64_t)((h->t + 1) % 2) : 0u;
   for (int k = 0; k < h->N; ++k) key |= (uint64_t)(h->cvalid[k] ? 1 : 0) << (1 + k);
   for (int q = 0; q < 2; ++q) {
     bool v = reuse_pairs(h) && half_valid(h, q);
@@ -1779,6 +1787,7 @@ uint64_t sweep_key(const fctn_handle* h) {
   if (h->hr.on) {
     key |= (uint64_t)(h->hr.m0_valid ? 1 : 0) << 14;
     key |= (uint64_t)(h->hr.xt_valid ? 1 : 0) << 24;
+    key |= (uint64_t)(h->hr.fp32_now ? 1 : 0) << 25;
     for (int k = 0; k < h->N; ++k) key |= (uint64_t)(h->hr.hvalid[k] ? 1 : 0) << (15 + k);
   }
   return key;
@@ -1872,6 +1881,42 @@ int fctn_internal_sweep_async(fctn_handle* h, double* pinned) {
 }
 
 cudaStream_t fctn_internal_stream(fctn_handle* h) { return h->st; }
+
+int fctn_internal_sweep_eager(fctn_handle* h, double* pinned) {
+  if (!h->data_set || !h->factors_set) return fail(FCTN_E_STATE, "set data and factors before sweeping");
+  int rc = sweep_body(h);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(pinned, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(pinned + 4, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  pinned[5] = (double)h->t;
+  return FCTN_OK;
+}
+
+int fctn_internal_sweep_dry(fctn_handle* h, double* pinned) {
+  h->dry = true;
+  int rc = sweep_body(h);
+  h->dry = false;
+  if (rc) return rc;
+  pinned[5] = (double)h->t;
+  return FCTN_OK;
+}
+
+uint64_t fctn_internal_sweep_key(fctn_handle* h) { return sweep_key(h); }
+
+void fctn_internal_after_sweep(fctn_handle* h, double rel_change) {
+  HeadRoute& r = h->hr;
+  if (!r.tc || r.fp32_now || !(h->p.finish_fp32_at > 0.0)) return;
+  // the change stalls at the tensor-core products' rounding floor, where it
+  // fluctuates: ten sweeps without a new low (1 % below the lowest so far)
+  // also turn to FP32
+  if (r.prev_rel <= 0.0 || rel_change < 0.99 * r.prev_rel) {
+    r.prev_rel = rel_change;
+    r.stall = 0;
+  } else {
+    r.stall++;
+  }
+  if (rel_change <= h->p.finish_fp32_at || r.stall >= 10) r.fp32_now = true;
+}
 
 extern "C" {
 
@@ -2110,6 +2155,9 @@ int fctn_set_data(fctn_handle* h, const void* Y, const uint8_t* mask, int where)
   h->Tvalid[0] = h->Tvalid[1] = false;
   for (int k = 0; k < h->N; ++k) h->cvalid[k] = false;
   h->hr.xt_valid = false;
+  h->hr.fp32_now = false;
+  h->hr.prev_rel = 0.0;
+  h->hr.stall = 0;
   return FCTN_OK;
 }
 
@@ -2331,6 +2379,9 @@ int fctn_set_factors(fctn_handle* h, const void* const* factors, int where) {
   for (int k = 0; k < h->N; ++k) h->cvalid[k] = false;
   h->hr.m0_valid = false;
   for (int k = 0; k < h->N; ++k) h->hr.hvalid[k] = false;
+  h->hr.fp32_now = false;
+  h->hr.prev_rel = 0.0;
+  h->hr.stall = 0;
   return FCTN_OK;
 }
 
@@ -2373,6 +2424,7 @@ int fctn_complete(fctn_handle* h, double tol, int max_sweeps, void* out_X, int w
     if ((rc = one_sweep(h))) break;
     if ((rc = read_stats(h, &st))) break;
     if (tol > 0 && st.rel_change <= tol) converged = 1;
+    fctn_internal_after_sweep(h, st.rel_change);
   } while (!converged && h->t < max_sweeps);
   st.converged = converged;
   st.status = rc;

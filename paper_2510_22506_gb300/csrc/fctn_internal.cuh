@@ -116,6 +116,17 @@ int fctn_internal_fail(int code, const char* msg);
 // `pinned` (host, 6 doubles); the handle's stream.
 int fctn_internal_sweep_async(fctn_handle* h, double* pinned);
 cudaStream_t fctn_internal_stream(fctn_handle* h);
+// Grouped sweeps (serving): one sweep's kernels and stop-test copy issued
+// eagerly on the handle's stream (for a stream capture that joins it), or
+// only the sweep's host bookkeeping (when a captured group graph that already
+// holds this sweep is launched again); the key of the next sweep's kernel
+// sequence (equal keys: the same kernels with the same arguments).
+int fctn_internal_sweep_eager(fctn_handle* h, double* pinned);
+int fctn_internal_sweep_dry(fctn_handle* h, double* pinned);
+uint64_t fctn_internal_sweep_key(fctn_handle* h);
+// After a sweep whose stop-test change was rel_change: a TF32 / BF16 handle
+// with finish_fp32_at > 0 turns to the FP32 products once rel_change <= it.
+void fctn_internal_after_sweep(fctn_handle* h, double rel_change);
 
 // ---- kernels_sgemm.cu -------------------------------------------------------
 // Table-driven FP32 contraction C[cm[m] + cn[n]] = sum_k A[am[m] + ak[k]] B[bn[n] + bk[k]]

@@ -48,6 +48,7 @@ class fctn_params(ctypes.Structure):
         ("rhs_ctas", ctypes.c_int32),
         ("eig_max_sweeps", ctypes.c_int32),
         ("eig_tol", ctypes.c_double),
+        ("finish_fp32_at", ctypes.c_double),
     ]
 
 
@@ -102,13 +103,13 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
-            "fctn_server_finished", "fctn_quality", "fctn_grow_ranks", "fctn_autotune")
+            "fctn_server_finished", "fctn_server_group_stats", "fctn_quality", "fctn_grow_ranks", "fctn_autotune")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6, "env": 7, "rhs2": 8,
       "eigaux": 9}
 
 
 class fctn_server_config(ctypes.Structure):
-    _fields_ = [("max_jobs", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t)]
+    _fields_ = [("max_jobs", ctypes.c_int32), ("flags", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_size_t)]
 
 
 class fctn_job_info(ctypes.Structure):
@@ -130,10 +131,11 @@ lib.fctn_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTE
 lib.fctn_server_result.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int]
 lib.fctn_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)]
 lib.fctn_server_destroy.argtypes = [ctypes.c_void_p]
+lib.fctn_server_group_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
 lib.fctn_server_finished.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int)]
 for _f in ("fctn_server_create", "fctn_server_submit", "fctn_server_step", "fctn_server_poll", "fctn_server_result",
-           "fctn_server_stats", "fctn_server_destroy", "fctn_server_finished"):
+           "fctn_server_stats", "fctn_server_destroy", "fctn_server_finished", "fctn_server_group_stats"):
     getattr(lib, _f).restype = ctypes.c_int
 
 
@@ -160,7 +162,7 @@ def fctn_version():
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
                 laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
-                eig_max_sweeps=0, eig_tol=0.0):
+                eig_max_sweeps=0, eig_tol=0.0, finish_fp32_at=0.0):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -188,6 +190,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     p.rhs_ctas = int(rhs_ctas)
     p.eig_max_sweeps = int(eig_max_sweeps)
     p.eig_tol = float(eig_tol)
+    p.finish_fp32_at = float(finish_fp32_at)
     return p
 
 
@@ -397,8 +400,12 @@ def factor_shapes(params):
     return out
 
 
-def fctn_server_create(max_jobs=32, mem_budget_bytes=0):
-    cfg = fctn_server_config(max_jobs=int(max_jobs), reserved=0, mem_budget_bytes=int(mem_budget_bytes))
+FCTN_SERVER_GROUP = 1
+
+
+def fctn_server_create(max_jobs=32, mem_budget_bytes=0, group=False):
+    cfg = fctn_server_config(max_jobs=int(max_jobs), flags=FCTN_SERVER_GROUP if group else 0,
+                             mem_budget_bytes=int(mem_budget_bytes))
     out = ctypes.c_void_p()
     _check(lib.fctn_server_create(ctypes.byref(cfg), ctypes.byref(out)))
     return out
@@ -450,6 +457,12 @@ def fctn_server_stats(srv):
     n, b = ctypes.c_int64(0), ctypes.c_size_t(0)
     _check(lib.fctn_server_stats(srv, ctypes.byref(n), ctypes.byref(b)))
     return {"sweeps_launched": n.value, "bytes_in_use": b.value}
+
+
+def fctn_server_group_stats(srv):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.fctn_server_group_stats(srv, ctypes.byref(a), ctypes.byref(b)))
+    return {"group_launches": a.value, "group_captures": b.value}
 
 
 def fctn_server_destroy(srv):

@@ -1,11 +1,12 @@
 """Serving driver: Poisson arrivals of completion jobs into the libfctn server.
 
 The scheduling itself (admission by device footprint, one CUDA-graph sweep
-per job per pass on the job's own stream, retirement on the stop test) lives
-in the library (fctn_server_*).  This module builds a job mix, submits jobs at
-their arrival times while stepping the server, and reports throughput and
-latency percentiles; `run_sequential` runs the same jobs one after another
-through fctn_complete for comparison.
+per job per pass on the job's own stream or, grouped, one graph per shape
+class, retirement on the stop test) lives in the library (fctn_server_*).
+This module builds a job mix, submits jobs at their arrival times while
+stepping the server, and reports throughput, latency percentiles and the
+final PSNR of every job; `run_sequential` serves the same arrivals one job at
+a time through fctn_complete (first come, first served) for comparison.
 """
 from __future__ import annotations
 
@@ -56,9 +57,14 @@ def mix_jobs(n_jobs, seed=5000, rate=20.0, shapes=MIX_SHAPES, contract=None):
     return jobs
 
 
+# mixed precision: tensor-core sweeps until the change falls to this, FP32 sweeps after
+FINISH_FP32_AT = 1e-3
+
+
 def job_params(job, precision, tuner=None):
     p = F.make_params(job["dims"], job["R"], lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO,
-                      precision=precision, reuse=True, order_policy="alternate")
+                      precision=precision, reuse=True, order_policy="plain",
+                      finish_fp32_at=FINISH_FP32_AT if precision in ("tf32", "bf16") else 0.0)
     if tuner is not None:
         p.rhs_ctas = tuner.get(job, p)
     return p
@@ -101,11 +107,21 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if xs else None
 
 
+def psnr(X, truth):
+    """PSNR of Sec. 4 for the serving report: mean over the slices of modes
+    1-2 of 10 log10(1 / MSE) (peak 1, data in [0, 1]), MSE floored at 1e-12."""
+    X = np.asarray(X, dtype=np.float64).reshape(truth.shape[0] * truth.shape[1], -1)
+    T = np.asarray(truth, dtype=np.float64).reshape(X.shape)
+    mse = np.maximum(np.mean((X - T) ** 2, axis=0), 1e-12)
+    return float(np.mean(10.0 * np.log10(1.0 / mse)))
+
+
 def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_budget_bytes=0,
-            keep_results=False, poll_sleep=2e-5, arrivals=True, tuner=None):
+            keep_results=False, poll_sleep=2e-5, arrivals=True, tuner=None, group=True):
     """Submit jobs at their arrival times, step the server until all finish;
-    `tuner` (a TuneCache) supplies each job's launch shape."""
-    srv = F.fctn_server_create(max_jobs=max_jobs, mem_budget_bytes=mem_budget_bytes)
+    `tuner` (a TuneCache) supplies each job's launch shape; `group` sweeps the
+    ready jobs of a shape class as one graph."""
+    srv = F.fctn_server_create(max_jobs=max_jobs, mem_budget_bytes=mem_budget_bytes, group=group)
     pending = sorted(jobs, key=lambda j: j["arrival"]) if arrivals else list(jobs)
     ids, t_arr, results, infos = {}, {}, {}, {}
     try:
@@ -132,17 +148,17 @@ def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_b
             for jid in done:
                 i = ids.pop(jid)
                 if infos[i]["state"] == F.FCTN_JOB_DONE:
-                    out = None
-                    if keep_results:
-                        j = jobs[i] if jobs[i]["i"] == i else next(x for x in jobs if x["i"] == i)
-                        out = np.empty(j["dims"], dtype=F.elem_dtype(job_params(j, precision)))
+                    j = jobs[i] if jobs[i]["i"] == i else next(x for x in jobs if x["i"] == i)
+                    out = np.empty(j["dims"], dtype=F.elem_dtype(job_params(j, precision)))
                     F.fctn_server_result(srv, jid, out)
+                    infos[i]["psnr_db"] = psnr(out, j["truth"])
                     if keep_results:
                         results[i] = out
             if not done and poll_sleep:
                 time.sleep(poll_sleep)
         t_end = time.perf_counter()
         stats = F.fctn_server_stats(srv)
+        gstats = F.fctn_server_group_stats(srv)
     finally:
         F.fctn_server_destroy(srv)
     lat = [infos[i]["t_wall_done"] - t_arr[i] for i in infos]
@@ -153,15 +169,24 @@ def run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=500, max_jobs=32, mem_b
             "wall_s": t_end - first, "jobs_per_s": len(infos) / (t_end - first), "sweeps": int(sweeps),
             "sweeps_per_s": sweeps / (t_end - first), "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
             "ttt_p50_s": _pct(ttt, 50), "ttt_p99_s": _pct(ttt, 99), "sweeps_launched": stats["sweeps_launched"],
-            "infos": infos, "results": results}
+            "psnr_mean_db": float(np.mean([v["psnr_db"] for v in infos.values() if "psnr_db" in v])),
+            **gstats, "infos": infos, "results": results}
 
 
-def run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500, keep_results=False):
-    """The same jobs one at a time through fctn_complete (no concurrency)."""
+def run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500, keep_results=False, arrivals=True):
+    """The same jobs one at a time through fctn_complete, first come first
+    served: a job starts at its arrival time or when the previous one ends,
+    whichever is later; latency = end - arrival, time to tolerance = end -
+    start."""
     infos, results = {}, {}
+    order = sorted(jobs, key=lambda j: j["arrival"]) if arrivals else list(jobs)
     t0 = time.perf_counter()
     sweeps = 0
-    for j in jobs:
+    for j in order:
+        if arrivals:
+            wait = t0 + j["arrival"] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
         p = job_params(j, precision)
         dt = F.elem_dtype(p)
         h = F.fctn_create(p)
@@ -171,7 +196,9 @@ def run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500, keep_result
             F.fctn_set_factors(h, [np.ascontiguousarray(a.astype(dt)) for a in j["init"]])
             out = np.empty(j["dims"], dtype=dt)
             st = F.fctn_complete(h, tol, max_sweeps, out)
-            infos[j["i"]] = dict(st, wall=time.perf_counter() - ts)
+            te = time.perf_counter()
+            infos[j["i"]] = dict(st, wall=te - ts, latency=te - (t0 + (j["arrival"] if arrivals else 0.0)),
+                                 psnr_db=psnr(out, j["truth"]))
             sweeps += st["t"]
             if keep_results:
                 results[j["i"]] = out
@@ -179,6 +206,9 @@ def run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=500, keep_result
             F.fctn_destroy(h)
     wall = time.perf_counter() - t0
     ttt = [v["wall"] for v in infos.values()]
+    lat = [v["latency"] for v in infos.values()]
     return {"jobs": len(jobs), "wall_s": wall, "jobs_per_s": len(jobs) / wall, "sweeps": int(sweeps),
-            "sweeps_per_s": sweeps / wall, "ttt_p50_s": _pct(ttt, 50), "ttt_p99_s": _pct(ttt, 99),
+            "sweeps_per_s": sweeps / wall, "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99),
+            "ttt_p50_s": _pct(ttt, 50), "ttt_p99_s": _pct(ttt, 99),
+            "psnr_mean_db": float(np.mean([v["psnr_db"] for v in infos.values()])),
             "infos": infos, "results": results}

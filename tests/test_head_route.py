@@ -106,3 +106,27 @@ def test_head_route_tensor_core_psnr_within_005_db(F, dims, r, cap, sweeps, prec
     p_or, p_gpu = O.psnr(st.X, d["truth"]), O.psnr(g["X"], d["truth"])
     print(f"{precision} {dims}: PSNR oracle {p_or:.4f} GPU {p_gpu:.4f}, X rel err {rel(g['X'], st.X):.2e}")
     assert abs(p_gpu - p_or) <= 0.05
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_mixed_precision_finishes_in_fp32(F, precision):
+    """finish_fp32_at: tensor-core sweeps until rel_change <= 1e-3, FP32 sweeps
+    after; fctn_complete then reaches rel_change <= 1e-4 and the completed
+    tensor's PSNR matches the plain FP32 run's within 0.05 dB."""
+    from oracle import fctn_oracle as O
+    d = inputs(None, dims=(48, 40, 9), r=4, p=0.3, idx=75, noise=0.0, cap=None, dtype=np.float32)
+    out = {}
+    for prec, fin in (("fp32", 0.0), (precision, 1e-3)):
+        p = F.make_params(d["dims"], d["R"], precision=prec, order_policy="plain", finish_fp32_at=fin)
+        h = F.fctn_create(p)
+        try:
+            F.fctn_set_data(h, np.ascontiguousarray(d["Y"]), np.ascontiguousarray(d["mask"].astype(np.uint8)))
+            F.fctn_set_factors(h, [np.ascontiguousarray(a) for a in d["init"]])
+            X = np.empty(d["dims"], dtype=np.float32)
+            st = F.fctn_complete(h, 1e-4, 400, X)
+        finally:
+            F.fctn_destroy(h)
+        out[prec] = (st, O.psnr(X, d["truth"]))
+    st, ps = out[precision]
+    assert st["converged"] and st["rel_change"] <= 1e-4, st
+    assert abs(ps - out["fp32"][1]) <= 0.05

@@ -30,8 +30,30 @@ def test_results_identical_alone_and_in_mix(mods):
     F, S = mods
     jobs = S.mix_jobs(8, seed=7, rate=1000.0, shapes=SMALL, contract=_contract)
     mix = S.run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=40, max_jobs=3, keep_results=True, arrivals=False)
-    alone = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=40, keep_results=True)
+    alone = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=40, keep_results=True, arrivals=False)
     assert mix["failed"] == 0 and mix["jobs"] == len(jobs)
+    for j in jobs:
+        i = j["i"]
+        assert mix["infos"][i]["sweeps"] == alone["infos"][i]["t"]
+        np.testing.assert_array_equal(mix["results"][i], alone["results"][i])
+
+
+@pytest.mark.parametrize("group", [True, False])
+def test_grouped_sweeps_identical_alone_and_in_mix(mods, group):
+    """Jobs of one shape class sweep as one captured graph (re-launched while
+    the members stay, captured anew when one leaves); every result keeps the
+    bytes of the job run alone.  Without grouping each job launches its own
+    sweep graph."""
+    F, S = mods
+    jobs = S.mix_jobs(8, seed=17, rate=1000.0, shapes=[(40, 36, 12)], contract=_contract)
+    mix = S.run_mix(jobs, precision="fp32", tol=1e-4, max_sweeps=40, max_jobs=8, keep_results=True,
+                    arrivals=False, group=group)
+    alone = S.run_sequential(jobs, precision="fp32", tol=1e-4, max_sweeps=40, keep_results=True, arrivals=False)
+    assert mix["failed"] == 0 and mix["jobs"] == len(jobs)
+    if group:
+        assert mix["group_launches"] > mix["group_captures"] > 0
+    else:
+        assert mix["group_launches"] == 0
     for j in jobs:
         i = j["i"]
         assert mix["infos"][i]["sweeps"] == alone["infos"][i]["t"]
