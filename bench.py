@@ -237,6 +237,13 @@ def run_ours(args):
     initd = [torch.from_numpy(np.ascontiguousarray(a.astype(dt))).to(dev) for a in init]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     torch.cuda.synchronize()
+    # launch shapes from libfctn's autotuner (probe handles on the same
+    # inputs), before the timed region
+    tune = None
+    if not args.no_tune:
+        best, tms = F.fctn_autotune_tiles(p, Yd, Md, initd, sweeps=3, stream=stream)
+        p.tile_code = best
+        tune = {"tile_code": best, "sweep_ms": {str(c): round(v, 4) for c, v in tms.items()}}
     h = F.fctn_create(p, stream)
     try:
         F.fctn_set_data(h, Yd, Md)
@@ -336,7 +343,8 @@ def run_ours(args):
         "config": {"workload": f"{name}: {DESC[name]}", "dims": list(w["dims"]), "rank": w["r"], "sampling": w["p"],
                    "precision": precision, "reuse": True, "order_policy": "plain", "lambda": synth.LAMBDA,
                    "delta": synth.DELTA, "rho": synth.RHO, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{ws}", "graphs": True},
+                   "parallelism": f"replicas x{ws}", "graphs": True,
+                   "autotune": tune if tune else "off (built-in launch shapes)"},
         "step_ms_p50": statistics.median(step_ms), "step_ms_max": max(step_ms),
         "rel_change_last": st["rel_change"], "eig_sweeps_last": st["eig_sweeps"],
         "gpu_launches": int(launches),
@@ -351,11 +359,12 @@ def run_ours(args):
                 "step": f"set_data + set_factors from pinned host buffers, {e2e_sweeps} sweeps, X back to pinned host memory"},
     }
     if ws == 1 and not args.no_extras:
-        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps)
+        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps, tune=not args.no_tune)
         if name != "c2":
-            line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), args.steps, quality_sweeps=0)
+            line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), args.steps, quality_sweeps=0,
+                                                   tune=not args.no_tune)
         line["rank_growth"] = rank_growth_run(F, "c2", *gpu_inputs(F, "c2"))
-        line["serving"] = serving_mix(args.serve_jobs, tune=False)
+        line["serving"] = serving_mix(args.serve_jobs, tune=not args.no_tune)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -363,14 +372,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100, tol=1e-4, max_sweeps=500):
+def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100, tol=1e-4, max_sweeps=500,
+                    tune=True):
     """The same workload in every precision (plain order, reuse): sweeps/s
     (graphs, L2 flushed between sweeps), PSNR / SSIM against the truth
     (Sec. 4, computed by libfctn) after `quality_sweeps` sweeps from the same
     start, and time to tolerance (fctn_complete to rel < tol, at most
     max_sweeps sweeps, wall clock) with its final PSNR."""
     import torch
-    out, quality, ttt = {}, {}, {}
+    out, quality, ttt, tuned = {}, {}, {}, {}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     truth32 = np.ascontiguousarray(truth.astype(np.float32))
     Y32, M8 = np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8)
@@ -381,6 +391,9 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100,
         p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=prec,
                           order_policy="plain", finish_fp32_at=1e-3 if prec != "fp32" else 0.0)
         st = torch.cuda.Stream()
+        if tune:
+            p.tile_code, _ = F.fctn_autotune_tiles(p, Y32, M8, init32, sweeps=3, stream=st)
+            tuned[prec] = p.tile_code
         h = F.fctn_create(p, st)
         try:
             F.fctn_set_data(h, Y32, M8)
@@ -414,7 +427,7 @@ def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100,
         finally:
             F.fctn_destroy(h)
     res = {"unit": UNIT, "sweeps_per_s": out, "workload": name, "order_policy": "plain",
-           "finish_fp32_at": 1e-3}
+           "finish_fp32_at": 1e-3, "tile_code_autotuned": tuned or "off"}
     if quality_sweeps > 0:
         res.update({"quality_after_sweeps": max(quality_sweeps, steps + 3), "quality": quality,
                     "time_to_tol": {"tol": tol, "max_sweeps": max_sweeps, **ttt}})

@@ -130,6 +130,13 @@ typedef struct fctn_params {
                              core products' rounding floor), later sweeps (fctn_complete,
                              the server) use the FP32 CUDA-core products, so that
                              rel_change can reach smaller tolerances; 0 = never         */
+  int32_t tile_code;      /* launch shapes of the head-mode route (fctn_autotune_tiles),
+                             0 = built-in rules.  bit 0: CUDA-core products in TF32 /
+                             BF16 too; bits 1-2: pipeline stages of X_(1) M_1^T (rule,
+                             2, 4, 6); bits 3-4: its K split over about (304, 152, 608,
+                             76) CTAs; bits 5-6: K split of the CUDA-core contractions
+                             over about (304, 152, 608, 1) CTAs.  Only the summation
+                             order of the contractions changes with it                  */
 } fctn_params;
 
 typedef struct fctn_stats {
@@ -227,6 +234,16 @@ int fctn_quality(fctn_handle* h, const void* truth, int where, double* psnr, dou
  * probe's create / set / sweep calls. */
 int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors, int where,
                   const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best, double* ms_out);
+
+/* The autotuner of the head-mode route: times `sweeps` sweeps (after twice as
+ * many untimed ones) of a probe handle per tile code in cand[0..ncand) (NULL:
+ * the built-in list {0, 1, 2, 4, 8, 16, 32, 64, 96}, one choice changed per
+ * candidate) on the caller's inputs, and returns the fastest in *best and,
+ * if ms_out is not NULL, each candidate's ms per sweep.  Errors as
+ * fctn_autotune; a candidate outside [0, 127] is FCTN_E_ARG. */
+int fctn_autotune_tiles(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors,
+                        int where, const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best,
+                        double* ms_out);
 
 /* Copy factor k (FCTN shape) / the completed tensor X out. */
 int fctn_get_factor(fctn_handle* h, int k, void* out, int where);

@@ -736,6 +736,7 @@ int check_params(const fctn_params* p) {
     return fail(FCTN_E_ARG, "eig_max_sweeps %d outside [0, 1000]", p->eig_max_sweeps);
   if (!(p->eig_tol >= 0.0 && p->eig_tol < 1.0)) return fail(FCTN_E_ARG, "eig_tol must lie in [0, 1)");
   if (!(p->finish_fp32_at >= 0.0)) return fail(FCTN_E_ARG, "finish_fp32_at must be >= 0");
+  if (p->tile_code < 0 || p->tile_code > 127) return fail(FCTN_E_ARG, "tile_code %d outside [0, 127]", p->tile_code);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
@@ -935,7 +936,7 @@ int64_t max_offset(const View& v) {
 // Plan C = A (x) B (every shared label contracted) with C laid out as `C`.
 // The operand that holds C's innermost label plays B, so that consecutive
 // columns n are consecutive in C.
-int sg_plan(const View& A0, const View& B0, const View& C, SgPlanH* out, std::vector<int>* tabs) {
+int sg_plan(const View& A0, const View& B0, const View& C, SgPlanH* out, std::vector<int>* tabs, int split = 0) {
   const bool swap = C.n > 0 && A0.find(C.lab[C.n - 1]) >= 0;
   const View& A = swap ? B0 : A0;
   const View& B = swap ? A0 : B0;
@@ -979,7 +980,7 @@ int sg_plan(const View& A0, const View& B0, const View& C, SgPlanH* out, std::ve
   radix_offsets(nm, mext, ma, mc, am, cm);
   radix_offsets(nn, next, nb, nc, bn, cn);
   radix_offsets(nk, kext, ka, kbs, ak, bk);
-  sg_shape((int)M, (int)Nn, (int)K, &out->sh);
+  sg_shape((int)M, (int)Nn, (int)K, &out->sh, split);
   // loader lanes: along k when A's (B's) innermost contracted digit is
   // contiguous, else along m (n) when that digit is
   out->sh.a_mfast = (nk == 0 || ka[nk - 1] != 1) && nm > 0 && ma[nm - 1] == 1;
@@ -1057,6 +1058,9 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
   r.P0 = h->Pk[0];
   int rc = FCTN_OK;
   std::vector<int> t0;  // tables of this plan (appended at the end, or dropped)
+  // tile code (fctn_autotune_tiles): K-split target of the CUDA-core contractions
+  static const int kSgSplit[4] = {0, 152, 4 * 152, 1};
+  const int sgs = kSgSplit[(h->p.tile_code >> 5) & 3];
   auto track = [](int64_t* mx, int64_t v) { *mx = v > *mx ? v : *mx; };
   // M_0: factors 1 .. N-1 in ascending order
   {
@@ -1066,14 +1070,14 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
       View o = (t == N - 1) ? m0_view(h) : joint_view(cur, nx, &rc);
       if (rc) return fail(rc, "head route: chain intermediate has too many indices");
       if (t < N - 1) track(&r.u_elems, o.size());
-      if ((rc = sg_plan(cur, nx, o, &r.m0[r.nm0], &t0))) return rc;
+      if ((rc = sg_plan(cur, nx, o, &r.m0[r.nm0], &t0, sgs))) return rc;
       track(&r.part_main, (int64_t)sg_part_elems(r.m0[r.nm0].sh));
       r.nm0++;
       cur = o;
     }
   }
-  if ((rc = sg_plan(x_view(h), m0_view(h), factor_view(h, 0), &r.y0, &t0))) return rc;
-  if ((rc = sg_plan(x_view(h), factor_view(h, 0), z_view(h), &r.z, &t0))) return rc;
+  if ((rc = sg_plan(x_view(h), m0_view(h), factor_view(h, 0), &r.y0, &t0, sgs))) return rc;
+  if ((rc = sg_plan(x_view(h), factor_view(h, 0), z_view(h), &r.z, &t0, sgs))) return rc;
   track(&r.part_main, (int64_t)sg_part_elems(r.y0.sh));
   track(&r.part_main, (int64_t)sg_part_elems(r.z.sh));
   // right-hand sides of k >= 1: Z contracted with the factors t != 0, k,
@@ -1091,7 +1095,7 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
       View o = (q == n - 1) ? factor_view(h, k) : joint_view(cur, nx, &rc);
       if (rc) return fail(rc, "head route: chain intermediate has too many indices");
       if (q < n - 1) track(&r.u_elems, o.size());
-      if ((rc = sg_plan(cur, nx, o, &r.ys[k][q], &t0))) return rc;
+      if ((rc = sg_plan(cur, nx, o, &r.ys[k][q], &t0, sgs))) return rc;
       track(&r.part_main, (int64_t)sg_part_elems(r.ys[k][q].sh));
       r.yfac[k][q] = ids[q];
       cur = o;
@@ -1100,7 +1104,7 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
   }
   // factor Grams and, per k, their chain over t != k (ascending)
   for (int t = 0; t < N; ++t) {
-    if ((rc = sg_plan(factor_view(h, t), factor_primed_view(h, t), hgram_view(h, t), &r.hg[t], &t0))) return rc;
+    if ((rc = sg_plan(factor_view(h, t), factor_primed_view(h, t), hgram_view(h, t), &r.hg[t], &t0, sgs))) return rc;
     track(&r.part_side, (int64_t)sg_part_elems(r.hg[t].sh));
   }
   for (int k = 0; k < N; ++k) {
@@ -1113,7 +1117,7 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
       View o = (q == n - 1) ? hgram_view(h, k) : joint_view(cur, nx, &rc);
       if (rc) return fail(rc, "head route: Gram chain intermediate has too many indices");
       if (q < n - 1) track(&r.e_elems, o.size());
-      if ((rc = sg_plan(cur, nx, o, &r.env[k][q - 1], &t0))) return rc;
+      if ((rc = sg_plan(cur, nx, o, &r.env[k][q - 1], &t0, sgs))) return rc;
       track(&r.part_side, (int64_t)sg_part_elems(r.env[k][q - 1].sh));
       cur = o;
     }
@@ -1125,15 +1129,21 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
     return FCTN_OK;
   }
   // tensor-core products: every operand row a multiple of 16 bytes (TMA)
-  if (h->tc) {
+  if (h->tc && !(h->p.tile_code & 1)) {  // tile code bit 0: CUDA-core products instead
     const int elem = h->p.precision == FCTN_BF16 ? 2 : 4, al = 16 / elem;
+    static const int kTySplit[4] = {2 * 152, 152, 4 * 152, 76};
+    static const int kTyStages[4] = {0, 2, 4, 6};
     const int64_t I0 = h->I[0];
     if (r.P0 % al == 0 && I0 % al == 0 && r.P0 < ((int64_t)1 << 31)) {
       r.tc = true;
       r.bf16 = elem == 2;
       r.ldt = I0;
       r.ld0 = (r.s0 + al - 1) / al * al;
-      tg_shape((int)I0, (int)r.s0, (int)r.P0, elem, 2 * 152, &r.ty);
+      tg_shape((int)I0, (int)r.s0, (int)r.P0, elem, kTySplit[(h->p.tile_code >> 3) & 3], &r.ty);
+      if (kTyStages[(h->p.tile_code >> 1) & 3]) {
+        r.ty.S = kTyStages[(h->p.tile_code >> 1) & 3];
+        while (r.ty.S > 2 && tg_smem_bytes(r.ty.BN, r.ty.S) > 200 * 1024) --r.ty.S;
+      }
       tg_shape((int)r.P0, (int)r.s0, (int)I0, elem, 0, &r.tz);
       tg_shape((int)r.P0, (int)I0, (int)r.s0, 4, 0, &r.tf);  // the reconstruction stays TF32 (see route_build_m0)
       r.ty.mode = TG_PARTIAL;
@@ -2300,6 +2310,64 @@ int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, cons
       if (ce != cudaSuccess) rc = fail(FCTN_E_CUDA, "fctn_autotune: %s", cudaGetErrorString(ce));
       if (!rc && !(rc = fctn_pam_sweep(h, 0, &st)) && st.status != FCTN_OK)
         rc = fail(st.status, "fctn_autotune: probe sweep failed with status %d", st.status);
+    }
+    const int drc = fctn_destroy(h);
+    if (!rc) rc = drc;
+    if (rc) break;
+    const double per = (double)ms / sweeps;
+    if (ms_out) ms_out[i] = per;
+    if (i == 0 || per < best_ms) {
+      best_ms = per;
+      *best = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int fctn_autotune_tiles(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors,
+                        int where, const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best,
+                        double* ms_out) {
+  // the built-in rule; CUDA-core products; 2 / 4 pipeline stages; K split of
+  // X_(1) M_1^T over 152 / 608 CTAs; K split of the CUDA-core contractions
+  // over 152 / 608 CTAs / none
+  static const int32_t builtin[9] = {0, 1, 2, 4, 8, 16, 32, 64, 96};
+  if (!p || !Y || !mask || !factors || !best) return fail(FCTN_E_ARG, "NULL argument");
+  if (sweeps < 1 || sweeps > 1000) return fail(FCTN_E_ARG, "sweeps %d outside [1, 1000]", sweeps);
+  if (!cand) {
+    cand = builtin;
+    ncand = 9;
+  }
+  if (ncand < 1 || ncand > 64) return fail(FCTN_E_ARG, "ncand %d outside [1, 64]", ncand);
+  for (int i = 0; i < ncand; ++i)
+    if (cand[i] < 0 || cand[i] > 127) return fail(FCTN_E_ARG, "candidate %d outside [0, 127]", cand[i]);
+  int rc = check_params(p);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(FCTN_E_CUDA, "fctn_autotune_tiles: cudaEventCreate failed");
+  }
+  double best_ms = 0.0;
+  for (int i = 0; i < ncand && rc == FCTN_OK; ++i) {
+    fctn_params q = *p;
+    q.tile_code = cand[i];
+    fctn_handle* h = nullptr;
+    if ((rc = fctn_create(&q, cuda_stream, &h))) break;
+    fctn_stats st{};
+    float ms = 0.f;
+    if (!(rc = fctn_set_data(h, Y, mask, where)) && !(rc = fctn_set_factors(h, factors, where)) &&
+        !(rc = fctn_pam_sweep(h, 2 * sweeps, nullptr))) {
+      cudaError_t ce = cudaEventRecord(e0, h->st);
+      if (ce == cudaSuccess) rc = fctn_pam_sweep(h, sweeps, nullptr);
+      if (ce == cudaSuccess && !rc) ce = cudaEventRecord(e1, h->st);
+      if (ce == cudaSuccess && !rc) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess && !rc) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) rc = fail(FCTN_E_CUDA, "fctn_autotune_tiles: %s", cudaGetErrorString(ce));
+      if (!rc && !(rc = fctn_pam_sweep(h, 0, &st)) && st.status != FCTN_OK)
+        rc = fail(st.status, "fctn_autotune_tiles: probe sweep failed with status %d", st.status);
     }
     const int drc = fctn_destroy(h);
     if (!rc) rc = drc;

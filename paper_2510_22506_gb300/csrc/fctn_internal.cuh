@@ -139,7 +139,7 @@ struct SgShape {
 struct SgTabs {
   const int *am, *cm, *bn, *cn, *ak, *bk;
 };
-void sg_shape(int M, int N, int K, SgShape* sh);
+void sg_shape(int M, int N, int K, SgShape* sh, int split_ctas = 0);  // split_ctas: CTA target of a K split
 size_t sg_part_elems(const SgShape& sh);
 void launch_sgemm(const SgShape& sh, const SgTabs& t, const float* A, const float* B, float* C, float* part,
                   cudaStream_t st);

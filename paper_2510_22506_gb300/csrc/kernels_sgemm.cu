@@ -245,16 +245,18 @@ int grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-void sg_shape(int M, int N, int K, SgShape* sh) {
+void sg_shape(int M, int N, int K, SgShape* sh, int split_ctas) {
   sh->a_mfast = sh->b_nfast = 0;
   sh->M = M;
   sh->N = N;
   sh->K = K;
   const int tiles = ((M + SG_BM - 1) / SG_BM) * ((N + SG_BN - 1) / SG_BN);
   int ks = 1;
-  // split K when the tiles alone would leave most SMs idle and K is long
-  if (tiles < 152 && K >= 8 * SG_BK) {
-    ks = (2 * 152 + tiles - 1) / tiles;
+  // split K when the tiles alone would leave most SMs idle and K is long:
+  // about split_ctas CTAs in all (0 = two per SM, 1 = no split)
+  const int target = split_ctas > 0 ? split_ctas : 2 * 152;
+  if (tiles < target && K >= 8 * SG_BK) {
+    ks = (target + tiles - 1) / tiles;
     const int maxks = K / (4 * SG_BK);
     ks = ks < maxks ? ks : maxks;
     if (ks < 1) ks = 1;

@@ -49,6 +49,7 @@ class fctn_params(ctypes.Structure):
         ("eig_max_sweeps", ctypes.c_int32),
         ("eig_tol", ctypes.c_double),
         ("finish_fp32_at", ctypes.c_double),
+        ("tile_code", ctypes.c_int32),
     ]
 
 
@@ -103,7 +104,8 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_get_X", "fctn_sync", "fctn_launch_count", "fctn_destroy", "fctn_set_graphs", "fctn_profile",
             "fctn_profile_read", "fctn_contract_noalloc", "fctn_server_create", "fctn_server_submit",
             "fctn_server_step", "fctn_server_poll", "fctn_server_result", "fctn_server_stats", "fctn_server_destroy",
-            "fctn_server_finished", "fctn_server_group_stats", "fctn_quality", "fctn_grow_ranks", "fctn_autotune")
+            "fctn_server_finished", "fctn_server_group_stats", "fctn_quality", "fctn_grow_ranks", "fctn_autotune",
+            "fctn_autotune_tiles")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6, "env": 7, "rhs2": 8,
       "eigaux": 9}
 
@@ -162,7 +164,7 @@ def fctn_version():
 
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
                 laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
-                eig_max_sweeps=0, eig_tol=0.0, finish_fp32_at=0.0):
+                eig_max_sweeps=0, eig_tol=0.0, finish_fp32_at=0.0, tile_code=0):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -191,6 +193,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     p.eig_max_sweeps = int(eig_max_sweeps)
     p.eig_tol = float(eig_tol)
     p.finish_fp32_at = float(finish_fp32_at)
+    p.tile_code = int(tile_code)
     return p
 
 
@@ -323,6 +326,35 @@ def fctn_autotune(params, Y, mask, factors, candidates=None, sweeps=3, stream=No
         sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(lib.fctn_autotune(ctypes.byref(params), py, pm, arr, where, carr if candidates is not None else None,
                              len(cand), int(sweeps), sp, ctypes.byref(best), ms))
+    return best.value, {c: ms[i] for i, c in enumerate(cand)}
+
+
+TILE_CANDIDATES = (0, 1, 2, 4, 8, 16, 32, 64, 96)
+
+
+def fctn_autotune_tiles(params, Y, mask, factors, candidates=None, sweeps=3, stream=None):
+    """Fastest tile code (fctn_params.tile_code) of the head-mode route for
+    these parameters and inputs.  Returns (best, {candidate: mean sweep ms})."""
+    py, wy = _ptr(Y)
+    pm, wm = _ptr(mask)
+    ptrs = []
+    for a in factors:
+        pa, wa = _ptr(a)
+        ptrs.append(pa)
+        if wa != wy:
+            raise ValueError("Y, mask and factors must all be on the host or all on the device")
+    if wm != wy:
+        raise ValueError("Y, mask and factors must all be on the host or all on the device")
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    cand = list(TILE_CANDIDATES if candidates is None else candidates)
+    carr = (ctypes.c_int32 * len(cand))(*[int(c) for c in cand])
+    ms = (ctypes.c_double * len(cand))()
+    best = ctypes.c_int32(0)
+    sp = None
+    if stream is not None:
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.fctn_autotune_tiles(ctypes.byref(params), py, pm, arr, wy, carr if candidates is not None else None,
+                                   len(cand), int(sweeps), sp, ctypes.byref(best), ms))
     return best.value, {c: ms[i] for i, c in enumerate(cand)}
 
 

@@ -66,13 +66,14 @@ def job_params(job, precision, tuner=None):
                       precision=precision, reuse=True, order_policy="plain",
                       finish_fp32_at=FINISH_FP32_AT if precision in ("tf32", "bf16") else 0.0)
     if tuner is not None:
-        p.rhs_ctas = tuner.get(job, p)
+        p.tile_code = tuner.get(job, p)
     return p
 
 
 class TuneCache:
-    """Launch shapes (fctn_params.rhs_ctas) per job class (dims, ranks,
-    precision), chosen by libfctn's autotuner on the first job of the class
+    """Tile codes (fctn_params.tile_code: tensor-core or CUDA-core products,
+    pipeline depth, K splits) per job class (dims, ranks, precision), chosen
+    by libfctn's autotuner (fctn_autotune_tiles) on the first job of the class
     and reused for the rest; `fill` tunes every class of a job list up front,
     as a server would load a stored cache before taking traffic."""
 
@@ -90,9 +91,10 @@ class TuneCache:
         if k not in self.table:
             dt = F.elem_dtype(p)
             t0 = time.perf_counter()
-            best, _ = F.fctn_autotune(p, np.ascontiguousarray(job["Y"].astype(dt)), job["mask"].astype(np.uint8),
-                                      [np.ascontiguousarray(a.astype(dt)) for a in job["init"]],
-                                      candidates=self.candidates, sweeps=self.sweeps)
+            best, _ = F.fctn_autotune_tiles(p, np.ascontiguousarray(job["Y"].astype(dt)),
+                                            job["mask"].astype(np.uint8),
+                                            [np.ascontiguousarray(a.astype(dt)) for a in job["init"]],
+                                            candidates=self.candidates, sweeps=self.sweeps)
             self.tune_s += time.perf_counter() - t0
             self.table[k] = best
         return self.table[k]

@@ -63,6 +63,10 @@ def test_footprint_scales_with_size(F):
     dict(refine_steps=99),
     dict(rhs_ctas=-1),
     dict(rhs_ctas=5000),
+    dict(tile_code=-1),
+    dict(tile_code=128),
+    dict(eig_tol=1.5),
+    dict(finish_fp32_at=-1.0),
 ])
 def test_invalid_params_rejected(F, bad):
     dims = bad.pop("dims", (30, 30, 10))

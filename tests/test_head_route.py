@@ -130,3 +130,32 @@ def test_mixed_precision_finishes_in_fp32(F, precision):
     st, ps = out[precision]
     assert st["converged"] and st["rel_change"] <= 1e-4, st
     assert abs(ps - out["fp32"][1]) <= 0.05
+
+
+# ---- every launch shape the autotuner may pick keeps parity ----------------
+@pytest.fixture(scope="module")
+def tile_case():
+    d = inputs(None, dims=(136, 40, 12), r=5, p=0.3, idx=76, noise=0.0, cap=None, dtype=np.float32)
+    st, _ = oracle_run(d, 6, policy="plain")
+    return d, st
+
+
+@pytest.mark.parametrize("code", [0, 1, 2, 4, 6, 8, 16, 24, 32, 64, 96])
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_tile_codes_keep_parity(F, tile_case, code, precision):
+    """Tile codes change only launch shapes and summation orders: FP32 stays
+    within 1e-4 of the oracle, TF32 within 3e-3 (X) after 6 sweeps."""
+    d, st = tile_case
+    g = gpu_run(F, d, 6, precision=precision, policy="plain", tile_code=code)
+    tol = 1e-4 if precision == "fp32" else 3e-3
+    assert g["stats"]["status"] == 0
+    assert rel(g["X"], st.X) <= tol, (code, rel(g["X"], st.X))
+
+
+def test_tile_autotuner_picks_a_candidate(F):
+    d = inputs(None, dims=(48, 40, 9), r=4, p=0.3, idx=77, noise=0.0, cap=None, dtype=np.float32)
+    p = F.make_params(d["dims"], d["R"], precision="tf32", order_policy="plain")
+    best, ms = F.fctn_autotune_tiles(p, np.ascontiguousarray(d["Y"]), d["mask"].astype(np.uint8),
+                                     [np.ascontiguousarray(a) for a in d["init"]], sweeps=2)
+    assert best in F.TILE_CANDIDATES and set(ms) == set(F.TILE_CANDIDATES)
+    assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
