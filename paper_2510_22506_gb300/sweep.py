@@ -1,6 +1,7 @@
 """Run PAM sweeps of a named synthetic workload through libfctn.
 
-    python -m paper_2510_22506_gb300.sweep --workload c2 --precision fp32 --sweeps 3 [--time] [--rhs-ctas N]
+    python -m paper_2510_22506_gb300.sweep --workload c4 --precision tf32 --sweeps 3 [--time]
+        [--order plain|alternate] [--reuse 1] [--tile-code N] [--rhs-ctas N]
 
 Workloads (seeded, see synth.WORKLOADS): c1 30x30x10, c2 256x256x31,
 c3 144x176x3x50, c4 256x256x31x8.  The ground-truth tensor is contracted by
@@ -45,10 +46,12 @@ def main(argv=None):
     ap.add_argument("--reuse", type=int, default=1)
     ap.add_argument("--time", action="store_true")
     ap.add_argument("--rhs-ctas", type=int, default=0, help="launch shape of the Gram / RHS kernel (0 = built-in)")
+    ap.add_argument("--order", default="plain", choices=["plain", "alternate"])
+    ap.add_argument("--tile-code", type=int, default=0, help="launch shapes of the head-mode route (0 = built-in)")
     a = ap.parse_args(argv)
     truth, Y, mask, init, R = library_inputs(a.workload)
     p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=a.precision,
-                      reuse=bool(a.reuse), rhs_ctas=a.rhs_ctas)
+                      reuse=bool(a.reuse), rhs_ctas=a.rhs_ctas, order_policy=a.order, tile_code=a.tile_code)
     dt = F.elem_dtype(p)
     out = {"workload": a.workload, "precision": a.precision, "sweeps": a.sweeps}
     if a.time:
