@@ -97,6 +97,19 @@ enum { FCTN_HOST = 0, FCTN_DEVICE = 1 };
  * in FP64. */
 enum { FCTN_GRAM_AUTO = 0, FCTN_GRAM_DIRECT = 1, FCTN_GRAM_FACTORED = 2 };
 
+/* How the Sylvester equation of Eq. 5 is solved (both give its unique
+ * solution, with other rounding).  EIG: Eq. 8 as printed, through the
+ * eigendecomposition G = C Phi C^T (Eq. 7; Jacobi on the GPU).  CHOL: in the
+ * real eigenbasis Q of L_k, Eq. 6 is block diagonal: row i of W = Q^T A
+ * solves W_i (G + (lam mu_i + rho) I) = (Q^T Y)_i, one FP32 Cholesky
+ * factorization per distinct mu_i (floor(I_k / 2) + 1 of them), no
+ * eigendecomposition; FP32 / TF32 / BF16 and s_k <= 256 only
+ * (FCTN_E_UNSUPPORTED otherwise).  A pivot that is not positive (G + c I not
+ * positive definite) is FCTN_E_SINGULAR, as min T <= 0 is for EIG.  AUTO:
+ * CHOL where it applies, else EIG.  The FP64 refinement (refine_steps)
+ * follows either. */
+enum { FCTN_SOLVE_AUTO = 0, FCTN_SOLVE_EIG = 1, FCTN_SOLVE_CHOL = 2 };
+
 typedef struct fctn_params {
   int32_t order;                                  /* N, 2 <= N <= FCTN_MAX_ORDER       */
   int32_t precision;                              /* FCTN_FP64 / FP32 / TF32 / BF16    */
@@ -137,6 +150,7 @@ typedef struct fctn_params {
                              76) CTAs; bits 5-6: K split of the CUDA-core contractions
                              over about (304, 152, 608, 1) CTAs.  Only the summation
                              order of the contractions changes with it                  */
+  int32_t solve_method;   /* FCTN_SOLVE_*: the solve of Eq. 5 (see above)               */
 } fctn_params;
 
 typedef struct fctn_stats {
@@ -264,8 +278,8 @@ enum {
   FCTN_KC_MERGED = 0,   /* pair intermediates / merged tensors M_k (contractions)      */
   FCTN_KC_GRAM = 1,     /* Gram + right-hand side, split over the columns of M_k        */
   FCTN_KC_REDUCE = 2,   /* fixed-order reduction of the split partials                  */
-  FCTN_KC_EIG = 3,      /* Gram eigendecomposition                                      */
-  FCTN_KC_SOLVE = 4,    /* Eq. 8 solve and its FP64 refinement                          */
+  FCTN_KC_EIG = 3,      /* Gram eigendecomposition, or the shifted Cholesky factors     */
+  FCTN_KC_SOLVE = 4,    /* Eq. 8 (or Cholesky) solve and its FP64 refinement            */
   FCTN_KC_XUPDATE = 5,  /* X update of Eq. 10 fused with F = A_k(k) M_k and the sums    */
   FCTN_KC_MISC = 6,     /* trace terms, finalisation, staging                           */
   FCTN_KC_ENV = 7,      /* Grams of the factors and their chains (Gram of M_k)          */

@@ -170,6 +170,8 @@ struct fctn_handle {
   int* eig_used = nullptr;
   int eig_cap = 60;  // Jacobi sweep cap per eigendecomposition (fctn_params.eig_max_sweeps)
   float* eig_rec = nullptr;  // rotation blocks of the large FP32 eigensolver (128 < s <= 224)
+  bool chol[FCTN_MAX_ORDER] = {};  // factor k solved by shifted Cholesky (FCTN_SOLVE_CHOL)
+  float *cholL = nullptr, *cholD = nullptr;  // its packed factors and diagonal-block inverses
   void* Ck[FCTN_MAX_ORDER] = {};
   bool cvalid[FCTN_MAX_ORDER] = {};
   double lam_min[FCTN_MAX_ORDER] = {};
@@ -737,12 +739,24 @@ int check_params(const fctn_params* p) {
   if (!(p->eig_tol >= 0.0 && p->eig_tol < 1.0)) return fail(FCTN_E_ARG, "eig_tol must lie in [0, 1)");
   if (!(p->finish_fp32_at >= 0.0)) return fail(FCTN_E_ARG, "finish_fp32_at must be >= 0");
   if (p->tile_code < 0 || p->tile_code > 127) return fail(FCTN_E_ARG, "tile_code %d outside [0, 127]", p->tile_code);
+  if (p->solve_method < FCTN_SOLVE_AUTO || p->solve_method > FCTN_SOLVE_CHOL)
+    return fail(FCTN_E_ARG, "unknown solve method %d", p->solve_method);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
   for (int k = 0; k < p->order; ++k) {
     if (p->dims[k] < 1 || p->dims[k] > (1 << 24)) return fail(FCTN_E_ARG, "dims[%d] = %lld out of range", k, (long long)p->dims[k]);
     if (!(p->lambda[k] >= 0) || !(p->delta[k] >= 0)) return fail(FCTN_E_ARG, "lambda/delta[%d] must be >= 0", k);
     for (int t = k + 1; t < p->order; ++t)
       if (p->ranks[k][t] < 1 || p->ranks[k][t] > 64) return fail(FCTN_E_ARG, "rank R[%d][%d] = %d out of range", k, t, p->ranks[k][t]);
+  }
+  if (p->solve_method == FCTN_SOLVE_CHOL) {
+    if (p->precision == FCTN_FP64) return fail(FCTN_E_UNSUPPORTED, "the Cholesky solve is FP32 (precision FP64 given)");
+    for (int k = 0; k < p->order; ++k) {
+      int64_t sk = 1;
+      for (int t = 0; t < p->order; ++t)
+        if (t != k) sk *= p->ranks[k < t ? k : t][k < t ? t : k];
+      if (!chol_supported((int)(sk > (1 << 20) ? (1 << 20) : sk)))
+        return fail(FCTN_E_UNSUPPORTED, "the Cholesky solve needs s_k <= 256 (s_%d = %lld)", k, (long long)sk);
+    }
   }
   // every chain intermediate of m factors has m (N - m + 1) labels at most
   for (int m = 1; m <= p->order; ++m)
@@ -771,6 +785,19 @@ void fill_shapes(fctn_handle* h, const fctn_params* p) {
   h->esz = h->f64 ? 8 : 4;
   h->tc = (p->precision == FCTN_TF32 || p->precision == FCTN_BF16);
   h->eig_cap = p->eig_max_sweeps > 0 ? p->eig_max_sweeps : 60;
+  for (int k = 0; k < h->N; ++k)
+    h->chol[k] = !h->f64 && p->solve_method != FCTN_SOLVE_EIG && chol_supported((int)h->s[k]);
+}
+
+// Floats of the shared Cholesky buffers (factors, diagonal-block inverses).
+void chol_floats(const fctn_handle* h, size_t* nl, size_t* nd) {
+  *nl = 0;
+  *nd = 0;
+  for (int k = 0; k < h->N; ++k)
+    if (h->chol[k]) {
+      *nl = std::max(*nl, chol_factor_floats((int)h->I[k], (int)h->s[k]));
+      *nd = std::max(*nd, chol_dinv_floats((int)h->I[k], (int)h->s[k]));
+    }
 }
 
 struct Sizes {
@@ -1253,6 +1280,9 @@ size_t footprint(const fctn_handle* h) {
     b += rec * 4;  // rotation record of the large eigensolver
   }
   for (int k = 0; k < h->N; ++k) b += h->s[k] * h->s[k] * se;  // warm-start eigenvectors
+  size_t nl, nd;
+  chol_floats(h, &nl, &nd);
+  b += (nl + nd) * 4;  // Cholesky factors
   b += (z.red_blocks * 3 + h->N * 32 + 8) * 8 + 16;
   int64_t stage = h->P > z.maxfac ? h->P : z.maxfac;
   b += stage * e + h->P;                                  // staging
@@ -1299,6 +1329,33 @@ double eig_tol_eff(const fctn_handle* h) {
   if (h->p.eig_tol > 0.0) return h->p.eig_tol;
   if (h->f64) return 0.0;
   return h->p.refine_steps >= 2 ? 2e-4 : h->p.refine_steps == 1 ? 2e-5 : 0.0;
+}
+
+// Factorization step of the FP32 solve of factor k on stream st: the shifted
+// Cholesky factors of G + (lam mu_j + rho) I, or the eigendecomposition of G
+// (Eq. 7) warm-started from the previous sweep's eigenbasis.
+void prep_f32(fctn_handle* h, int k, cudaStream_t st) {
+  const int I = (int)h->I[k], s = (int)h->s[k];
+  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
+  if (h->chol[k]) {
+    launch_chol_factor((const float*)h->Gs, I, s, h->p.lambda[k], sgn * (2.0 + h->p.delta[k]), -sgn, h->p.rho,
+                       h->cholL, h->cholD, h->status, st);
+    return;
+  }
+  launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, h->cvalid[k] ? 1 : 0,
+                 h->eig_cap, h->lam_min[k] + h->p.rho, h->status, h->eig_used + k, st, h->eig_rec, eig_tol_eff(h));
+}
+int prep_f32_launches(const fctn_handle* h, int k) {
+  return h->chol[k] ? 1 : eig_launches((int)h->s[k], h->cvalid[k] ? 1 : 0, h->eig_rec != nullptr);
+}
+// Forward half of the FP32 solve of factor k: W from the right-hand side R.
+void fwd_f32(fctn_handle* h, int k, const float* R, float* W) {
+  const int I = (int)h->I[k], s = (int)h->s[k];
+  if (h->chol[k])
+    launch_chol_solve(h->QT32[k], R, I, s, h->cholL, h->cholD, W, h->status, h->st);
+  else
+    launch_solve_fwd_f32(h->QT32[k], R, (const float*)h->Ck[k], h->Lam[k], (const float*)h->Phi, h->p.lambda[k],
+                         h->p.rho, I, s, W, h->status, h->st);
 }
 
 // Eqs. 5-9 for factor k; M_k is formed on chip from its pair operands L, R
@@ -1349,9 +1406,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       } else {
         LAUNCH_ON(3, launch_fact_gram_f32(fg, (const float*)L, (const float*)R, (float*)HL, (float*)HR, s, h->Gd,
                                           (float*)h->Gs, fst));
-        LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
-                  launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                 h->eig_cap, tmin, h->status, h->eig_used + k, fst, h->eig_rec, eig_tol_eff(h)));
+        LAUNCH_ON(prep_f32_launches(h, k), prep_f32(h, k, fst));
       }
       if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
     } else if (h->f64) {
@@ -1409,15 +1464,12 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
            launch_reduce_gram_rhs_f32((const float*)h->part, g, h->A64[k], rho, h->Gd, h->Yd, (float*)h->Gs,
                                       (float*)h->Ys, h->st));
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-    if (!fork)
-      LAUNCH(FCTN_KC_EIG, 0.0, 0.0,
-             launch_eig_f32((const float*)h->Gs, Ck, Phi, (float*)h->gwork, s, warm, h->eig_cap, tmin, h->status,
-                            h->eig_used + k, h->st, h->eig_rec, eig_tol_eff(h)));
-    if (!fork) h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
+    if (!fork) {
+      LAUNCH(FCTN_KC_EIG, 0.0, 0.0, prep_f32(h, k, h->st));
+      h->launches += prep_f32_launches(h, k) - 1;
+    }
     const int nref = h->p.refine_steps;
-    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
-           launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
-                                h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
     LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
            launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
                                 nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
@@ -1425,9 +1477,7 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       if (r > 0)
         LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
                launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
-             launch_solve_fwd_f32(h->QT32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
-                                  h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
       LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
              launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
                                   c1, nullptr, h->status, h->st));
@@ -1522,7 +1572,9 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
   const double bwd_flops = 2.0 * (double)I * I * s;
   const double resid_flops = 2.0 * (double)I * s * s;
   float *Ck = (float*)h->Ck[k], *Phi = (float*)h->Phi, *Z = (float*)h->Z;
-  if (!eig_done && eig_is_big(s)) {  // the two stages timed apart
+  if (!eig_done && h->chol[k]) {
+    LAUNCH(FCTN_KC_EIG, 0.0, (double)chol_groups(I) * s * s * s / 3.0, prep_f32(h, k, h->st));
+  } else if (!eig_done && eig_is_big(s)) {  // the two stages timed apart
     const double ss = (double)s * s;
     if (warm) {
       LAUNCH(FCTN_KC_EIGAUX, 0.0, 8.0 * ss * s,
@@ -1539,9 +1591,7 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
     h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
   }
   const int nref = h->p.refine_steps;
-  LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
-         launch_solve_fwd_f32(h->QT32[k], (const float*)h->Ys, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
-                              h->st));
+  LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
   LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
          launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
                               nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
@@ -1549,9 +1599,7 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
     if (r > 0)
       LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
              launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops,
-           launch_solve_fwd_f32(h->QT32[k], (const float*)h->Rs, Ck, h->Lam[k], Phi, lam, rho, I, s, Z, h->status,
-                                h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
     LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
            launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
                                 c1, nullptr, h->status, h->st));
@@ -1625,9 +1673,7 @@ int route_sweep(fctn_handle* h) {
       }
       if (fork) {
         LAUNCH_ON(1, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
-        LAUNCH_ON(eig_launches(s, warm, h->eig_rec != nullptr),
-                  launch_eig_f32((const float*)h->Gs, (float*)h->Ck[k], (float*)h->Phi, (float*)h->gwork, s, warm,
-                                 h->eig_cap, tmin, h->status, h->eig_used + k, gs, h->eig_rec, eig_tol_eff(h)));
+        LAUNCH_ON(prep_f32_launches(h, k), prep_f32(h, k, gs));
         if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
       } else {
         LAUNCH(FCTN_KC_ENV, 0.0, 0.0, launch_finish_gram((float*)h->Gs, h->Gd, s, gs));
@@ -2024,6 +2070,14 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     size_t rec = 0;
     for (int k = 0; k < h->N; ++k) rec = std::max(rec, eig_record_floats((int)h->s[k]));
     if (rec) A_(h->eig_rec, rec * 4);
+  }
+  {
+    size_t nl, nd;
+    chol_floats(h, &nl, &nd);
+    if (nl) {
+      A_(h->cholL, nl * 4);
+      A_(h->cholD, nd * 4);
+    }
   }
   A_(h->status, 16);
   A_(h->eig_used, FCTN_MAX_ORDER * sizeof(int));

@@ -158,6 +158,21 @@ void launch_transpose_bf16(const float* src, int64_t rows, int64_t cols, int64_t
 void launch_copy_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst, int64_t ldd,
                       cudaStream_t st);
 
+// ---- kernels_chol.cu --------------------------------------------------------
+// Shifted-Cholesky solve of Eq. 5 (FCTN_SOLVE_CHOL): floor(I / 2) + 1 groups
+// of basis rows sharing lam mu_i + rho; per group the packed factor of
+// G + c I and the inverses of its 32 x 32 diagonal blocks.
+int chol_groups(int I);
+bool chol_supported(int s);
+size_t chol_factor_floats(int I, int s);
+size_t chol_dinv_floats(int I, int s);
+// L, Dinv of every group from the FP32 Gram G (s x s); c0, c1: the stencil of L_k.
+void launch_chol_factor(const float* G, int I, int s, double lam, double c0, double c1, double rho, float* L,
+                        float* Dinv, int* status, cudaStream_t st);
+// W (I x s) with W_i (G + c_i I) = (Q^T R)_i, from the factors of launch_chol_factor.
+void launch_chol_solve(const float* QT, const float* R, int I, int s, const float* L, const float* Dinv, float* W,
+                       int* status, cudaStream_t st);
+
 // ---- kernels_tma.cu ---------------------------------------------------------
 // D[M x N] = A[M x K] B[N x K]^T on tcgen05 with TMA-fed operands (both
 // K-major); see kernels_tma.cu.  Epilogue modes:

@@ -50,6 +50,7 @@ class fctn_params(ctypes.Structure):
         ("eig_tol", ctypes.c_double),
         ("finish_fp32_at", ctypes.c_double),
         ("tile_code", ctypes.c_int32),
+        ("solve_method", ctypes.c_int32),
     ]
 
 
@@ -162,9 +163,12 @@ def fctn_version():
     return lib.fctn_version().decode()
 
 
+SOLVE_METHODS = {"auto": 0, "eig": 1, "chol": 2}
+
+
 def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=True, order_policy="alternate",
                 laplacian_sign="psd", refine_steps=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
-                eig_max_sweeps=0, eig_tol=0.0, finish_fp32_at=0.0, tile_code=0):
+                eig_max_sweeps=0, eig_tol=0.0, finish_fp32_at=0.0, tile_code=0, solve_method="auto"):
     """fctn_params from Python values; R is an N x N symmetric rank matrix."""
     N = len(dims)
     p = fctn_params()
@@ -194,6 +198,7 @@ def make_params(dims, R, lam=0.01, delta=0.5, rho=0.1, precision="fp32", reuse=T
     p.eig_tol = float(eig_tol)
     p.finish_fp32_at = float(finish_fp32_at)
     p.tile_code = int(tile_code)
+    p.solve_method = SOLVE_METHODS[solve_method] if isinstance(solve_method, str) else int(solve_method)
     return p
 
 

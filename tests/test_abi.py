@@ -67,6 +67,7 @@ def test_footprint_scales_with_size(F):
     dict(tile_code=128),
     dict(eig_tol=1.5),
     dict(finish_fp32_at=-1.0),
+    dict(solve_method=3),
 ])
 def test_invalid_params_rejected(F, bad):
     dims = bad.pop("dims", (30, 30, 10))
@@ -133,3 +134,16 @@ def test_order8_planning_stays_in_bounds(F):
     rc = F.lib.fctn_contract_noalloc(N, d, r, F.FCTN_FP32, fake, ctypes.c_void_p(256), None)
     assert rc == F.FCTN_E_ARG
     assert "scratch" in F.fctn_last_error()
+
+
+@pytest.mark.parametrize("kw", [dict(precision="fp64", solve_method="chol"),
+                                dict(precision="fp32", solve_method="chol", r=17)])
+def test_cholesky_solve_limits(F, kw):
+    """The Cholesky solve is FP32 with s_k <= 256: FP64, or s = 17^2 = 289,
+    is a valid request that it does not serve (AUTO takes Eq. 8 there)."""
+    r = kw.pop("r", 3)
+    with pytest.raises(F.FctnError) as ei:
+        F.fctn_footprint_bytes(_params(F, (40, 36, 30), r=r, **kw))
+    assert ei.value.code == F.FCTN_E_UNSUPPORTED
+    assert F.fctn_footprint_bytes(_params(F, (40, 36, 30), r=17, precision="fp32")) > 0
+    assert F.fctn_footprint_bytes(_params(F, (40, 36, 30), r=16, precision="fp32", solve_method="chol")) > 0

@@ -179,7 +179,7 @@ def test_fp32_eigensolver_sizes(F, r):
     chip, rotation blocks recorded and applied to V by many CTAs)."""
     d = inputs(None, dims=(40, 36, 12), r=r, p=0.3, idx=46, noise=0.0, cap=None, dtype=np.float32)
     st, _ = oracle_run(d, 10)
-    g = gpu_run(F, d, 10, precision="fp32")
+    g = gpu_run(F, d, 10, precision="fp32", solve_method="eig")
     assert rel(g["X"], st.X) <= 1e-4, rel(g["X"], st.X)
     for k, (a, b) in enumerate(zip(g["factors"], st.factors)):
         assert rel(a, b) <= 1e-4, (k, rel(a, b))
@@ -304,12 +304,12 @@ def test_eig_sweep_cap_is_reported(F, precision, dims, r):
     finite values).  The default cap is not reached on the same inputs."""
     dt = np.float64 if precision == "fp64" else np.float32
     d = inputs(None, dims=dims, r=r, p=0.3, idx=63, noise=0.0, cap=None, dtype=dt)
-    g = gpu_run(F, d, 1, precision=precision, eig_max_sweeps=1)
+    g = gpu_run(F, d, 1, precision=precision, eig_max_sweeps=1, solve_method="eig")
     st = g["stats"]
     assert st["status"] == 0
     assert st["eig_capped"] == len(dims), st
     assert st["eig_sweeps"] == 1
     assert np.isfinite(g["X"]).all()
-    g2 = gpu_run(F, d, 1, precision=precision)
+    g2 = gpu_run(F, d, 1, precision=precision, solve_method="eig")
     assert g2["stats"]["eig_capped"] == 0, g2["stats"]
     assert g2["stats"]["eig_sweeps"] > 1

@@ -33,11 +33,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("solve", ["chol", "eig"])
 @pytest.mark.parametrize("dims,r,cap,sweeps", CASES)
-def test_head_route_fp32_matches_oracle(F, dims, r, cap, sweeps):
+def test_head_route_fp32_matches_oracle(F, dims, r, cap, sweeps, solve):
     d = inputs(None, dims=dims, r=r, p=0.3, idx=70, noise=0.0, cap=cap, dtype=np.float32)
     st, hist = oracle_run(d, sweeps, reuse=True, policy="plain")
-    g = gpu_run(F, d, sweeps, precision="fp32", reuse=True, policy="plain")
+    g = gpu_run(F, d, sweeps, precision="fp32", reuse=True, policy="plain", solve_method=solve)
     e = rel(g["X"], st.X)
     assert e <= 1e-4, e
     for k, (a, b) in enumerate(zip(g["factors"], st.factors)):

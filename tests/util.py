@@ -31,11 +31,12 @@ def oracle_run(d, sweeps, lam=0.01, delta=0.5, rho=0.1, reuse=True, policy="alte
 
 def gpu_run(F, d, sweeps, precision="fp64", lam=0.01, delta=0.5, rho=0.1, reuse=True, policy="alternate",
             sign="psd", refine_steps=None, stats_every=None, extrapolation=None, gram_mode="auto", rhs_ctas=0,
-            eig_max_sweeps=0, eig_tol=0.0, tile_code=0):
+            eig_max_sweeps=0, eig_tol=0.0, tile_code=0, solve_method="auto"):
     p = F.make_params(d["dims"], d["R"], lam=lam, delta=delta, rho=rho, precision=precision, reuse=reuse,
                       order_policy=policy, laplacian_sign=sign, refine_steps=refine_steps,
                       extrapolation=extrapolation, gram_mode=gram_mode, rhs_ctas=rhs_ctas,
-                      eig_max_sweeps=eig_max_sweeps, eig_tol=eig_tol, tile_code=tile_code)
+                      eig_max_sweeps=eig_max_sweeps, eig_tol=eig_tol, tile_code=tile_code,
+                      solve_method=solve_method)
     dt = F.elem_dtype(p)
     h = F.fctn_create(p)
     try:
