@@ -197,13 +197,39 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
   } else if (warp >= 2) {
     // ---- epilogue: TMEM lane quarter (warp % 4) = rows 32 q .. 32 q + 31
     const int q = warp & 3;
+    const int row = m0 + 32 * q + lane;
+    const int rowc = row < a.M ? row : a.M - 1;  // clamped: loads stay in bounds, stores are skipped
+    float d2 = 0.f, x2 = 0.f, r2 = 0.f;  // per-thread sums in FP32, combined in FP64 below
+    // Eq. 10 epilogue: X_(1)[i, j] and its mask word for the 16 columns of
+    // the next TMEM block are loaded before this block's stores, so that a
+    // block's loads are in flight together and overlap the previous block
+    float xp[16];
+    uint32_t bp[16];
+    auto xload = [&](int c0) {
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int i = min(n0 + c0 + jj, a.N - 1);
+        const int64_t e = (int64_t)i * a.P0 + rowc;
+        xp[jj] = a.X[e];
+        bp[jj] = a.bits[e >> 5];
+      }
+    };
+    if (a.mode == TG_XUPDATE) xload(0);  // independent of the accumulator: overlaps the MMAs
     const bool ok = nk == 0 || mb_wait(&accf, 0u, &abort_flag);
     if (!ok) abort_flag = 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int row = m0 + 32 * q + lane;
-    float d2 = 0.f, x2 = 0.f, r2 = 0.f;  // per-thread sums in FP32, combined in FP64 below
     if (ok) {
       for (int c0 = 0; c0 < BN; c0 += 16) {
+        float xo[16];
+        uint32_t bw[16];
+        if (a.mode == TG_XUPDATE) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            xo[jj] = xp[jj];
+            bw[jj] = bp[jj];
+          }
+          if (c0 + 16 < BN) xload(c0 + 16);
+        }
         uint32_t v[16];
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0;
         asm volatile(
@@ -230,20 +256,18 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int i = n0 + c0 + jj;
-            xt[jj] = 0.f;
-            if (i >= a.N) continue;
             const float f = nk > 0 ? __uint_as_float(v[jj]) : 0.f;
             const int64_t e = (int64_t)i * a.P0 + row;
-            const float xo = a.X[e];
-            const bool obs = (a.bits[e >> 5] >> (e & 31)) & 1u;
-            const float xn = obs ? xo : (f + r * xo) * inv;
+            const bool obs = (bw[jj] >> (e & 31)) & 1u;
+            const float xn = obs ? xo[jj] : (f + r * xo[jj]) * inv;
+            xt[jj] = xn;
+            if (i >= a.N) continue;
             a.X[e] = xn;
             if (a.Xb) a.Xb[e] = __float2bfloat16_rn(xn);
-            const float d = xn - xo, qq = xn - f;
+            const float d = xn - xo[jj], qq = xn - f;
             d2 = fmaf(d, d, d2);
-            x2 = fmaf(xo, xo, x2);
+            x2 = fmaf(xo[jj], xo[jj], x2);
             r2 = fmaf(qq, qq, r2);
-            xt[jj] = xn;
           }
           if (a.XT) {  // 16 consecutive columns of row j: four 16-byte stores when the row is whole
             float* o = a.XT + (int64_t)row * a.ldt + n0 + c0;
