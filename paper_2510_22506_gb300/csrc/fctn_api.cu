@@ -172,6 +172,7 @@ struct fctn_handle {
   float* eig_rec = nullptr;  // rotation blocks of the large FP32 eigensolver (128 < s <= 224)
   bool chol[FCTN_MAX_ORDER] = {};  // factor k solved by shifted Cholesky (FCTN_SOLVE_CHOL)
   float *cholL = nullptr, *cholD = nullptr;  // its packed factors and diagonal-block inverses
+  float *cholRt = nullptr, *Alo = nullptr;   // Q^T R, and the low half of the double-float factor
   void* Ck[FCTN_MAX_ORDER] = {};
   bool cvalid[FCTN_MAX_ORDER] = {};
   double lam_min[FCTN_MAX_ORDER] = {};
@@ -1283,6 +1284,7 @@ size_t footprint(const fctn_handle* h) {
   size_t nl, nd;
   chol_floats(h, &nl, &nd);
   b += (nl + nd) * 4;  // Cholesky factors
+  if (nl) b += 2 * z.Is * 4;  // Q^T R and the double-float split of the factor
   b += (z.red_blocks * 3 + h->N * 32 + 8) * 8 + 16;
   int64_t stage = h->P > z.maxfac ? h->P : z.maxfac;
   b += stage * e + h->P;                                  // staging
@@ -1348,14 +1350,38 @@ void prep_f32(fctn_handle* h, int k, cudaStream_t st) {
 int prep_f32_launches(const fctn_handle* h, int k) {
   return h->chol[k] ? 1 : eig_launches((int)h->s[k], h->cvalid[k] ? 1 : 0, h->eig_rec != nullptr);
 }
-// Forward half of the FP32 solve of factor k: W from the right-hand side R.
+// Solve of Eq. 5 for factor k through the shifted Cholesky factors, then
+// refine_steps passes on the residual of Eq. 5 (summed in double-float):
+// Q^T Y, substitution, A = Q W; R, Q^T R, substitution, A += Q W.
+int chol_solve(fctn_handle* h, int k) {
+  const int I = (int)h->I[k], s = (int)h->s[k];
+  const double lam = h->p.lambda[k], rho = h->p.rho;
+  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
+  const double c0 = sgn * (2.0 + h->p.delta[k]), c1 = -sgn;
+  float* W = (float*)h->Z;
+  float* Ac = (float*)h->Ac[k];
+  const double ge = 2.0 * (double)I * I * s, sub = 2.0 * (double)I * s * s;
+  LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
+         launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
+  LAUNCH(FCTN_KC_SOLVE, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
+  LAUNCH(FCTN_KC_SOLVE, 0.0, ge, launch_basis_gemm(1, h->Q32[k], W, I, s, nullptr, h->A64[k], Ac, h->Alo, h->st));
+  for (int r = 0; r < h->p.refine_steps; ++r) {
+    LAUNCH(FCTN_KC_SOLVE, 0.0, sub,
+           launch_resid_df(h->Yd, h->A64[k], Ac, h->Alo, (const float*)h->Gs, I, s, lam, rho, c0, c1, (float*)h->Rs,
+                           h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
+           launch_basis_gemm(0, h->QT32[k], (const float*)h->Rs, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, ge, launch_basis_gemm(2, h->Q32[k], W, I, s, nullptr, h->A64[k], Ac, h->Alo, h->st));
+  }
+  return FCTN_OK;
+}
+
+// Forward half of the FP32 Eq. 8 solve of factor k: W from the right-hand side R.
 void fwd_f32(fctn_handle* h, int k, const float* R, float* W) {
   const int I = (int)h->I[k], s = (int)h->s[k];
-  if (h->chol[k])
-    launch_chol_solve(h->QT32[k], R, I, s, h->cholL, h->cholD, W, h->status, h->st);
-  else
-    launch_solve_fwd_f32(h->QT32[k], R, (const float*)h->Ck[k], h->Lam[k], (const float*)h->Phi, h->p.lambda[k],
-                         h->p.rho, I, s, W, h->status, h->st);
+  launch_solve_fwd_f32(h->QT32[k], R, (const float*)h->Ck[k], h->Lam[k], (const float*)h->Phi, h->p.lambda[k],
+                       h->p.rho, I, s, W, h->status, h->st);
 }
 
 // Eqs. 5-9 for factor k; M_k is formed on chip from its pair operands L, R
@@ -1469,18 +1495,23 @@ int update_factor(fctn_handle* h, int k, const void* L, const void* R, void* Mou
       h->launches += prep_f32_launches(h, k) - 1;
     }
     const int nref = h->p.refine_steps;
-    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
-           launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
-                                nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
-    for (int r = 0; r < nref; ++r) {
-      if (r > 0)
-        LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
-               launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
-      LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
-             launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
-                                  c1, nullptr, h->status, h->st));
+    if (h->chol[k]) {
+      int rc = chol_solve(h, k);
+      if (rc) return rc;
+    } else {
+      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
+             launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
+                                  nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
+      for (int r = 0; r < nref; ++r) {
+        if (r > 0)
+          LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
+                 launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
+        LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
+        LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
+               launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho,
+                                    c0, c1, nullptr, h->status, h->st));
+      }
     }
   }
   if (extrap) {
@@ -1591,18 +1622,23 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
     h->launches += eig_launches(s, warm, h->eig_rec != nullptr) - 1;
   }
   const int nref = h->p.refine_steps;
-  LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
-  LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
-         launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
-                              nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
-  for (int r = 0; r < nref; ++r) {
-    if (r > 0)
-      LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
-             launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
-           launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
-                                c1, nullptr, h->status, h->st));
+  if (h->chol[k]) {
+    int rc = chol_solve(h, k);
+    if (rc) return rc;
+  } else {
+    LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
+    LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops + (nref > 0 ? resid_flops : 0.0),
+           launch_solve_bwd_f32(h->Q32[k], Z, I, s, 0, h->A64[k], (float*)h->Ac[k], h->Yd, h->Gd, lam, rho, c0, c1,
+                                nref > 0 ? (float*)h->Rs : nullptr, h->status, h->st));
+    for (int r = 0; r < nref; ++r) {
+      if (r > 0)
+        LAUNCH(FCTN_KC_SOLVE, 0.0, resid_flops,
+               launch_resid_f32(h->Yd, h->A64[k], h->Gd, I, s, lam, rho, c0, c1, (float*)h->Rs, h->st));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Rs, Z));
+      LAUNCH(FCTN_KC_SOLVE, 0.0, bwd_flops,
+             launch_solve_bwd_f32(h->Q32[k], Z, I, s, 1, h->A64[k], (float*)h->Ac[k], nullptr, nullptr, lam, rho, c0,
+                                  c1, nullptr, h->status, h->st));
+    }
   }
   if (h->p.extrap_alpha != 0.0)
     LAUNCH(FCTN_KC_SOLVE, 0.0, 0.0,
@@ -2077,6 +2113,8 @@ int fctn_create(const fctn_params* p, void* stream, fctn_handle** out) {
     if (nl) {
       A_(h->cholL, nl * 4);
       A_(h->cholD, nd * 4);
+      A_(h->cholRt, z.Is * 4);
+      A_(h->Alo, z.Is * 4);
     }
   }
   A_(h->status, 16);

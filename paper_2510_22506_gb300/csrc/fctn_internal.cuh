@@ -14,6 +14,28 @@
 #define FCTN_MAXC 8   // digits of its contracted index
 #define FCTN_CON_TABLE 4096  // contracted-index offsets kept in shared memory
 
+// Sum over z = 0 .. n - 1 of part[z * MN + e] in split order with Neumaier's
+// compensation (about twice the FP32 precision; FP64 adds run at 1/64 of the
+// FP32 rate), eight loads in flight: the fixed-order reduce of K-split partials.
+__device__ __forceinline__ float split_sum(const float* __restrict__ part, int n, int64_t MN, int64_t e) {
+  float s = 0.f, c = 0.f;
+  int z = 0;
+  auto add = [&](float v) {
+    const float t = s + v;
+    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  };
+  for (; z + 8 <= n; z += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = part[(int64_t)(z + u) * MN + e];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) add(v[u]);
+  }
+  for (; z < n; ++z) add(part[(int64_t)z * MN + e]);
+  return s + c;
+}
+
 // Index plan of one tensor contraction (Definition 3): the output is dense
 // row-major over `out_ext`; each output digit walks operand A with `a_str`
 // and operand B with `b_str` (0 = not present); the contracted digits walk
@@ -169,9 +191,17 @@ size_t chol_dinv_floats(int I, int s);
 // L, Dinv of every group from the FP32 Gram G (s x s); c0, c1: the stencil of L_k.
 void launch_chol_factor(const float* G, int I, int s, double lam, double c0, double c1, double rho, float* L,
                         float* Dinv, int* status, cudaStream_t st);
-// W (I x s) with W_i (G + c_i I) = (Q^T R)_i, from the factors of launch_chol_factor.
-void launch_chol_solve(const float* QT, const float* R, int I, int s, const float* L, const float* Dinv, float* W,
-                       int* status, cudaStream_t st);
+// Rows of W (I x s) with W_i (G + c_i I) = Rt_i (Rt = Q^T R), from the factors of launch_chol_factor.
+void launch_chol_subst(const float* Rt, int I, int s, const float* L, const float* Dinv, float* W, int* status,
+                       cudaStream_t st);
+// Products with the L_k basis (FP32, I x I times I x s): mode 0 out32 = Qm B;
+// 1: A64 = Qm B; 2: A64 += Qm B (modes 1, 2 also write Ac = float(A64) and
+// Alo = float(A64 - Ac)).
+void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, float* out32, double* A64, float* Ac,
+                       float* Alo, cudaStream_t st);
+// FP32 R = Yd - lam L A - rho A - A G with A = Ac + Alo, the A G products summed in double-float arithmetic.
+void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const float* Alo, const float* G, int I,
+                     int s, double lam, double rho, double c0, double c1, float* R, cudaStream_t st);
 
 // ---- kernels_tma.cu ---------------------------------------------------------
 // D[M x N] = A[M x K] B[N x K]^T on tcgen05 with TMA-fed operands (both

@@ -23,9 +23,11 @@
 // the inverses of its diagonal blocks.  A pivot that is not positive means
 // that G + c_j I is not positive definite (some T_ij of Eq. 8 <= 0): status
 // FCTN_E_SINGULAR, as for the eigen route.
-// k_chol_solve: one CTA per group: b = (Q^T R) for the group's rows, R
-// streamed through shared memory by bulk copies, then L z = b and L^T w = z
-// panel by panel (diagonal blocks through their inverses), w into W.
+// The solve around the factors (one refinement step shown):
+//   R~ = Q^T Y (k_bgemm), W = rows of R~ through L L^T (k_chol_subst),
+//   A = Q W (k_bgemm, FP64 master with its double-float split),
+//   R = Y - lam L A - rho A - A G (k_resid_df), then R~ = Q^T R, the
+//   substitution again and A += Q W.
 #include "fctn_internal.cuh"
 
 namespace {
@@ -58,29 +60,104 @@ __device__ inline int ch_rows(int g, int I, int* r) {
 
 __device__ __forceinline__ unsigned ch_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ bool ch_wait(uint64_t* bar, unsigned phase) {
+  for (long long it = 0; it < (1ll << 26); ++it) {
+    unsigned r;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(ch_su32(bar)), "r"(phase));
+    if (r) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void ch_expect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ch_su32(bar)), "r"(bytes));
+}
+// Bulk copy that completes on `bar` (whose expected bytes were set beforehand).
+__device__ __forceinline__ void ch_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(ch_su32(dst)),
+      "l"(src), "r"(bytes), "r"(ch_su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void ch_bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ch_su32(bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+}
+
+// Diagonal-block inverses are stored with a row stride of 33 floats (the
+// layout the solve kernel reads without bank conflicts in both orientations).
+constexpr int CH_DSTR = 33, CH_DBLK = 32 * CH_DSTR;
+
+
 __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__ G, int s, int I, double lam,
                                                        double c0, double c1, double rho, float* __restrict__ Lout,
                                                        float* __restrict__ Dout, int* status) {
   extern __shared__ __align__(16) float P[];
   __shared__ float rdiag[32];
   __shared__ int bad;
+  __shared__ __align__(8) uint64_t gbar;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = ch_npan(s), sp = 32 * np;
   const float shift = (float)(lam * (c0 + 2.0 * c1 * cospi(2.0 * (double)g / (double)I)) + rho);
-  if (tid == 0) bad = 0;
-  // G + c I into the panels; G is symmetric, so element (r, col) is read as
-  // G[col][r], consecutive threads on consecutive r
+  // G into the panels.  G is symmetric, so column col of a panel (rows
+  // 32 q .. s - 1) is the contiguous row segment G[col][32 q .. s): one bulk
+  // copy per column when the segments are 16-byte aligned, else loads with
+  // several in flight per thread
+  const bool bulk = (s % 4) == 0 && ((uintptr_t)G % 16) == 0;
+  if (tid == 0) {
+    bad = 0;
+    if (bulk) ch_bar_init(&gbar);
+  }
+  __syncthreads();
+  bool ok_g = true;
+  if (bulk) {
+    if (warp == 0) {
+      if (lane == 0) {
+        unsigned bytes = 0;
+        for (int col = 0; col < s; ++col) bytes += (unsigned)(s - (col & ~31)) * 4u;
+        ch_expect(&gbar, bytes);
+      }
+      __syncwarp();
+      for (int col = lane; col < s; col += 32) {
+        const int q = col >> 5, c = col & 31, nr = sp - 32 * q;
+        ch_copy(P + ch_poff(q, sp) + c * nr, G + (size_t)col * s + 32 * q, (unsigned)(s - 32 * q) * 4u, &gbar);
+      }
+    }
+    ok_g = ch_wait(&gbar, 0);
+  } else {
+    for (int q = 0; q < np; ++q) {
+      const int nr = sp - 32 * q;
+      float* Pq = P + ch_poff(q, sp);
+      const int n = 32 * nr;
+      for (int e0 = tid; e0 < n; e0 += 4 * CH_NT) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * CH_NT;
+          const int c = e / nr, r = 32 * q + (e - c * nr), col = 32 * q + c;
+          v[u] = (e < n && r < s && col < s) ? G[(size_t)col * s + r] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (e0 + u * CH_NT < n) Pq[e0 + u * CH_NT] = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  // the padding (identity) and the shift c on the diagonal
   for (int q = 0; q < np; ++q) {
     const int nr = sp - 32 * q;
     float* Pq = P + ch_poff(q, sp);
     for (int e = tid; e < 32 * nr; e += CH_NT) {
-      const int c = e / nr, rl = e - c * nr;
-      const int r = 32 * q + rl, col = 32 * q + c;
-      float v = (r == col) ? 1.0f : 0.0f;
-      if (r < s && col < s) v = G[(size_t)col * s + r] + (r == col ? shift : 0.0f);
-      Pq[e] = v;
+      const int c = e / nr, r = 32 * q + (e - c * nr), col = 32 * q + c;
+      if (r >= s || col >= s) Pq[e] = (r == col) ? 1.0f : 0.0f;
+      else if (r == col) Pq[e] += shift;
     }
   }
+  if (!ok_g && tid == 0) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
   __syncthreads();
   for (int p = 0; p < np; ++p) {
     const int nr = sp - 32 * p;
@@ -191,173 +268,74 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
 #pragma unroll
       for (int k = j + 1; k < 32; ++k) y[k] = fmaf(-Pp[j * nr + k], y[j], y[k]);
     }
-    float* Dg = Dout + ((size_t)g * np + p) * 1024;
+    float* Dg = Dout + ((size_t)g * np + p) * CH_DBLK;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) Dg[k * 32 + lane] = y[k];
+    for (int k = 0; k < 32; ++k) Dg[k * CH_DSTR + lane] = y[k];
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) Dg[k * CH_DSTR + 32] = 0.0f;
   }
   if (tid == 0 && bad) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
 }
 
-// Shared-memory layout of k_chol_solve (byte offsets, 16-byte aligned).
-struct ChSolveLayout {
-  size_t l, rs, ds, b, qs, red, total;
-  int NC;
-};
-__host__ __device__ inline size_t ch_al16(size_t b) { return (b + 15) & ~(size_t)15; }
-__host__ __device__ inline ChSolveLayout ch_solve_layout(int I, int s) {
-  ChSolveLayout o;
-  const int np = ch_npan(s), sp = 32 * np;
-  const size_t fixed = (size_t)ch_pack(s) * 4 + (size_t)np * 32 * 33 * 4 + 2 * (size_t)sp * 4 + 64 * 4 + 256;
-  const size_t budget = 216 * 1024;
-  long nc = budget > fixed ? (long)((budget - fixed) / (2 * 4 * (size_t)s + 16)) : 4;
-  nc = nc > 32 ? 32 : nc;
-  nc = nc < 4 ? 4 : (nc & ~3L);
-  if (nc > I) nc = I;
-  // the partial sums of the column groups reuse the staging buffers
-  const int KS = s >= CH_NT ? 1 : CH_NT / s;
-  const long need = (KS * 2 * (long)s + 2 * (long)s - 1) / (2 * (long)s);
-  if (nc < need) nc = need;
-  o.NC = (int)nc;
-  o.l = 0;
-  o.rs = ch_al16(o.l + (size_t)ch_pack(s) * 4);
-  o.ds = ch_al16(o.rs + 2 * (size_t)o.NC * s * 4);
-  o.b = ch_al16(o.ds + (size_t)np * 32 * 33 * 4);
-  o.qs = ch_al16(o.b + 2 * (size_t)sp * 4);
-  o.red = ch_al16(o.qs + 4 * (size_t)o.NC * 4);
-  o.total = ch_al16(o.red + 64 * 4);
-  return o;
+// k_chol_subst: one CTA per group: L z = b and L^T w = z for the group's
+// rows b of R~ = Q^T R, panel by panel: the diagonal block through its
+// inverse (one warp), the rest of the panel by the other threads.  L and the
+// block inverses arrive by bulk copies; w is written to the rows of W.
+__host__ __device__ inline size_t ch_subst_bytes(int s) {
+  const int np = ch_npan(s);
+  return (size_t)ch_pack(s) * 4 + (size_t)np * CH_DBLK * 4 + 2 * 32 * (size_t)np * 4 + 64 * 4;
 }
 
-__device__ __forceinline__ bool ch_wait(uint64_t* bar, unsigned phase) {
-  for (long long it = 0; it < (1ll << 26); ++it) {
-    unsigned r;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(r)
-        : "r"(ch_su32(bar)), "r"(phase));
-    if (r) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void ch_bulk(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ch_su32(bar)), "r"(bytes));
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(ch_su32(dst)),
-      "l"(src), "r"(bytes), "r"(ch_su32(bar))
-      : "memory");
-}
-
-__global__ void __launch_bounds__(CH_NT) k_chol_solve(const float* __restrict__ QT, const float* __restrict__ R,
-                                                      int I, int s, const float* __restrict__ Lp,
-                                                      const float* __restrict__ Dinv, float* __restrict__ W,
-                                                      int* status) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[3];
-  const ChSolveLayout Ly = ch_solve_layout(I, s);
-  float* Ls = (float*)(sm + Ly.l);
-  float* Rs = (float*)(sm + Ly.rs);
-  float* Ds = (float*)(sm + Ly.ds);
-  float* bv = (float*)(sm + Ly.b);
-  float* qs = (float*)(sm + Ly.qs);
-  float* red = (float*)(sm + Ly.red);
-  const int NC = Ly.NC;
+__global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ Rt, int I, int s,
+                                                      const float* __restrict__ Lp, const float* __restrict__ Dinv,
+                                                      float* __restrict__ W, int* status) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ __align__(8) uint64_t bar;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int rows[2] = {0, 0};
   const int nrw = ch_rows(g, I, rows);
   const int np = ch_npan(s), sp = 32 * np, tot = ch_pack(s);
+  float* Ls = smf;
+  float* Ds = Ls + tot;
+  float* bv = Ds + np * CH_DBLK;
+  float* red = bv + 2 * sp;
   const float* Lg = Lp + (size_t)g * tot;
-  const bool bulkL = ((uintptr_t)Lg % 16) == 0;
-  const bool bulkR = ((uintptr_t)R % 16) == 0 && (s % 4) == 0;
-  if (tid == 0) {
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(ch_su32(&bars[i])));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  const float* Dg = Dinv + (size_t)g * np * CH_DBLK;
+  const bool bulk = ((uintptr_t)Lg % 16) == 0 && ((uintptr_t)Dg % 16) == 0;
+  if (tid == 0 && bulk) {
+    ch_bar_init(&bar);
+    ch_expect(&bar, (unsigned)(tot + np * CH_DBLK) * 4u);
+    ch_copy(Ls, Lg, (unsigned)tot * 4u, &bar);
+    ch_copy(Ds, Dg, (unsigned)(np * CH_DBLK) * 4u, &bar);
   }
-  __syncthreads();
-  if (tid == 0 && bulkL) ch_bulk(Ls, Lg, (unsigned)tot * 4u, &bars[0]);
-  if (!bulkL)
+  if (!bulk) {
     for (int e = tid; e < tot; e += CH_NT) Ls[e] = Lg[e];
-  for (int e = tid; e < np * 1024; e += CH_NT) {
-    const int p = e >> 10, w = e & 1023;
-    Ds[p * 1056 + (w >> 5) * 33 + (w & 31)] = Dinv[(size_t)g * np * 1024 + e];
+    for (int e = tid; e < np * CH_DBLK; e += CH_NT) Ds[e] = Dg[e];
   }
-  // b = (Q^T R)[rows]: thread (kq, j) sums rows m = kq, kq + KS, ... of each chunk
-  const int KS = s >= CH_NT ? 1 : CH_NT / s;
-  const int j = tid % s, kq = tid / s;
-  const bool act = kq < KS && j < s;
-  float acc0 = 0.0f, acc1 = 0.0f;
-  const int nch = (I + NC - 1) / NC;
-  unsigned ph[2] = {0u, 0u};
-  bool ok = true;
-  if (bulkR && tid == 0) ch_bulk(Rs, R, (unsigned)(min(NC, I) * s * 4), &bars[1]);
-  for (int c = 0; c < nch; ++c) {
-    const int n0 = c * NC, nc = min(NC, I - n0);
-    float* buf = Rs + (size_t)(c & 1) * NC * s;
-    float* qb = qs + (c & 1) * 2 * NC;
-    if (bulkR && tid == 0 && c + 1 < nch) {
-      const int n1 = n0 + NC, nc1 = min(NC, I - n1);
-      ch_bulk(Rs + (size_t)((c + 1) & 1) * NC * s, R + (size_t)n1 * s, (unsigned)(nc1 * s * 4), &bars[1 + ((c + 1) & 1)]);
-    }
-    for (int e = tid; e < nrw * nc; e += CH_NT) {
-      const int t = e / nc, m = e - t * nc;
-      qb[t * NC + m] = QT[(size_t)rows[t] * I + n0 + m];
-    }
-    if (bulkR) {
-      ok = ch_wait(&bars[1 + (c & 1)], ph[c & 1]) && ok;
-      ph[c & 1] ^= 1u;
-    } else {
-      for (int e = tid; e < nc * s; e += CH_NT) buf[e] = R[(size_t)n0 * s + e];
-    }
-    __syncthreads();
-    if (act) {
-      if (nrw == 2) {
-        for (int m = kq; m < nc; m += KS) {
-          const float x = buf[m * s + j];
-          acc0 = fmaf(qb[m], x, acc0);
-          acc1 = fmaf(qb[NC + m], x, acc1);
-        }
-      } else {
-        for (int m = kq; m < nc; m += KS) acc0 = fmaf(qb[m], buf[m * s + j], acc0);
-      }
-    }
-    __syncthreads();
-  }
-  // combine the column groups' partial sums in group order (staging buffers are free now)
-  if (act) {
-    Rs[(kq * 2 + 0) * s + j] = acc0;
-    Rs[(kq * 2 + 1) * s + j] = acc1;
-  }
-  __syncthreads();
   for (int e = tid; e < 2 * sp; e += CH_NT) {
-    const int t = e / sp, jj = e - t * sp;
-    float v = 0.0f;
-    if (jj < s && t < nrw)
-      for (int q = 0; q < KS; ++q) v += Rs[(q * 2 + t) * s + jj];
-    bv[e] = v;
+    const int t = e / sp, j = e - t * sp;
+    bv[e] = (t < nrw && j < s) ? Rt[(size_t)rows[t] * s + j] : 0.0f;
   }
-  if (bulkL) ok = ch_wait(&bars[0], 0) && ok;
-  if (!ok) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
+  __syncthreads();  // the barrier's initialisation is visible before anyone waits on it
+  if (bulk && !ch_wait(&bar, 0) && tid == 0) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
   __syncthreads();
   // L z = b
   for (int p = 0; p < np; ++p) {
     const int nr = sp - 32 * p;
     const float* Lq = Ls + ch_poff(p, sp);
-    const float* D = Ds + p * 1056;
+    const float* D = Ds + p * CH_DBLK;
     if (warp == 0) {
-      float z[2];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        float a = 0.0f;
-        if (t < nrw)
+      float z0 = 0.0f, z1 = 0.0f;
 #pragma unroll 8
-          for (int k = 0; k < 32; ++k) a = fmaf(D[lane * 33 + k], bv[t * sp + 32 * p + k], a);
-        z[t] = a;
+      for (int k = 0; k < 32; ++k) {
+        const float d = D[lane * CH_DSTR + k];
+        z0 = fmaf(d, bv[32 * p + k], z0);
+        z1 = fmaf(d, bv[sp + 32 * p + k], z1);
       }
       __syncwarp();
-#pragma unroll
-      for (int t = 0; t < 2; ++t)
-        if (t < nrw) bv[t * sp + 32 * p + lane] = z[t];
+      bv[32 * p + lane] = z0;
+      bv[sp + 32 * p + lane] = z1;
     }
     __syncthreads();
     for (int i = tid; i < nr - 32; i += CH_NT) {
@@ -378,7 +356,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_solve(const float* __restrict__ 
   for (int p = np - 1; p >= 0; --p) {
     const int nr = sp - 32 * p;
     const float* Lq = Ls + ch_poff(p, sp);
-    const float* D = Ds + p * 1056;
+    const float* D = Ds + p * CH_DBLK;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       const int c = warp * 4 + cc;
@@ -400,21 +378,158 @@ __global__ void __launch_bounds__(CH_NT) k_chol_solve(const float* __restrict__ 
     }
     __syncthreads();
     if (warp == 0) {
+      const float y0 = bv[32 * p + lane] - red[lane];
+      const float y1 = bv[sp + 32 * p + lane] - red[32 + lane];
+      float w0 = 0.0f, w1 = 0.0f;
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (t >= nrw) break;
-        const float y = bv[t * sp + 32 * p + lane] - red[t * 32 + lane];
-        float a = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) a = fmaf(D[k * 33 + lane], __shfl_sync(CH_FULL, y, k), a);
-        bv[t * sp + 32 * p + lane] = a;
+      for (int k = 0; k < 32; ++k) {
+        const float d = D[k * CH_DSTR + lane];
+        w0 = fmaf(d, __shfl_sync(CH_FULL, y0, k), w0);
+        w1 = fmaf(d, __shfl_sync(CH_FULL, y1, k), w1);
       }
+      bv[32 * p + lane] = w0;
+      bv[sp + 32 * p + lane] = w1;
     }
     __syncthreads();
   }
   for (int e = tid; e < nrw * s; e += CH_NT) {
-    const int t = e / s, jj = e - t * s;
-    W[(size_t)rows[t] * s + jj] = bv[t * sp + jj];
+    const int t = e / s, j = e - t * s;
+    W[(size_t)rows[t] * s + j] = bv[t * sp + j];
+  }
+}
+
+// ---- products with the L_k basis and the residual of Eq. 5 -----------------
+// C (M x N) = A (M x K) B (K x N), row-major FP32 operands, one 32 x 32 tile
+// of C per CTA of 256 threads (thread (ty, tx) owns rows ty, ty + 16 and
+// columns tx, tx + 16); K in chunks of 64 staged through shared memory, the
+// next chunk's loads in flight while the current chunk is multiplied.
+// Epilogues: BG_STORE out32 = C; BG_SET A64 = C; BG_ADD A64 += C; with
+// BG_SET / BG_ADD also Ac = hi(A64) = float(A64) and Alo = float(A64 - hi),
+// the double-float split that the residual kernel reads.
+enum { BG_STORE = 0, BG_SET = 1, BG_ADD = 2 };
+constexpr int BG_KC = 64;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bgemm(const float* __restrict__ A, const float* __restrict__ B, int M, int N,
+                                               int K, float* __restrict__ out32, double* __restrict__ A64,
+                                               float* __restrict__ Ac, float* __restrict__ Alo) {
+  __shared__ float As[32][BG_KC + 1];
+  __shared__ float Bs[BG_KC][33];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float ra[8], rb[8];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256;
+      const int am = e >> 6, ak = e & 63;  // A: 32 rows x 64 k
+      const int bk = e >> 5, bn = e & 31;  // B: 64 k x 32 columns
+      ra[u] = (m0 + am < M && k0 + ak < K) ? A[(size_t)(m0 + am) * K + k0 + ak] : 0.0f;
+      rb[u] = (k0 + bk < K && n0 + bn < N) ? B[(size_t)(k0 + bk) * N + n0 + bn] : 0.0f;
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += BG_KC) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256;
+      As[e >> 6][e & 63] = ra[u];
+      Bs[e >> 5][e & 31] = rb[u];
+    }
+    __syncthreads();
+    if (k0 + BG_KC < K) load(k0 + BG_KC);
+#pragma unroll 16
+    for (int k = 0; k < BG_KC; ++k) {
+      const float a0 = As[ty][k], a1 = As[ty + 16][k];
+      const float b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+      acc[0][0] = fmaf(a0, b0, acc[0][0]);
+      acc[0][1] = fmaf(a0, b1, acc[0][1]);
+      acc[1][0] = fmaf(a1, b0, acc[1][0]);
+      acc[1][1] = fmaf(a1, b1, acc[1][1]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int m = m0 + ty + 16 * a, n = n0 + tx + 16 * b;
+      if (m >= M || n >= N) continue;
+      const size_t o = (size_t)m * N + n;
+      if (MODE == BG_STORE) {
+        out32[o] = acc[a][b];
+      } else {
+        const double v = MODE == BG_SET ? (double)acc[a][b] : A64[o] + (double)acc[a][b];
+        A64[o] = v;
+        const float hi = (float)v;
+        Ac[o] = hi;
+        Alo[o] = (float)(v - (double)hi);
+      }
+    }
+}
+
+// R = Y - lam L A - rho A - A G (Eq. 5) on a 16 x 32 tile (rows i0.., columns
+// j0..), stored as FP32: the right-hand side of the refinement solve.  A is
+// the double-float pair (Ac, Alo) of the FP64 factor; the products A G are
+// exact FP32 products (fma gives each rounding error) summed with
+// Neumaier's compensation, so the sum carries about twice the FP32
+// precision (FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU);
+// Y, the stencil of L and the final difference are FP64.
+constexpr int RD_ROWS = 16;
+
+__device__ __forceinline__ void df_add(float& s, float& c, float p) {
+  const float t = s + p;
+  c += fabsf(s) >= fabsf(p) ? (s - t) + p : (p - t) + s;
+  s = t;
+}
+
+__global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd, const double* __restrict__ A64,
+                                                  const float* __restrict__ Ac, const float* __restrict__ Alo,
+                                                  const float* __restrict__ G, int I, int s, double lam, double rho,
+                                                  double c0, double c1, float* __restrict__ R) {
+  extern __shared__ __align__(16) float rsm[];
+  float* Ah = rsm;                    // [RD_ROWS][s]
+  float* Al = Ah + RD_ROWS * s;       // [RD_ROWS][s]
+  float* Gt = Al + RD_ROWS * s;       // [s][33]: columns j0 .. j0 + 31 of G
+  const int tid = threadIdx.x, r = tid >> 4, cx = tid & 15;
+  const int i0 = blockIdx.y * RD_ROWS, j0 = blockIdx.x * 32;
+  for (int e = tid; e < RD_ROWS * s; e += 256) {
+    const int rr = e / s, q = e - rr * s;
+    const bool in = i0 + rr < I;
+    Ah[e] = in ? Ac[(size_t)(i0 + rr) * s + q] : 0.0f;
+    Al[e] = in ? Alo[(size_t)(i0 + rr) * s + q] : 0.0f;
+  }
+  for (int e = tid; e < s * 32; e += 256) {
+    const int q = e >> 5, c = e & 31;
+    Gt[q * 33 + c] = j0 + c < s ? G[(size_t)q * s + j0 + c] : 0.0f;
+  }
+  __syncthreads();
+  float s0 = 0.f, k0 = 0.f, s1 = 0.f, k1 = 0.f;
+  const float* ah = Ah + r * s;
+  const float* al = Al + r * s;
+  for (int q = 0; q < s; ++q) {
+    const float h = ah[q], l = al[q];
+    const float g0 = Gt[q * 33 + cx], g1 = Gt[q * 33 + cx + 16];
+    const float p0 = h * g0, p1 = h * g1;
+    k0 += fmaf(h, g0, -p0);
+    k1 += fmaf(h, g1, -p1);
+    k0 = fmaf(l, g0, k0);
+    k1 = fmaf(l, g1, k1);
+    df_add(s0, k0, p0);
+    df_add(s1, k1, p1);
+  }
+  const int i = i0 + r;
+  if (i >= I) return;
+  const int im = (i - 1 + I) % I, ip = (i + 1) % I;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int j = j0 + cx + 16 * b;
+    if (j >= s) continue;
+    const double ag = b == 0 ? (double)s0 + (double)k0 : (double)s1 + (double)k1;
+    const double a = A64[(size_t)i * s + j];
+    const double la = c0 * a + c1 * (A64[(size_t)im * s + j] + A64[(size_t)ip * s + j]);
+    R[(size_t)i * s + j] = (float)(Yd[(size_t)i * s + j] - lam * la - rho * a - ag);
   }
 }
 
@@ -423,7 +538,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_solve(const float* __restrict__ 
 int chol_groups(int I) { return I / 2 + 1; }
 bool chol_supported(int s) { return s >= 1 && s <= CH_MAXS; }
 size_t chol_factor_floats(int I, int s) { return (size_t)chol_groups(I) * ch_pack(s); }
-size_t chol_dinv_floats(int I, int s) { return (size_t)chol_groups(I) * ch_npan(s) * 1024; }
+size_t chol_dinv_floats(int I, int s) { return (size_t)chol_groups(I) * ch_npan(s) * CH_DBLK; }
 
 void launch_chol_factor(const float* G, int I, int s, double lam, double c0, double c1, double rho, float* L,
                         float* Dinv, int* status, cudaStream_t st) {
@@ -436,13 +551,35 @@ void launch_chol_factor(const float* G, int I, int s, double lam, double c0, dou
   k_chol_factor<<<chol_groups(I), CH_NT, bytes, st>>>(G, s, I, lam, c0, c1, rho, L, Dinv, status);
 }
 
-void launch_chol_solve(const float* QT, const float* R, int I, int s, const float* L, const float* Dinv, float* W,
-                       int* status, cudaStream_t st) {
+void launch_chol_subst(const float* Rt, int I, int s, const float* L, const float* Dinv, float* W, int* status,
+                       cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_chol_subst, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  const ChSolveLayout Ly = ch_solve_layout(I, s);
-  k_chol_solve<<<chol_groups(I), CH_NT, Ly.total, st>>>(QT, R, I, s, L, Dinv, W, status);
+  k_chol_subst<<<chol_groups(I), CH_NT, ch_subst_bytes(s), st>>>(Rt, I, s, L, Dinv, W, status);
+}
+
+void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, float* out32, double* A64, float* Ac,
+                       float* Alo, cudaStream_t st) {
+  dim3 grid((unsigned)((s + 31) / 32), (unsigned)((I + 31) / 32));
+  if (mode == BG_STORE)
+    k_bgemm<BG_STORE><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+  else if (mode == BG_SET)
+    k_bgemm<BG_SET><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+  else
+    k_bgemm<BG_ADD><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+}
+
+void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const float* Alo, const float* G, int I,
+                     int s, double lam, double rho, double c0, double c1, float* R, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_resid_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+    attr = true;
+  }
+  const size_t bytes = ((size_t)2 * RD_ROWS * s + (size_t)s * 33) * 4;
+  dim3 grid((unsigned)((s + 31) / 32), (unsigned)((I + RD_ROWS - 1) / RD_ROWS));
+  k_resid_df<<<grid, 256, bytes, st>>>(Yd, A64, Ac, Alo, G, I, s, lam, rho, c0, c1, R);
 }

@@ -135,14 +135,13 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
   }
 }
 
-// C[cm[m] + cn[n]] = sum over the K split (in split order, FP64) of the partials.
+// C[cm[m] + cn[n]] = sum over the K split (in split order, compensated) of the partials.
 __global__ void k_sg_reduce(SgShape sh, SgTabs t, const float* __restrict__ part, float* __restrict__ C) {
   const int64_t MN = (int64_t)sh.M * sh.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int z = 0; z < sh.ksplit; ++z) s += (double)part[(int64_t)z * MN + e];
+    const float s = split_sum(part, sh.ksplit, MN, e);
     const int m = (int)(e / sh.N), n = (int)(e - (int64_t)m * sh.N);
-    C[(int64_t)t.cm[m] + t.cn[n]] = (float)s;
+    C[(int64_t)t.cm[m] + t.cn[n]] = s;
   }
 }
 

@@ -313,13 +313,11 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
 }
 
-// Sum of the K-split partials of a TG_PARTIAL launch (split order, FP64):
+// Sum of the K-split partials of a TG_PARTIAL launch (split order, compensated):
 // out[row * N + col] = sum_z part[z][row][col].
 __global__ void k_tg_reduce(const float* __restrict__ part, int ksplit, int64_t MN, float* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int z = 0; z < ksplit; ++z) s += (double)part[(int64_t)z * MN + e];
-    out[e] = (float)s;
+    out[e] = split_sum(part, ksplit, MN, e);
   }
 }
 
