@@ -63,11 +63,11 @@ def eig_sms(s):
 CLASS_KERNEL = {
     "gram": ("k_tg_gemm (X_(1) M_1^T, X_(1)^T A_(1))", "hbm"),
     "xupdate": ("k_tg_gemm (F^T = M_1^T A_(1)^T, Eq. 10 epilogue)", "hbm"),
-    "eig": ("k_eigc (cluster) / k_eig3 (one CTA)", "alu1"),
+    "eig": ("k_chol_factor (one CTA per distinct shift of Eq. 6)", "chol"),
     "env": ("k_sgemm (factor Grams and their chains)", "alu"),
     "rhs2": ("k_sgemm (right-hand sides 2..N from Z)", "alu"),
     "merged": ("k_sgemm (M_1) + operand copies", "alu"),
-    "solve": ("k_solve_fwd / k_solve_bwd", "alu"),
+    "solve": ("k_bgemm (Q^T R, Q W), k_chol_subst, k_resid_df", "alu"),
     "eigaux": ("k_mm_small, k_first_order, k_eig_apply", "alu"),
     "reduce": ("k_tg_reduce, k_finish_rhs", "hbm"),
     "misc": ("k_trace, k_finalize, copies", "hbm"),
@@ -183,12 +183,25 @@ def sweep_floor_bytes(dims, R):
     return (len(dims) + 2) * 4.0 * P + P / 8.0
 
 
-def class_roofline(cls, prof, peaks, peak_src, precision, svals, eig_sweeps):
+def class_roofline(cls, prof, peaks, peak_src, precision, svals, eig_sweeps, dims=None):
     """Achieved rate of one kernel class (one kernel per launch) against its roof."""
     kernel, bound = CLASS_KERNEL.get(cls, (cls, "hbm"))
     n = max(prof["launches"], 1)
     avg_s = prof["ms"] / n / 1e3
-    if bound == "alu1":  # the SMs the eigensolver runs on; two-sided Jacobi on B and V^T, 9 s^3 flops per sweep
+    if bound == "chol" and eig_sweeps == 0:
+        # one CTA per distinct shift (floor(I / 2) + 1 of them), s^3 / 3 flops
+        # each (Cholesky of an s x s matrix); every CTA does the same work, so
+        # the per-CTA rate against one SM's FP32 rate is the fraction
+        groups = [I // 2 + 1 for I in dims]
+        flops = float(np.mean([g * sv ** 3 / 3.0 for g, sv in zip(groups, svals)]))
+        sms = float(np.mean([min(g, 152) for g in groups]))
+        ach = flops / avg_s / 1e12
+        peak = sms * SM_FP32_TFLOPS
+        return dict(kernel=kernel, bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_source=f"derived: {sms:.1f} SMs (one CTA per shift, mean over the factors) x 128 FP32 "
+                                "lanes x 2 x 2.07 GHz",
+                    flops_per_launch=flops)
+    if bound in ("alu1", "chol"):  # the SMs the eigensolver runs on; two-sided Jacobi on B and V^T, 9 s^3 flops per sweep
         flops = float(np.mean([9.0 * sv ** 3 for sv in svals])) * max(eig_sweeps, 1)
         sms, kname = eig_sms(max(svals))
         ach = flops / avg_s / 1e12
@@ -320,8 +333,8 @@ def run_ours(args):
     value = job_value(args.steps, ws, total_ms)
     peaks, peak_src = load_peaks()
     svals = [int(np.prod([R[min(k, t), max(k, t)] for t in range(N) if t != k])) for k in range(N)]
-    eig_sw = max(int(st2["eig_sweeps"]), 1)
-    rows = {c: class_roofline(c, v, peaks, peak_src, precision, svals, eig_sw)
+    eig_sw = int(st2["eig_sweeps"])
+    rows = {c: class_roofline(c, v, peaks, peak_src, precision, svals, eig_sw, dims=w["dims"])
             for c, v in per_class.items() if v["launches"] > 0}
     for c, v in per_class.items():
         if c in rows:
@@ -359,6 +372,7 @@ def run_ours(args):
                 "step": f"set_data + set_factors from pinned host buffers, {e2e_sweeps} sweeps, X back to pinned host memory"},
     }
     if ws == 1 and not args.no_extras:
+        line["solve_routes"] = solve_routes(F, Y, mask, init, R, precision, args.steps)
         line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps, tune=not args.no_tune)
         if name != "c2":
             line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), args.steps, quality_sweeps=0,
@@ -370,6 +384,40 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def solve_routes(F, Y, mask, init, R, precision, steps, warm=5):
+    """ms per sweep with each solve of Eq. 5 (FCTN_SOLVE_CHOL, the default
+    here, and FCTN_SOLVE_EIG, Eq. 8 through the Jacobi eigendecomposition),
+    graphs, L2 flushed between sweeps, after `warm` untimed sweeps."""
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    Y32, M8 = np.ascontiguousarray(Y.astype(np.float32)), mask.astype(np.uint8)
+    init32 = [np.ascontiguousarray(a.astype(np.float32)) for a in init]
+    out = {}
+    for m in ("chol", "eig"):
+        p = F.make_params(Y.shape, R, lam=synth.LAMBDA, delta=synth.DELTA, rho=synth.RHO, precision=precision,
+                          order_policy="plain", solve_method=m)
+        st = torch.cuda.Stream()
+        h = F.fctn_create(p, st)
+        try:
+            F.fctn_set_data(h, Y32, M8)
+            F.fctn_set_factors(h, init32)
+            F.fctn_pam_sweep(h, warm, want_stats=False)
+            tot = 0.0
+            with torch.cuda.stream(st):
+                for _ in range(steps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    F.fctn_pam_sweep(h, 1, want_stats=False)
+                    b.record(st)
+                    flush.zero_()
+                    b.synchronize()
+                    tot += a.elapsed_time(b)
+            out[m] = {"ms_per_sweep": tot / steps, "eig_sweeps_last": F.fctn_pam_sweep(h, 0)["eig_sweeps"]}
+        finally:
+            F.fctn_destroy(h)
+    return out
 
 
 def precision_modes(F, name, truth, Y, mask, init, R, steps, quality_sweeps=100, tol=1e-4, max_sweeps=500,

@@ -98,66 +98,36 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
   extern __shared__ __align__(16) float P[];
   __shared__ float rdiag[32];
   __shared__ int bad;
-  __shared__ __align__(8) uint64_t gbar;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = ch_npan(s), sp = 32 * np;
   const float shift = (float)(lam * (c0 + 2.0 * c1 * cospi(2.0 * (double)g / (double)I)) + rho);
   // G into the panels.  G is symmetric, so column col of a panel (rows
-  // 32 q .. s - 1) is the contiguous row segment G[col][32 q .. s): one bulk
-  // copy per column when the segments are 16-byte aligned, else loads with
-  // several in flight per thread
-  const bool bulk = (s % 4) == 0 && ((uintptr_t)G % 16) == 0;
-  if (tid == 0) {
-    bad = 0;
-    if (bulk) ch_bar_init(&gbar);
-  }
-  __syncthreads();
-  bool ok_g = true;
-  if (bulk) {
-    if (warp == 0) {
-      if (lane == 0) {
-        unsigned bytes = 0;
-        for (int col = 0; col < s; ++col) bytes += (unsigned)(s - (col & ~31)) * 4u;
-        ch_expect(&gbar, bytes);
-      }
-      __syncwarp();
-      for (int col = lane; col < s; col += 32) {
-        const int q = col >> 5, c = col & 31, nr = sp - 32 * q;
-        ch_copy(P + ch_poff(q, sp) + c * nr, G + (size_t)col * s + 32 * q, (unsigned)(s - 32 * q) * 4u, &gbar);
-      }
-    }
-    ok_g = ch_wait(&gbar, 0);
-  } else {
-    for (int q = 0; q < np; ++q) {
-      const int nr = sp - 32 * q;
-      float* Pq = P + ch_poff(q, sp);
-      const int n = 32 * nr;
-      for (int e0 = tid; e0 < n; e0 += 4 * CH_NT) {
-        float v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = e0 + u * CH_NT;
-          const int c = e / nr, r = 32 * q + (e - c * nr), col = 32 * q + c;
-          v[u] = (e < n && r < s && col < s) ? G[(size_t)col * s + r] : 0.0f;
+  // 32 q .. s - 1) is the contiguous row segment G[col][32 q .. s): with
+  // s % 4 == 0, 16-byte asynchronous copies (all of them in flight at once),
+  // else scalar loads.  Rows s .. sp - 1 are zero and columns s .. sp - 1 the
+  // identity (the padding); the shift c is added to the pivots in step 1.
+  const bool vec = (s % 4) == 0 && ((uintptr_t)G % 16) == 0;
+  if (tid == 0) bad = 0;
+  for (int col = warp; col < sp; col += CH_NT / 32) {
+    const int q = col >> 5, nr = sp - 32 * q;
+    float* dst = P + ch_poff(q, sp) + (col & 31) * nr - 32 * q;  // dst[r] = element (r, col)
+    if (col >= s) {
+      for (int r = 32 * q + lane; r < sp; r += 32) dst[r] = (r == col) ? 1.0f : 0.0f;
+    } else if (vec) {
+      for (int r = 32 * q + 4 * lane; r < sp; r += 128) {
+        if (r < s) {
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ch_su32(dst + r)),
+                       "l"(G + (size_t)col * s + r)
+                       : "memory");
+        } else {
+          *reinterpret_cast<float4*>(dst + r) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (e0 + u * CH_NT < n) Pq[e0 + u * CH_NT] = v[u];
       }
+    } else {
+      for (int r = 32 * q + lane; r < sp; r += 32) dst[r] = r < s ? G[(size_t)col * s + r] : 0.0f;
     }
   }
-  __syncthreads();
-  // the padding (identity) and the shift c on the diagonal
-  for (int q = 0; q < np; ++q) {
-    const int nr = sp - 32 * q;
-    float* Pq = P + ch_poff(q, sp);
-    for (int e = tid; e < 32 * nr; e += CH_NT) {
-      const int c = e / nr, r = 32 * q + (e - c * nr), col = 32 * q + c;
-      if (r >= s || col >= s) Pq[e] = (r == col) ? 1.0f : 0.0f;
-      else if (r == col) Pq[e] += shift;
-    }
-  }
-  if (!ok_g && tid == 0) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
+  if (vec) asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   for (int p = 0; p < np; ++p) {
     const int nr = sp - 32 * p;
@@ -167,7 +137,10 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
     if (warp == 0) {
       float d[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) d[c] = Pp[c * nr + lane];
+      for (int c = 0; c < 32; ++c) {
+        d[c] = Pp[c * nr + lane];
+        if (c == lane && 32 * p + c < s) d[c] += shift;  // G + c I
+      }
       bool ok = true;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -188,8 +161,30 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
       if (!ok && lane == 0) bad = 1;
     }
     __syncthreads();
-    // 2. rows below the block: x L_pp^T = a, one row per thread
-    for (int t = tid; t < nr - 32; t += CH_NT) {
+    // 2. rows below the block: x L_pp^T = a, one row per thread of warps
+    //    1..7; warp 0 meanwhile forms the block's inverse for the solve
+    if (warp == 0) {
+      float y[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) y[k] = (k == lane) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        y[j] *= rdiag[j];
+#pragma unroll
+        for (int kb = (j + 1) / 4; kb < 8; ++kb) {  // column j of L_pp below the diagonal, 16 bytes at a time
+          const float4 l = *reinterpret_cast<const float4*>(Pp + j * nr + 4 * kb);
+          const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (4 * kb + i > j) y[4 * kb + i] = fmaf(-lv[i], y[j], y[4 * kb + i]);
+        }
+      }
+      float* Dg = Dout + ((size_t)g * np + p) * CH_DBLK;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) Dg[k * CH_DSTR + lane] = y[k];
+      Dg[lane * CH_DSTR + 32] = 0.0f;
+    }
+    for (int t = tid - 32; t >= 0 && t < nr - 32; t += CH_NT - 32) {
       const int rl = 32 + t;
       float x[32];
 #pragma unroll
@@ -198,12 +193,24 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
       for (int j = 0; j < 32; ++j) {
         x[j] *= rdiag[j];
 #pragma unroll
-        for (int k = j + 1; k < 32; ++k) x[k] = fmaf(-x[j], Pp[j * nr + k], x[k]);
+        for (int kb = (j + 1) / 4; kb < 8; ++kb) {
+          const float4 l = *reinterpret_cast<const float4*>(Pp + j * nr + 4 * kb);
+          const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (4 * kb + i > j) x[4 * kb + i] = fmaf(-x[j], lv[i], x[4 * kb + i]);
+        }
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) Pp[c * nr + rl] = x[c];
     }
     __syncthreads();
+    // panel p is final: to global memory (the stores overlap the update below)
+    {
+      float* Lg = Lout + (size_t)g * ch_pack(s) + ch_poff(p, sp);
+      for (int e = tid * 4; e < 32 * nr; e += CH_NT * 4)
+        *reinterpret_cast<float4*>(Lg + e) = *reinterpret_cast<const float4*>(Pp + e);
+    }
     // 3. trailing update: block (rb, q), p < q <= rb < np, of panel q minus
     //    L[rb rows, panel p] L[q rows, panel p]^T; one warp per block
     const int nt = np - 1 - p, ntile = nt * (nt + 1) / 2;
@@ -249,32 +256,6 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
     }
     __syncthreads();
   }
-  // L (packed) to global memory
-  const int tot = ch_pack(s);
-  float* Lg = Lout + (size_t)g * tot;
-  for (int e = tid * 4; e < tot; e += CH_NT * 4)
-    *reinterpret_cast<float4*>(Lg + e) = *reinterpret_cast<const float4*>(P + e);
-  // inverses of the diagonal blocks, row-major: lane c forms column c of
-  // L_pp^{-1} by forward substitution on e_c
-  for (int p = warp; p < np; p += CH_NT / 32) {
-    const int nr = sp - 32 * p;
-    const float* Pp = P + ch_poff(p, sp);
-    float y[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) y[k] = (k == lane) ? 1.0f : 0.0f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      y[j] *= __frcp_rn(Pp[j * nr + j]);
-#pragma unroll
-      for (int k = j + 1; k < 32; ++k) y[k] = fmaf(-Pp[j * nr + k], y[j], y[k]);
-    }
-    float* Dg = Dout + ((size_t)g * np + p) * CH_DBLK;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) Dg[k * CH_DSTR + lane] = y[k];
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 32; ++k) Dg[k * CH_DSTR + 32] = 0.0f;
-  }
   if (tid == 0 && bad) atomicCAS(status, FCTN_OK, FCTN_E_SINGULAR);
 }
 
@@ -284,7 +265,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
 // block inverses arrive by bulk copies; w is written to the rows of W.
 __host__ __device__ inline size_t ch_subst_bytes(int s) {
   const int np = ch_npan(s);
-  return (size_t)ch_pack(s) * 4 + (size_t)np * CH_DBLK * 4 + 2 * 32 * (size_t)np * 4 + 64 * 4;
+  return (size_t)ch_pack(s) * 4 + (size_t)np * CH_DBLK * 4 + 2 * 32 * (size_t)np * 4;
 }
 
 __global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ Rt, int I, int s,
@@ -299,7 +280,6 @@ __global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ 
   float* Ls = smf;
   float* Ds = Ls + tot;
   float* bv = Ds + np * CH_DBLK;
-  float* red = bv + 2 * sp;
   const float* Lg = Lp + (size_t)g * tot;
   const float* Dg = Dinv + (size_t)g * np * CH_DBLK;
   const bool bulk = ((uintptr_t)Lg % 16) == 0 && ((uintptr_t)Dg % 16) == 0;
@@ -352,34 +332,12 @@ __global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ 
     }
     __syncthreads();
   }
-  // L^T w = z
+  // L^T w = z, right-looking: w_p from the diagonal block's inverse, then
+  // its contribution removed from every earlier z (one thread per column)
   for (int p = np - 1; p >= 0; --p) {
-    const int nr = sp - 32 * p;
-    const float* Lq = Ls + ch_poff(p, sp);
     const float* D = Ds + p * CH_DBLK;
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const int c = warp * 4 + cc;
-      float a0 = 0.0f, a1 = 0.0f;
-      for (int rl = 32 + lane; rl < nr; rl += 32) {
-        const float l = Lq[c * nr + rl];
-        a0 = fmaf(l, bv[32 * p + rl], a0);
-        a1 = fmaf(l, bv[sp + 32 * p + rl], a1);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(CH_FULL, a0, o);
-        a1 += __shfl_xor_sync(CH_FULL, a1, o);
-      }
-      if (lane == 0) {
-        red[c] = a0;
-        red[32 + c] = a1;
-      }
-    }
-    __syncthreads();
     if (warp == 0) {
-      const float y0 = bv[32 * p + lane] - red[lane];
-      const float y1 = bv[sp + 32 * p + lane] - red[32 + lane];
+      const float y0 = bv[32 * p + lane], y1 = bv[sp + 32 * p + lane];
       float w0 = 0.0f, w1 = 0.0f;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
@@ -389,6 +347,24 @@ __global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ 
       }
       bv[32 * p + lane] = w0;
       bv[sp + 32 * p + lane] = w1;
+    }
+    __syncthreads();
+    for (int c = tid; c < 32 * p; c += CH_NT) {
+      const int q = c >> 5, nrq = sp - 32 * q;
+      const float* Lc = Ls + ch_poff(q, sp) + (c & 31) * nrq + 32 * (p - q);  // Lc[i] = L[32 p + i][c]
+      float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+      for (int i4 = 0; i4 < 8; ++i4) {
+        const float4 l = *reinterpret_cast<const float4*>(Lc + 4 * i4);
+        const float lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a0 = fmaf(lv[u], bv[32 * p + 4 * i4 + u], a0);
+          a1 = fmaf(lv[u], bv[sp + 32 * p + 4 * i4 + u], a1);
+        }
+      }
+      bv[c] -= a0;
+      bv[sp + c] -= a1;
     }
     __syncthreads();
   }
@@ -476,7 +452,7 @@ __global__ void __launch_bounds__(256) k_bgemm(const float* __restrict__ A, cons
 // Neumaier's compensation, so the sum carries about twice the FP32
 // precision (FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU);
 // Y, the stencil of L and the final difference are FP64.
-constexpr int RD_ROWS = 16;
+constexpr int RD_ROWS = 8;
 
 __device__ __forceinline__ void df_add(float& s, float& c, float p) {
   const float t = s + p;
@@ -484,6 +460,8 @@ __device__ __forceinline__ void df_add(float& s, float& c, float p) {
   s = t;
 }
 
+// One output per thread (row r = tid / 32 of the tile, column tid % 32); the
+// even and odd terms of the sum go to two independent compensated chains.
 __global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd, const double* __restrict__ A64,
                                                   const float* __restrict__ Ac, const float* __restrict__ Alo,
                                                   const float* __restrict__ G, int I, int s, double lam, double rho,
@@ -492,7 +470,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd,
   float* Ah = rsm;                    // [RD_ROWS][s]
   float* Al = Ah + RD_ROWS * s;       // [RD_ROWS][s]
   float* Gt = Al + RD_ROWS * s;       // [s][33]: columns j0 .. j0 + 31 of G
-  const int tid = threadIdx.x, r = tid >> 4, cx = tid & 15;
+  const int tid = threadIdx.x, r = tid >> 5, cx = tid & 31;
   const int i0 = blockIdx.y * RD_ROWS, j0 = blockIdx.x * 32;
   for (int e = tid; e < RD_ROWS * s; e += 256) {
     const int rr = e / s, q = e - rr * s;
@@ -505,32 +483,35 @@ __global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd,
     Gt[q * 33 + c] = j0 + c < s ? G[(size_t)q * s + j0 + c] : 0.0f;
   }
   __syncthreads();
-  float s0 = 0.f, k0 = 0.f, s1 = 0.f, k1 = 0.f;
+  float sa = 0.f, ka = 0.f, sb = 0.f, kb = 0.f;
   const float* ah = Ah + r * s;
   const float* al = Al + r * s;
-  for (int q = 0; q < s; ++q) {
-    const float h = ah[q], l = al[q];
-    const float g0 = Gt[q * 33 + cx], g1 = Gt[q * 33 + cx + 16];
-    const float p0 = h * g0, p1 = h * g1;
-    k0 += fmaf(h, g0, -p0);
-    k1 += fmaf(h, g1, -p1);
-    k0 = fmaf(l, g0, k0);
-    k1 = fmaf(l, g1, k1);
-    df_add(s0, k0, p0);
-    df_add(s1, k1, p1);
+  int q = 0;
+  for (; q + 1 < s; q += 2) {
+    const float h0 = ah[q], l0 = al[q], g0 = Gt[q * 33 + cx];
+    const float h1 = ah[q + 1], l1 = al[q + 1], g1 = Gt[(q + 1) * 33 + cx];
+    const float p0 = h0 * g0, p1 = h1 * g1;
+    ka += fmaf(h0, g0, -p0);
+    kb += fmaf(h1, g1, -p1);
+    ka = fmaf(l0, g0, ka);
+    kb = fmaf(l1, g1, kb);
+    df_add(sa, ka, p0);
+    df_add(sb, kb, p1);
   }
-  const int i = i0 + r;
-  if (i >= I) return;
+  if (q < s) {
+    const float h0 = ah[q], l0 = al[q], g0 = Gt[q * 33 + cx];
+    const float p0 = h0 * g0;
+    ka += fmaf(h0, g0, -p0);
+    ka = fmaf(l0, g0, ka);
+    df_add(sa, ka, p0);
+  }
+  const int i = i0 + r, j = j0 + cx;
+  if (i >= I || j >= s) return;
   const int im = (i - 1 + I) % I, ip = (i + 1) % I;
-#pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    const int j = j0 + cx + 16 * b;
-    if (j >= s) continue;
-    const double ag = b == 0 ? (double)s0 + (double)k0 : (double)s1 + (double)k1;
-    const double a = A64[(size_t)i * s + j];
-    const double la = c0 * a + c1 * (A64[(size_t)im * s + j] + A64[(size_t)ip * s + j]);
-    R[(size_t)i * s + j] = (float)(Yd[(size_t)i * s + j] - lam * la - rho * a - ag);
-  }
+  const double ag = ((double)sa + (double)sb) + ((double)ka + (double)kb);
+  const double a = A64[(size_t)i * s + j];
+  const double la = c0 * a + c1 * (A64[(size_t)im * s + j] + A64[(size_t)ip * s + j]);
+  R[(size_t)i * s + j] = (float)(Yd[(size_t)i * s + j] - lam * la - rho * a - ag);
 }
 
 }  // namespace
