@@ -237,6 +237,8 @@ struct TgArgs {
 // elements, 16-byte multiple) for the GEMM: boxes of 128 bytes of K by
 // box_rows rows, 128-byte swizzle.  elem: 4 (FP32 / TF32) or 2 (BF16).
 int tg_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int elem, int box_rows);
+// Unswizzled FP32 map (box box_rows x box_cols, zero fill outside the matrix).
+int tma_map_f32(void* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows);
 size_t tg_smem_bytes(int BN, int S);
 // Launch; bf16 selects the BF16 operands and MMA kind.
 void launch_tg_gemm(const void* mapA, const void* mapB, const TgArgs& a, int bf16, cudaStream_t st);

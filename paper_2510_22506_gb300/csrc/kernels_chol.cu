@@ -28,6 +28,10 @@
 //   A = Q W (k_bgemm, FP64 master with its double-float split),
 //   R = Y - lam L A - rho A - A G (k_resid_df), then R~ = Q^T R, the
 //   substitution again and A += Q W.
+#include <cuda.h>
+
+#include <cstring>
+
 #include "fctn_internal.cuh"
 
 namespace {
@@ -91,43 +95,61 @@ __device__ __forceinline__ void ch_bar_init(uint64_t* bar) {
 // layout the solve kernel reads without bank conflicts in both orientations).
 constexpr int CH_DSTR = 33, CH_DBLK = 32 * CH_DSTR;
 
+// Tensor maps of G for the panels: map q loads rows 32 q .. 32 q + 31 of G
+// (columns of panel q) and columns 32 q .. sp - 1 (its rows) as one dense
+// 32 x (sp - 32 q) box, which is the panel's column-major layout; outside G
+// the box reads zero.
+struct ChMaps {
+  CUtensorMap m[CH_MAXS / 32];
+  int on;
+};
+
 
 __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__ G, int s, int I, double lam,
                                                        double c0, double c1, double rho, float* __restrict__ Lout,
-                                                       float* __restrict__ Dout, int* status) {
-  extern __shared__ __align__(16) float P[];
+                                                       float* __restrict__ Dout, int* status,
+                                                       const __grid_constant__ ChMaps maps) {
+  // TMA boxes need a 128-byte aligned destination: checked below, the
+  // scalar path is taken otherwise
+  extern __shared__ __align__(128) float P[];
   __shared__ float rdiag[32];
   __shared__ int bad;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = ch_npan(s), sp = 32 * np;
   const float shift = (float)(lam * (c0 + 2.0 * c1 * cospi(2.0 * (double)g / (double)I)) + rho);
-  // G into the panels.  G is symmetric, so column col of a panel (rows
-  // 32 q .. s - 1) is the contiguous row segment G[col][32 q .. s): with
-  // s % 4 == 0, 16-byte asynchronous copies (all of them in flight at once),
-  // else scalar loads.  Rows s .. sp - 1 are zero and columns s .. sp - 1 the
-  // identity (the padding); the shift c is added to the pivots in step 1.
-  const bool vec = (s % 4) == 0 && ((uintptr_t)G % 16) == 0;
+  // G into the panels.  G is symmetric, so column col of panel q (rows
+  // 32 q .. s - 1) is the row segment G[col][32 q .. s).  With tensor maps
+  // (s % 4 == 0): one TMA box per panel (zero outside G), then the identity
+  // on the padded diagonal; otherwise scalar loads.  The shift c is added to
+  // the pivots in step 1.
+  __shared__ __align__(8) uint64_t gbar;
   if (tid == 0) bad = 0;
-  for (int col = warp; col < sp; col += CH_NT / 32) {
-    const int q = col >> 5, nr = sp - 32 * q;
-    float* dst = P + ch_poff(q, sp) + (col & 31) * nr - 32 * q;  // dst[r] = element (r, col)
-    if (col >= s) {
-      for (int r = 32 * q + lane; r < sp; r += 32) dst[r] = (r == col) ? 1.0f : 0.0f;
-    } else if (vec) {
-      for (int r = 32 * q + 4 * lane; r < sp; r += 128) {
-        if (r < s) {
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ch_su32(dst + r)),
-                       "l"(G + (size_t)col * s + r)
-                       : "memory");
-        } else {
-          *reinterpret_cast<float4*>(dst + r) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-    } else {
-      for (int r = 32 * q + lane; r < sp; r += 32) dst[r] = r < s ? G[(size_t)col * s + r] : 0.0f;
+  if (maps.on && (ch_su32(P) & 127u) == 0) {
+    if (tid == 0) {
+      ch_bar_init(&gbar);
+      ch_expect(&gbar, (unsigned)ch_pack(s) * 4u);
+      for (int q = 0; q < np; ++q)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];\n" ::"r"(ch_su32(P + ch_poff(q, sp))),
+            "l"((uint64_t)&maps.m[q]), "r"(32 * q), "r"(32 * q), "r"(ch_su32(&gbar))
+            : "memory");
+    }
+    __syncthreads();
+    if (!ch_wait(&gbar, 0) && tid == 0) atomicCAS(status, FCTN_OK, FCTN_E_TIMEOUT);
+    __syncthreads();
+    if (tid < sp - s) {  // padded columns: identity on the diagonal
+      const int col = s + tid, q = col >> 5;
+      P[ch_poff(q, sp) + (col & 31) * (sp - 32 * q) + (col - 32 * q)] = 1.0f;
+    }
+  } else {
+    for (int col = warp; col < sp; col += CH_NT / 32) {
+      const int q = col >> 5, nr = sp - 32 * q;
+      float* dst = P + ch_poff(q, sp) + (col & 31) * nr - 32 * q;  // dst[r] = element (r, col)
+      for (int r = 32 * q + lane; r < sp; r += 32)
+        dst[r] = (col < s && r < s) ? G[(size_t)col * s + r] : (r == col ? 1.0f : 0.0f);
     }
   }
-  if (vec) asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   for (int p = 0; p < np; ++p) {
     const int nr = sp - 32 * p;
@@ -529,7 +551,13 @@ void launch_chol_factor(const float* G, int I, int s, double lam, double c0, dou
     attr = true;
   }
   const size_t bytes = (size_t)ch_pack(s) * 4;
-  k_chol_factor<<<chol_groups(I), CH_NT, bytes, st>>>(G, s, I, lam, c0, c1, rho, L, Dinv, status);
+  ChMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  maps.on = (s % 4) == 0 ? 1 : 0;
+  const int np = ch_npan(s), sp = 32 * np;
+  for (int q = 0; q < np && maps.on; ++q)
+    if (tma_map_f32(&maps.m[q], G, s, s, s, sp - 32 * q, 32) != FCTN_OK) maps.on = 0;
+  k_chol_factor<<<chol_groups(I), CH_NT, bytes, st>>>(G, s, I, lam, c0, c1, rho, L, Dinv, status, maps);
 }
 
 void launch_chol_subst(const float* Rt, int I, int s, const float* L, const float* Dinv, float* W, int* status,

@@ -362,6 +362,25 @@ int tg_make_map(void* map, const void* base, int64_t rows, int64_t cols, int64_t
   return r == CUDA_SUCCESS ? FCTN_OK : FCTN_E_UNSUPPORTED;
 }
 
+// Row-major FP32 matrix (rows x cols, leading dimension ld) with an
+// unswizzled box of box_rows x box_cols (dense in shared memory, inner
+// dimension box_cols); elements outside the matrix load as zero.
+int tma_map_f32(void* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return FCTN_E_CUDA;
+  if (((uintptr_t)base & 15) || (ld * 4) % 16 || box_rows < 1 || box_rows > 256 || box_cols < 4 || box_cols > 256 ||
+      (box_cols * 4) % 16)
+    return FCTN_E_UNSUPPORTED;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  CUresult r = fn((CUtensorMap*)map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? FCTN_OK : FCTN_E_UNSUPPORTED;
+}
+
 size_t tg_smem_bytes(int BN, int S) { return (size_t)S * (128 * 128 + (size_t)BN * 128) + 1024; }
 
 // BN: N rounded up to 16 (one column tile when N <= 256, else tiles of 256);
