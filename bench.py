@@ -372,10 +372,11 @@ def run_ours(args):
                 "step": f"set_data + set_factors from pinned host buffers, {e2e_sweeps} sweeps, X back to pinned host memory"},
     }
     if ws == 1 and not args.no_extras:
-        line["solve_routes"] = solve_routes(F, Y, mask, init, R, precision, args.steps)
-        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, args.steps, tune=not args.no_tune)
+        xs = min(args.steps, 20)  # timed sweeps of the comparison runs
+        line["solve_routes"] = solve_routes(F, Y, mask, init, R, precision, xs)
+        line["precision_modes"] = precision_modes(F, name, truth, Y, mask, init, R, xs, tune=not args.no_tune)
         if name != "c2":
-            line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), args.steps, quality_sweeps=0,
+            line["secondary_c2"] = precision_modes(F, "c2", *gpu_inputs(F, "c2"), xs, quality_sweeps=0,
                                                    tune=not args.no_tune)
         line["rank_growth"] = rank_growth_run(F, "c2", *gpu_inputs(F, "c2"))
         line["serving"] = serving_mix(args.serve_jobs, tune=not args.no_tune)
@@ -573,23 +574,28 @@ def run_reference(args):
     if rank != 0:
         return
     O, st, prob = oracle_setup(args.workload)
-    for _ in range(args.warmup):
+    # bounded sample: one untimed sweep at most, then full sweeps until K are
+    # done or the time budget is spent (a 256x256x31x8 sweep takes seconds)
+    for _ in range(min(args.warmup, 1)):
         O.pam_sweep(st, prob, policy="plain")
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done = 0
+    while done < args.steps and (done == 0 or time.perf_counter() - t0 < args.ref_budget):
         O.pam_sweep(st, prob, policy="plain")
+        done += 1
     el = time.perf_counter() - t0
-    value = args.steps / el
+    value = done / el
     w = synth.WORKLOADS[args.workload]
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": done,
+        "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {DESC[args.workload]}", "dims": list(w["dims"]), "rank": w["r"],
                    "sampling": w["p"], "precision": "fp64 (CPU oracle)", "reuse": True,
                    "order_policy": "plain", "lambda": synth.LAMBDA, "delta": synth.DELTA, "rho": synth.RHO},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{args.steps} full sweeps of workload {args.workload}, one per step"},
+                         "sample": f"{done} full sweeps of workload {args.workload} (one per step, at most "
+                                   f"{args.steps} or {args.ref_budget:.0f} s) after {min(args.warmup, 1)} untimed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -598,7 +604,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4", choices=sorted(DESC))
@@ -608,6 +614,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the precision and serving comparisons")
     ap.add_argument("--no-tune", action="store_true", help="built-in launch shape instead of the autotuner's")
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--ref-budget", type=float, default=60.0, help="seconds of timed oracle sweeps (reference arm)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

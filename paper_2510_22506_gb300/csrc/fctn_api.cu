@@ -1548,9 +1548,11 @@ int sg_launches(const SgPlanH& q) { return q.sh.ksplit > 1 ? 2 : 1; }
 int route_build_m0(fctn_handle* h) {
   HeadRoute& r = h->hr;
   const float* cur = (const float*)h->Ac[1];
+  const bool tf32_ops = r.tc && !r.fp32_now && !r.bf16;  // M_0 is then a TF32 operand: rounded as it is written
   for (int i = 0; i < r.nm0; ++i) {
     float* o = (i == r.nm0 - 1) ? r.M0 : r.U[i % 2];
-    const SgPlanH& q = r.m0[i];
+    SgPlanH q = r.m0[i];
+    q.sh.round_tf32 = (i == r.nm0 - 1 && tf32_ops) ? 1 : 0;
     LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q), run_sg(h, q, cur, (const float*)h->Ac[i + 2], o, r.pm, h->st));
     h->launches += sg_launches(q) - 1;
     cur = o;
@@ -1565,9 +1567,8 @@ int route_build_m0(fctn_handle* h) {
       LAUNCH(FCTN_KC_MERGED, mb, 0.0,
              launch_copy_bf16(r.M0, r.s0, r.P0, r.P0, (__nv_bfloat16*)r.M0b, r.P0, h->st));
       LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 1, h->st));
-    } else {
-      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_copy_f32(r.M0, r.s0, r.P0, r.P0, r.M0, r.P0, 1, h->st));
-      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 1, h->st));
+    } else {  // M_0 already rounded by its contraction
+      LAUNCH(FCTN_KC_MERGED, mb, 0.0, launch_transpose_f32(r.M0, r.s0, r.P0, r.P0, (float*)r.M0T, r.ld0, 0, h->st));
     }
   }
   r.m0_valid = true;

@@ -157,6 +157,7 @@ void fctn_internal_after_sweep(fctn_handle* h, double rel_change);
 struct SgShape {
   int M, N, K, ksplit, kchunk;
   int a_mfast, b_nfast;  // loader lanes run along m (n) when that digit is contiguous in A (B), else along k
+  int round_tf32;        // C rounded to the nearest TF32 value (a tensor-core operand)
 };
 struct SgTabs {
   const int *am, *cm, *bn, *cn, *ak, *bk;

@@ -19,6 +19,12 @@ namespace {
 
 constexpr int SG_BM = 128, SG_BN = 64, SG_BK = 16, SG_THREADS = 256;
 
+__device__ __forceinline__ float sg_tf32(float v) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+  return __uint_as_float(u);
+}
+
 __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, const float* __restrict__ A,
                                                       const float* __restrict__ B, float* __restrict__ C,
                                                       float* __restrict__ part) {
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
       const int n = n0 + tx * 4 + j;
       if (n >= sh.N) continue;
       if (sh.ksplit == 1)
-        C[(int64_t)t.cm[m] + t.cn[n]] = acc[i][j];
+        C[(int64_t)t.cm[m] + t.cn[n]] = sh.round_tf32 ? sg_tf32(acc[i][j]) : acc[i][j];
       else
         part[((int64_t)blockIdx.z * sh.M + m) * sh.N + n] = acc[i][j];
     }
@@ -141,7 +147,7 @@ __global__ void k_sg_reduce(SgShape sh, SgTabs t, const float* __restrict__ part
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
     const float s = split_sum(part, sh.ksplit, MN, e);
     const int m = (int)(e / sh.N), n = (int)(e - (int64_t)m * sh.N);
-    C[(int64_t)t.cm[m] + t.cn[n]] = s;
+    C[(int64_t)t.cm[m] + t.cn[n]] = sh.round_tf32 ? sg_tf32(s) : s;
   }
 }
 
@@ -246,6 +252,7 @@ int grid_for(int64_t n, int threads) {
 
 void sg_shape(int M, int N, int K, SgShape* sh, int split_ctas) {
   sh->a_mfast = sh->b_nfast = 0;
+  sh->round_tf32 = 0;
   sh->M = M;
   sh->N = N;
   sh->K = K;
