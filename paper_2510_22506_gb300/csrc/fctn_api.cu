@@ -96,9 +96,12 @@ struct HeadRoute {
   SgPlanH ys[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k >= 1: Z (x) A_t for t in yfac[k]
   int yfac[FCTN_MAX_ORDER][FCTN_MAX_ORDER] = {};
   int nys[FCTN_MAX_ORDER] = {};
+  int yshare[FCTN_MAX_ORDER] = {};  // leading steps of ys[k] whose result factor k-1's chain left in U
   SgPlanH hg[FCTN_MAX_ORDER];  // H_t
-  SgPlanH env[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k: chain of H_t, t != k (ascending)
+  SgPlanH env[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k: chain of H_t, t != k, in the order efac[k]
+  int efac[FCTN_MAX_ORDER][FCTN_MAX_ORDER] = {};
   int nenv[FCTN_MAX_ORDER] = {};
+  int eshare[FCTN_MAX_ORDER] = {};  // leading steps of env[k] whose result factor k-1's chain left in E
   int64_t u_elems = 0, e_elems = 0, part_main = 0, part_side = 0;
   float *M0 = nullptr, *Zb = nullptr, *U[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr};
   float* H[FCTN_MAX_ORDER] = {};
@@ -1130,15 +1133,37 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
     }
     r.nys[k] = n;
   }
+  // Leading steps shared with factor k-1's chain: the same factors in the
+  // same order give the same intermediate (Z and those factors do not change
+  // between the two right-hand sides, since neither k-1 nor k is among
+  // them); shared when the intermediate is still in its U buffer, i.e. when
+  // only the final step of k-1's chain follows it.  With N = 4 the first
+  // step Z (x) A_(1) of factors 2 and 3 is formed once.
+  for (int k = 2; k < N; ++k) {
+    int L = 0;
+    while (L < r.nys[k] - 1 && L < r.nys[k - 1] - 1 && r.yfac[k][L] == r.yfac[k - 1][L]) ++L;
+    r.yshare[k] = (L > 0 && r.nys[k - 1] == L + 1) ? L : 0;
+  }
   // factor Grams and, per k, their chain over t != k (ascending)
   for (int t = 0; t < N; ++t) {
     if ((rc = sg_plan(factor_view(h, t), factor_primed_view(h, t), hgram_view(h, t), &r.hg[t], &t0, sgs))) return rc;
     track(&r.part_side, (int64_t)sg_part_elems(r.hg[t].sh));
   }
+  // Chain order: for the pair {k, k ^ 1} (N >= 4) the factors other than
+  // both come first (ascending) and the partner last, so that the two
+  // chains share everything but their last step: those Grams do not change
+  // between the two factor updates, and the odd member reuses the even
+  // member's intermediate (still in its E buffer: only the final step,
+  // which writes G, follows it).  Otherwise ascending.
   for (int k = 0; k < N; ++k) {
     int ids[FCTN_MAX_ORDER], n = 0;
+    const int pk = k ^ 1;
+    const bool paired = N >= 4 && pk < N;
     for (int t = 0; t < N; ++t)
-      if (t != k) ids[n++] = t;
+      if (t != k && !(paired && t == pk)) ids[n++] = t;
+    if (paired) ids[n++] = pk;
+    for (int i = 0; i < n; ++i) r.efac[k][i] = ids[i];
+    r.eshare[k] = (paired && (k & 1)) ? n - 2 : 0;
     View cur = hgram_view(h, ids[0]);
     for (int q = 1; q < n; ++q) {
       View nx = hgram_view(h, ids[q]);
@@ -1693,11 +1718,10 @@ int route_sweep(fctn_handle* h) {
       CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     }
     {
-      int ids[FCTN_MAX_ORDER], n = 0;
-      for (int t = 0; t < N; ++t)
-        if (t != k) ids[n++] = t;
-      const float* cur = r.H[ids[0]];
-      for (int q = 0; q < r.nenv[k]; ++q) {
+      const int* ids = r.efac[k];
+      const int q0 = r.eshare[k];  // steps already formed for the partner factor
+      const float* cur = q0 > 0 ? r.E[(q0 - 1) % 2] : r.H[ids[0]];
+      for (int q = q0; q < r.nenv[k]; ++q) {
         float* o = (q == r.nenv[k] - 1) ? (float*)h->Gs : r.E[q % 2];
         const SgPlanH& pl = r.env[k][q];
         if (fork) {
@@ -1730,8 +1754,9 @@ int route_sweep(fctn_handle* h) {
       LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.y0), run_sg(h, r.y0, X, r.M0, r.Yraw, r.pm, h->st));
       h->launches += sg_launches(r.y0) - 1;
     } else {
-      const float* cur = r.Zb;
-      for (int q = 0; q < r.nys[k]; ++q) {
+      const int q0 = r.yshare[k];
+      const float* cur = q0 > 0 ? r.U[(q0 - 1) % 2] : r.Zb;
+      for (int q = q0; q < r.nys[k]; ++q) {
         float* o = (q == r.nys[k] - 1) ? r.Yraw : r.U[q % 2];
         const SgPlanH& pl = r.ys[k][q];
         LAUNCH(FCTN_KC_RHS2, 0.0, sg_flops(pl),
