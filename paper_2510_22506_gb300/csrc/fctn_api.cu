@@ -1347,6 +1347,21 @@ int copy_out(fctn_handle* h, void* dst, const void* src, size_t bytes, int where
 }
 
 
+// The trace terms of Eq. 2 for every factor (one launch).
+void launch_traces(fctn_handle* h) {
+  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
+  TraceArgs a{};
+  for (int k = 0; k < h->N; ++k) {
+    a.A[k] = h->A64[k];
+    a.I[k] = h->I[k];
+    a.s[k] = h->s[k];
+    a.c0[k] = sgn * (2.0 + h->p.delta[k]);
+    a.c1[k] = -sgn;
+    a.lam[k] = h->p.lambda[k];
+  }
+  launch_trace_all(a, h->N, h->traces, h->st);
+}
+
 // Rotation threshold of the FP32 Gram eigensolver: the caller's, else one
 // matched to the FP64 refinement of the solve, which removes what the
 // eigenbasis leaves: two refinement steps tolerate off-diagonal ratios of
@@ -1687,8 +1702,7 @@ int route_sweep(fctn_handle* h) {
   for (int t = 0; t < N; ++t)
     if (!r.hvalid[t]) {
       LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[t]),
-             run_sg(h, r.hg[t], (const float*)h->Ac[t], (const float*)h->Ac[t], r.H[t], r.pm, h->st));
-      h->launches += sg_launches(r.hg[t]) - 1;
+             launch_gram_at((const float*)h->Ac[t], (int)h->I[t], (int)h->s[t], r.H[t], h->st));
       r.hvalid[t] = true;
     }
   int rc;
@@ -1771,8 +1785,7 @@ int route_sweep(fctn_handle* h) {
     if ((rc = route_solve(h, k, fork))) return rc;
     // Gram of the new factor for the later Gram chains
     LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[k]),
-           run_sg(h, r.hg[k], (const float*)h->Ac[k], (const float*)h->Ac[k], r.H[k], r.pm, h->st));
-    h->launches += sg_launches(r.hg[k]) - 1;
+           launch_gram_at((const float*)h->Ac[k], (int)h->I[k], (int)h->s[k], r.H[k], h->st));
     if (k == 0 && tcp) {  // Z = X_(0)^T A_(0) with the new head factor (tensor cores)
       if ((rc = route_a0_copies(h))) return rc;
       TgArgs a = r.tz;
@@ -1816,11 +1829,7 @@ int route_sweep(fctn_handle* h) {
            launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
     r.xt_valid = false;  // X moved without its transposed copy
   }
-  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
-  for (int k = 0; k < N; ++k)
-    LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
-           launch_trace_term(h->A64[k], h->I[k], h->s[k], sgn * (2.0 + h->p.delta[k]), -sgn, h->p.lambda[k],
-                             h->traces + 32 * k, h->st));
+  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h));
   LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, nred, h->traces, h->N, h->stats, h->st));
   h->t++;
   return FCTN_OK;
@@ -1880,11 +1889,7 @@ int sweep_body(fctn_handle* h) {
              launch_xupdate_fused_f32(h->pp[last], (const float*)L, (const float*)R, (const float*)h->Ac[last],
                                       (float*)h->X, h->bits, h->p.rho, g, h->red, h->st));
   }
-  const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
-  for (int k = 0; k < h->N; ++k)
-    LAUNCH(FCTN_KC_MISC, 0.0, 0.0,
-           launch_trace_term(h->A64[k], h->I[k], h->s[k], sgn * (2.0 + h->p.delta[k]), -sgn, h->p.lambda[k],
-                             h->traces + 32 * k, h->st));
+  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h));
   LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, xupdate_blocks(g), h->traces, h->N, h->stats, h->st));
   h->t++;
   return FCTN_OK;

@@ -200,6 +200,8 @@ void launch_chol_subst(const float* Rt, int I, int s, const float* L, const floa
 // Alo = float(A64 - Ac)).
 void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, float* out32, double* A64, float* Ac,
                        float* Alo, cudaStream_t st);
+// H = A^T A (s x s) for A (I x s) row-major FP32.
+void launch_gram_at(const float* A, int I, int s, float* H, cudaStream_t st);
 // FP32 R = Yd - lam L A - rho A - A G with A = Ac + Alo, the A G products summed in double-float arithmetic.
 void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const float* Alo, const float* G, int I,
                      int s, double lam, double rho, double c0, double c1, float* R, cudaStream_t st);
@@ -333,7 +335,12 @@ void launch_extrap_f32(double* A, const double* Aold, double alpha, double beta,
 void launch_extrap_f64(double* A, const double* Aold, double alpha, double beta, double* Ac, int64_t n,
                        cudaStream_t st);
 // trace term lam/2 tr(A^T L A) for one factor (A: I x s double) -> out[0]
-void launch_trace_term(const double* A, int64_t I, int64_t s, double c0, double c1, double lam, double* out,
-                       cudaStream_t st);
+// Trace terms lambda_k / 2 tr(A_(k)^T L_k A_(k)) of every factor (Eq. 2), one launch.
+struct TraceArgs {
+  const double* A[FCTN_MAX_ORDER];
+  int64_t I[FCTN_MAX_ORDER], s[FCTN_MAX_ORDER];
+  double c0[FCTN_MAX_ORDER], c1[FCTN_MAX_ORDER], lam[FCTN_MAX_ORDER];
+};
+void launch_trace_all(const TraceArgs& a, int N, double* out, cudaStream_t st);
 // finalize: stats[0]=rel, [1]=objective, [2]=data term, [3]=nonfinite flag
 void launch_finalize(const double* red, int nblocks, const double* traces, int N, double* stats, cudaStream_t st);

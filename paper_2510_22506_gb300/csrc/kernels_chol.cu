@@ -474,6 +474,63 @@ __global__ void __launch_bounds__(256) k_bgemm(const float* __restrict__ A, cons
 // Neumaier's compensation, so the sum carries about twice the FP32
 // precision (FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU);
 // Y, the stencil of L and the final difference are FP64.
+// H = A^T A for A (I x s, row-major FP32): the factor Gram H_t = A_(t)^T A_(t)
+// of the Gram chains.  One 32 x 32 tile of H per CTA for tiles (ta <= tb)
+// only, each written to both triangles; K = I in chunks of 64 as in k_bgemm.
+__global__ void __launch_bounds__(256) k_gram_at(const float* __restrict__ A, int I, int s, float* __restrict__ H) {
+  __shared__ float As[BG_KC][33];
+  __shared__ float Bs[BG_KC][33];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int nt = (s + 31) / 32;
+  int t = blockIdx.x, ta = 0;
+  while (t >= nt - ta) {
+    t -= nt - ta;
+    ++ta;
+  }
+  const int a0 = 32 * ta, b0 = 32 * (ta + t);
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float ra[8], rb[8];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256, k = e >> 5, c = e & 31;
+      const bool kin = k0 + k < I;
+      ra[u] = (kin && a0 + c < s) ? A[(size_t)(k0 + k) * s + a0 + c] : 0.0f;
+      rb[u] = (kin && b0 + c < s) ? A[(size_t)(k0 + k) * s + b0 + c] : 0.0f;
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < I; k0 += BG_KC) {
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256;
+      As[e >> 5][e & 31] = ra[u];
+      Bs[e >> 5][e & 31] = rb[u];
+    }
+    __syncthreads();
+    if (k0 + BG_KC < I) load(k0 + BG_KC);
+#pragma unroll 16
+    for (int k = 0; k < BG_KC; ++k) {
+      const float x0 = As[k][ty], x1 = As[k][ty + 16];
+      const float y0 = Bs[k][tx], y1 = Bs[k][tx + 16];
+      acc[0][0] = fmaf(x0, y0, acc[0][0]);
+      acc[0][1] = fmaf(x0, y1, acc[0][1]);
+      acc[1][0] = fmaf(x1, y0, acc[1][0]);
+      acc[1][1] = fmaf(x1, y1, acc[1][1]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
+      if (a >= s || b >= s) continue;
+      H[(size_t)a * s + b] = acc[u][v];
+      H[(size_t)b * s + a] = acc[u][v];
+    }
+}
+
 constexpr int RD_ROWS = 8;
 
 __device__ __forceinline__ void df_add(float& s, float& c, float p) {
@@ -579,6 +636,11 @@ void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, 
     k_bgemm<BG_SET><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
   else
     k_bgemm<BG_ADD><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+}
+
+void launch_gram_at(const float* A, int I, int s, float* H, cudaStream_t st) {
+  const int nt = (s + 31) / 32;
+  k_gram_at<<<nt * (nt + 1) / 2, 256, 0, st>>>(A, I, s, H);
 }
 
 void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const float* Alo, const float* G, int I,

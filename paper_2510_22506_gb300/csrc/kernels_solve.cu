@@ -1679,16 +1679,22 @@ __global__ void k_extrap(double* __restrict__ A, const double* __restrict__ Aold
 
 // lam/2 * tr(A^T L A) partial sums; L is the cyclic stencil (c0 on the
 // diagonal, c1 on both neighbours, coinciding entries summed).
-__global__ void k_trace(const double* __restrict__ A, int64_t I, int64_t s, double c0, double c1, double lam,
-                        double* __restrict__ out) {
+constexpr int TRACE_BLOCKS = 32;
+
+// The trace terms of every factor in one launch: block (b, k) sums rows
+// b, b + TRACE_BLOCKS, ... of factor k (threads over the columns).
+__global__ void k_trace_all(TraceArgs a, double* __restrict__ out) {
   __shared__ double red[32];
+  const int k = blockIdx.y;
+  const double* A = a.A[k];
+  const int64_t I = a.I[k], s = a.s[k];
   double acc = 0.0;
-  const int64_t n = I * s;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / s, j = e % s;
-    int64_t ip = (i + 1) % I, im = (i - 1 + I) % I;
-    double a = A[e];
-    acc += a * (c0 * a + c1 * (A[ip * s + j] + A[im * s + j]));
+  for (int64_t i = blockIdx.x; i < I; i += gridDim.x) {
+    const int64_t ip = (i + 1) % I, im = (i - 1 + I) % I;
+    for (int64_t j = threadIdx.x; j < s; j += blockDim.x) {
+      const double v = A[i * s + j];
+      acc += v * (a.c0[k] * v + a.c1[k] * (A[ip * s + j] + A[im * s + j]));
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -1696,11 +1702,9 @@ __global__ void k_trace(const double* __restrict__ A, int64_t I, int64_t s, doub
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    out[blockIdx.x] = 0.5 * lam * t;
+    out[k * gridDim.x + blockIdx.x] = 0.5 * a.lam[k] * t;
   }
 }
-
-constexpr int TRACE_BLOCKS = 32;
 
 __global__ void k_finalize(const double* __restrict__ red, int nblocks, const double* __restrict__ traces, int N,
                            double* __restrict__ stats) {
@@ -1781,9 +1785,8 @@ void launch_resid_f64(const double* Y, const double* A, const double* G, int I, 
                       double c0, double c1, double* R, cudaStream_t st) {
   k_resid<double><<<I, 128, 0, st>>>(Y, A, G, I, s, lam, rho, c0, c1, R);
 }
-void launch_trace_term(const double* A, int64_t I, int64_t s, double c0, double c1, double lam, double* out,
-                       cudaStream_t st) {
-  k_trace<<<TRACE_BLOCKS, 256, 0, st>>>(A, I, s, c0, c1, lam, out);
+void launch_trace_all(const TraceArgs& a, int N, double* out, cudaStream_t st) {
+  k_trace_all<<<dim3(TRACE_BLOCKS, (unsigned)N), 256, 0, st>>>(a, out);
 }
 void launch_finalize(const double* red, int nblocks, const double* traces, int N, double* stats, cudaStream_t st) {
   k_finalize<<<1, 256, 0, st>>>(red, nblocks, traces, N, stats);
