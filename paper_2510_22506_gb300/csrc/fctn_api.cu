@@ -90,7 +90,8 @@ struct SgPlanH {
 struct HeadRoute {
   bool on = false;
   int64_t s0 = 0, P0 = 0;
-  SgPlanH m0[FCTN_MAX_ORDER];  // chain 1 .. N-1 building M_0 (nm0 steps)
+  SgPlanH m0[FCTN_MAX_ORDER];  // chain building M_0 from factors m0fac[0], m0fac[1], ... (nm0 steps)
+  int m0fac[FCTN_MAX_ORDER] = {};
   int nm0 = 0;
   SgPlanH y0, z;               // Y_0 raw = X_(0) M_0^T, Z = X_(0)^T A_(0)
   SgPlanH ys[FCTN_MAX_ORDER][FCTN_MAX_ORDER];  // per k >= 1: Z (x) A_t for t in yfac[k]
@@ -1093,14 +1094,48 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
   static const int kSgSplit[4] = {0, 152, 4 * 152, 1};
   const int sgs = kSgSplit[(h->p.tile_code >> 5) & 3];
   auto track = [](int64_t* mx, int64_t v) { *mx = v > *mx ? v : *mx; };
-  // M_0: factors 1 .. N-1 in ascending order
+  // M_0: factors 1 .. N-1, greedily in the order that keeps the chain
+  // intermediates smallest (the pair with the smallest joint tensor first:
+  // for 256x256x31x8, A_(2) (x) A_(3) is 1.3 MB where A_(1) (x) A_(2) is 41 MB)
   {
-    View cur = factor_view(h, 1);
-    for (int t = 2; t < N; ++t) {
-      View nx = factor_view(h, t);
-      View o = (t == N - 1) ? m0_view(h) : joint_view(cur, nx, &rc);
+    int order[FCTN_MAX_ORDER], n = 0;
+    bool used[FCTN_MAX_ORDER] = {};
+    int64_t best = -1;
+    for (int a = 1; a < N; ++a)
+      for (int b = a + 1; b < N; ++b) {
+        int rcj = FCTN_OK;
+        const int64_t sz = N == 3 ? 0 : joint_view(factor_view(h, a), factor_view(h, b), &rcj).size();
+        if (rcj == FCTN_OK && (best < 0 || sz < best)) {
+          best = sz;
+          order[0] = a;
+          order[1] = b;
+        }
+      }
+    used[order[0]] = used[order[1]] = true;
+    n = 2;
+    View cur = joint_view(factor_view(h, order[0]), factor_view(h, order[1]), &rc);
+    if (rc) return fail(rc, "head route: chain intermediate has too many indices");
+    while (n < N - 1) {
+      int pick = -1;
+      int64_t bs = -1;
+      for (int t = 1; t < N; ++t) {
+        if (used[t]) continue;
+        int rcj = FCTN_OK;
+        const int64_t sz = joint_view(cur, factor_view(h, t), &rcj).size();
+        if (rcj == FCTN_OK && (bs < 0 || sz < bs)) bs = sz, pick = t;
+      }
+      if (pick < 0) return fail(FCTN_E_UNSUPPORTED, "head route: chain intermediate has too many indices");
+      used[pick] = true;
+      order[n++] = pick;
+      cur = joint_view(cur, factor_view(h, pick), &rc);
+    }
+    for (int i = 0; i < N - 1; ++i) r.m0fac[i] = order[i];
+    cur = factor_view(h, order[0]);
+    for (int i = 1; i < N - 1; ++i) {
+      View nx = factor_view(h, order[i]);
+      View o = (i == N - 2) ? m0_view(h) : joint_view(cur, nx, &rc);
       if (rc) return fail(rc, "head route: chain intermediate has too many indices");
-      if (t < N - 1) track(&r.u_elems, o.size());
+      if (i < N - 2) track(&r.u_elems, o.size());
       if ((rc = sg_plan(cur, nx, o, &r.m0[r.nm0], &t0, sgs))) return rc;
       track(&r.part_main, (int64_t)sg_part_elems(r.m0[r.nm0].sh));
       r.nm0++;
@@ -1584,16 +1619,17 @@ void run_sg(const fctn_handle* h, const SgPlanH& q, const float* A, const float*
 double sg_flops(const SgPlanH& q) { return 2.0 * (double)q.sh.M * q.sh.N * q.sh.K; }
 int sg_launches(const SgPlanH& q) { return q.sh.ksplit > 1 ? 2 : 1; }
 
-// M_0 from the present factors 1 .. N-1 (ascending chain).
+// M_0 from the present factors 1 .. N-1 (the planned chain order).
 int route_build_m0(fctn_handle* h) {
   HeadRoute& r = h->hr;
-  const float* cur = (const float*)h->Ac[1];
+  const float* cur = (const float*)h->Ac[r.m0fac[0]];
   const bool tf32_ops = r.tc && !r.fp32_now && !r.bf16;  // M_0 is then a TF32 operand: rounded as it is written
   for (int i = 0; i < r.nm0; ++i) {
     float* o = (i == r.nm0 - 1) ? r.M0 : r.U[i % 2];
     SgPlanH q = r.m0[i];
     q.sh.round_tf32 = (i == r.nm0 - 1 && tf32_ops) ? 1 : 0;
-    LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q), run_sg(h, q, cur, (const float*)h->Ac[i + 2], o, r.pm, h->st));
+    LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q),
+           run_sg(h, q, cur, (const float*)h->Ac[r.m0fac[i + 1]], o, r.pm, h->st));
     h->launches += sg_launches(q) - 1;
     cur = o;
   }
