@@ -124,19 +124,40 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
       buf ^= 1;
     }
   }
+  // this thread's four columns: one 16-byte store per row when they are
+  // consecutive in the output (and aligned), else element by element
+  const int nb = n0 + tx * 4;
+  int cn4[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cn4[j] = (nb + j < sh.N) ? t.cn[nb + j] : -1;
+  const bool run4 = sh.ksplit == 1 && nb + 3 < sh.N && cn4[1] == cn4[0] + 1 && cn4[2] == cn4[0] + 2 &&
+                    cn4[3] == cn4[0] + 3;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int mm = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
     const int m = m0 + mm;
     if (m >= sh.M) continue;
+    float v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx * 4 + j;
-      if (n >= sh.N) continue;
-      if (sh.ksplit == 1)
-        C[(int64_t)t.cm[m] + t.cn[n]] = sh.round_tf32 ? sg_tf32(acc[i][j]) : acc[i][j];
-      else
-        part[((int64_t)blockIdx.z * sh.M + m) * sh.N + n] = acc[i][j];
+    for (int j = 0; j < 4; ++j) v[j] = sh.round_tf32 ? sg_tf32(acc[i][j]) : acc[i][j];
+    if (sh.ksplit == 1) {
+      float* o = C + (int64_t)t.cm[m];
+      if (run4 && (((uintptr_t)(o + cn4[0])) & 15) == 0) {
+        *reinterpret_cast<float4*>(o + cn4[0]) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (cn4[j] >= 0) o[cn4[j]] = v[j];
+      }
+    } else {
+      float* o = part + ((int64_t)blockIdx.z * sh.M + m) * sh.N + nb;
+      if (nb + 3 < sh.N && (((uintptr_t)o) & 15) == 0) {
+        *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (nb + j < sh.N) o[j] = acc[i][j];
+      }
     }
   }
 }

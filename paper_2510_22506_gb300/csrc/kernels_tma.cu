@@ -239,16 +239,23 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         if (row >= a.M) continue;
-        if (a.mode == TG_PARTIAL) {
-          float* o = a.out + ((int64_t)blockIdx.z * a.M + row) * a.N;
+        if (a.mode == TG_PARTIAL || a.mode == TG_STORE) {
+          // 16 consecutive columns of this lane's row: four 16-byte stores
+          // when they are whole and aligned, else element by element
+          float* o = a.mode == TG_PARTIAL ? a.out + ((int64_t)blockIdx.z * a.M + row) * a.N + n0 + c0
+                                          : a.out + (int64_t)row * a.ldo + n0 + c0;
+          float f[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (n0 + c0 + j < a.N) o[n0 + c0 + j] = nk > 0 ? __uint_as_float(v[j]) : 0.f;
-        } else if (a.mode == TG_STORE) {
-          float* o = a.out + (int64_t)row * a.ldo;
+          for (int j = 0; j < 16; ++j) f[j] = nk > 0 ? __uint_as_float(v[j]) : 0.f;
+          if (n0 + c0 + 16 <= a.N && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (n0 + c0 + j < a.N) o[n0 + c0 + j] = nk > 0 ? __uint_as_float(v[j]) : 0.f;
+            for (int u = 0; u < 4; ++u)
+              *reinterpret_cast<float4*>(o + 4 * u) = make_float4(f[4 * u], f[4 * u + 1], f[4 * u + 2], f[4 * u + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (n0 + c0 + j < a.N) o[j] = f[j];
+          }
         } else {
           // F^T[j, i]: Eq. 10 on X_(1)[i, j] (row j = this lane, i = column)
           const float r = (float)a.rho, inv = (float)(1.0 / (1.0 + a.rho));
