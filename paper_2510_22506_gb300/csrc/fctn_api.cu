@@ -1428,7 +1428,7 @@ int prep_f32_launches(const fctn_handle* h, int k) {
 // Solve of Eq. 5 for factor k through the shifted Cholesky factors, then
 // refine_steps passes on the residual of Eq. 5 (summed in double-float):
 // Q^T Y, substitution, A = Q W; R, Q^T R, substitution, A += Q W.
-int chol_solve(fctn_handle* h, int k) {
+int chol_solve(fctn_handle* h, int k, bool rt_done = false) {
   const int I = (int)h->I[k], s = (int)h->s[k];
   const double lam = h->p.lambda[k], rho = h->p.rho;
   const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
@@ -1436,8 +1436,9 @@ int chol_solve(fctn_handle* h, int k) {
   float* W = (float*)h->Z;
   float* Ac = (float*)h->Ac[k];
   const double ge = 2.0 * (double)I * I * s, sub = 2.0 * (double)I * s * s;
-  LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
-         launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
+  if (!rt_done)  // Q^T Y (the head route forms it before joining the factorization branch)
+    LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
+           launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
   LAUNCH(FCTN_KC_SOLVE, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
   LAUNCH(FCTN_KC_SOLVE, 0.0, ge, launch_basis_gemm(1, h->Q32[k], W, I, s, nullptr, h->A64[k], Ac, h->Alo, h->st));
   for (int r = 0; r < h->p.refine_steps; ++r) {
@@ -1669,7 +1670,7 @@ int route_a0_copies(fctn_handle* h) {
 
 // Eq. 8 solve with its FP64 refinement for factor k (FP32 operands), the
 // eigendecomposition first unless it already ran on the side stream.
-int route_solve(fctn_handle* h, int k, bool eig_done) {
+int route_solve(fctn_handle* h, int k, bool eig_done, bool rt_done) {
   const int I = (int)h->I[k], s = (int)h->s[k];
   const double lam = h->p.lambda[k], rho = h->p.rho;
   const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
@@ -1700,7 +1701,7 @@ int route_solve(fctn_handle* h, int k, bool eig_done) {
   }
   const int nref = h->p.refine_steps;
   if (h->chol[k]) {
-    int rc = chol_solve(h, k);
+    int rc = chol_solve(h, k, rt_done);
     if (rc) return rc;
   } else {
     LAUNCH(FCTN_KC_SOLVE, 0.0, fwd_flops, fwd_f32(h, k, (const float*)h->Ys, Z));
@@ -1817,8 +1818,13 @@ int route_sweep(fctn_handle* h) {
     }
     LAUNCH(FCTN_KC_REDUCE, 0.0, 0.0,
            launch_finish_rhs(r.Yraw, h->A64[k], rho, h->Yd, (float*)h->Ys, (int64_t)I * s, h->st));
+    // Q^T Y of the Cholesky solve does not need the factorization: formed
+    // here, beside the factorization branch, before the join
+    if (h->chol[k])
+      LAUNCH(FCTN_KC_SOLVE, 0.0, 2.0 * (double)I * I * s,
+             launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
     if (fork && !h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-    if ((rc = route_solve(h, k, fork))) return rc;
+    if ((rc = route_solve(h, k, fork, h->chol[k]))) return rc;
     // Gram of the new factor for the later Gram chains
     LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(r.hg[k]),
            launch_gram_at((const float*)h->Ac[k], (int)h->I[k], (int)h->s[k], r.H[k], h->st));
