@@ -67,7 +67,9 @@ CLASS_KERNEL = {
     "env": ("k_sgemm (factor Grams and their chains)", "alu"),
     "rhs2": ("k_sgemm (right-hand sides 2..N from Z)", "alu"),
     "merged": ("k_sgemm (M_1) + operand copies", "alu"),
-    "solve": ("k_bgemm (Q^T R, Q W), k_chol_subst, k_resid_df", "alu"),
+    "solve": ("k_bgemm (Q^T R, Q W with the L_k basis)", "alu"),
+    "subst": ("k_chol_subst (triangular substitutions, one CTA per row group)", "alu"),
+    "resid": ("k_resid_df (Eq. 5 residual, double-float A G)", "alu"),
     "eigaux": ("k_mm_small, k_first_order, k_eig_apply", "alu"),
     "reduce": ("k_tg_reduce, k_finish_rhs", "hbm"),
     "misc": ("k_trace, k_finalize, copies", "hbm"),

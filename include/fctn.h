@@ -279,14 +279,16 @@ enum {
   FCTN_KC_GRAM = 1,     /* Gram + right-hand side, split over the columns of M_k        */
   FCTN_KC_REDUCE = 2,   /* fixed-order reduction of the split partials                  */
   FCTN_KC_EIG = 3,      /* Gram eigendecomposition, or the shifted Cholesky factors     */
-  FCTN_KC_SOLVE = 4,    /* Eq. 8 (or Cholesky) solve and its FP64 refinement            */
+  FCTN_KC_SOLVE = 4,    /* Eq. 8 solve and refinement; products with the L_k basis      */
   FCTN_KC_XUPDATE = 5,  /* X update of Eq. 10 fused with F = A_k(k) M_k and the sums    */
   FCTN_KC_MISC = 6,     /* trace terms, finalisation, staging                           */
   FCTN_KC_ENV = 7,      /* Grams of the factors and their chains (Gram of M_k)          */
   FCTN_KC_RHS2 = 8,     /* right-hand sides of factors 2..N from Z (chain contractions) */
   FCTN_KC_EIGAUX = 9,   /* warm-start products and rotation application of the large
                            eigensolver (the Jacobi kernel itself is FCTN_KC_EIG)        */
-  FCTN_KC_COUNT = 10
+  FCTN_KC_SUBST = 10,   /* Cholesky solve: triangular substitutions of each row group   */
+  FCTN_KC_RESID = 11,   /* Cholesky solve: residual of Eq. 5 for the refinement         */
+  FCTN_KC_COUNT = 12
 };
 
 /* Time every launch of one kernel class with CUDA events recorded on the

@@ -1439,15 +1439,15 @@ int chol_solve(fctn_handle* h, int k, bool rt_done = false) {
   if (!rt_done)  // Q^T Y (the head route forms it before joining the factorization branch)
     LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
            launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
-  LAUNCH(FCTN_KC_SOLVE, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
+  LAUNCH(FCTN_KC_SUBST, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
   LAUNCH(FCTN_KC_SOLVE, 0.0, ge, launch_basis_gemm(1, h->Q32[k], W, I, s, nullptr, h->A64[k], Ac, h->Alo, h->st));
   for (int r = 0; r < h->p.refine_steps; ++r) {
-    LAUNCH(FCTN_KC_SOLVE, 0.0, sub,
+    LAUNCH(FCTN_KC_RESID, 0.0, sub,
            launch_resid_df(h->Yd, h->A64[k], Ac, h->Alo, (const float*)h->Gs, I, s, lam, rho, c0, c1, (float*)h->Rs,
                            h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
            launch_basis_gemm(0, h->QT32[k], (const float*)h->Rs, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
-    LAUNCH(FCTN_KC_SOLVE, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
+    LAUNCH(FCTN_KC_SUBST, 0.0, sub, launch_chol_subst(h->cholRt, I, s, h->cholL, h->cholD, W, h->status, h->st));
     LAUNCH(FCTN_KC_SOLVE, 0.0, ge, launch_basis_gemm(2, h->Q32[k], W, I, s, nullptr, h->A64[k], Ac, h->Alo, h->st));
   }
   return FCTN_OK;

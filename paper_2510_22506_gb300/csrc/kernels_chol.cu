@@ -19,8 +19,9 @@
 // k_chol_factor: one CTA per group: G + c_j I (FP32) in shared memory,
 // right-looking blocked Cholesky G + c_j I = L L^T over the panels (the 32 x 32
 // diagonal block by one warp in registers, the rows below by one thread each,
-// the trailing update in 4 x 8 register tiles of 32 x 32 blocks); writes L and
-// the inverses of its diagonal blocks.  A pivot that is not positive means
+// the trailing update in 4 x 8 register tiles of 32 x 32 blocks, with the
+// next diagonal block factored beside it); writes L and the inverses of its
+// diagonal blocks.  A pivot that is not positive means
 // that G + c_j I is not positive definite (some T_ij of Eq. 8 <= 0): status
 // FCTN_E_SINGULAR, as for the eigen route.
 // The solve around the factors (one refinement step shown):
@@ -105,6 +106,87 @@ struct ChMaps {
 };
 
 
+// Diagonal block of panel p, by one warp: lane r holds row r; column j is
+// scaled by 1 / sqrt(pivot), then the rank-1 update of the columns right of
+// it; rdiag[j] = 1 / l_jj.  Not inlined: it keeps its registers apart from
+// the trailing update it runs beside.
+__device__ __noinline__ void ch_factor_diag(float* __restrict__ P, int p, int sp, int s, float shift,
+                                            float* __restrict__ rdiag, int* bad) {
+  const int lane = threadIdx.x & 31;
+  const int nr = sp - 32 * p;
+  float* Pp = P + ch_poff(p, sp);
+  float d[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    d[c] = Pp[c * nr + lane];
+    if (c == lane && 32 * p + c < s) d[c] += shift;  // G + c I
+  }
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float piv = __shfl_sync(CH_FULL, d[j], j);
+    if (!(piv > 0.0f)) {
+      ok = false;
+      piv = 1.0f;
+    }
+    const float rs = rsqrtf(piv);
+    d[j] = (lane == j) ? piv * rs : d[j] * rs;
+#pragma unroll
+    for (int c = j + 1; c < 32; ++c) d[c] = fmaf(-d[j], __shfl_sync(CH_FULL, d[j], c), d[c]);
+    if (lane == 0) rdiag[j] = rs;
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c <= lane) Pp[c * nr + lane] = d[c];
+  if (!ok && lane == 0) *bad = 1;
+}
+
+// Trailing-update tile ti of panel p (one warp): block (rb, q), p < q <= rb <
+// np, of panel q minus L[rb rows, panel p] L[q rows, panel p]^T.
+__device__ __forceinline__ void ch_syrk_tile(float* __restrict__ P, int p, int sp, int np, int ti) {
+  const int lane = threadIdx.x & 31;
+  const int nr = sp - 32 * p;
+  const float* Pp = P + ch_poff(p, sp);
+  const int r0 = (lane & 7) * 4, cb = (lane >> 3) * 8;
+  int q = p + 1, rem = ti;
+  while (rem >= np - q) {
+    rem -= np - q;
+    ++q;
+  }
+  const int rb = q + rem;
+  const float* Ap = Pp + (32 * rb - 32 * p) + r0;
+  const float* Bp = Pp + (32 * q - 32 * p) + cb;
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < 32; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(Ap + k * nr);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bp + k * nr);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bp + k * nr + 4);
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  const int nq = sp - 32 * q;
+  float* Cq = P + ch_poff(q, sp) + (32 * rb - 32 * q) + r0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float4* o = reinterpret_cast<float4*>(Cq + (cb + j) * nq);
+    float4 v = *o;
+    v.x -= acc[0][j];
+    v.y -= acc[1][j];
+    v.z -= acc[2][j];
+    v.w -= acc[3][j];
+    *o = v;
+  }
+}
+
 __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__ G, int s, int I, double lam,
                                                        double c0, double c1, double rho, float* __restrict__ Lout,
                                                        float* __restrict__ Dout, int* status,
@@ -151,38 +233,11 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
     }
   }
   __syncthreads();
+  if (warp == 0) ch_factor_diag(P, 0, sp, s, shift, rdiag, &bad);
+  __syncthreads();
   for (int p = 0; p < np; ++p) {
     const int nr = sp - 32 * p;
     float* Pp = P + ch_poff(p, sp);
-    // 1. diagonal block: lane r holds row r; column j is scaled by
-    //    1 / sqrt(pivot), then the rank-1 update of the columns right of it
-    if (warp == 0) {
-      float d[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        d[c] = Pp[c * nr + lane];
-        if (c == lane && 32 * p + c < s) d[c] += shift;  // G + c I
-      }
-      bool ok = true;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float piv = __shfl_sync(CH_FULL, d[j], j);
-        if (!(piv > 0.0f)) {
-          ok = false;
-          piv = 1.0f;
-        }
-        const float rs = rsqrtf(piv);
-        d[j] = (lane == j) ? piv * rs : d[j] * rs;
-#pragma unroll
-        for (int c = j + 1; c < 32; ++c) d[c] = fmaf(-d[j], __shfl_sync(CH_FULL, d[j], c), d[c]);
-        if (lane == 0) rdiag[j] = rs;
-      }
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c <= lane) Pp[c * nr + lane] = d[c];
-      if (!ok && lane == 0) bad = 1;
-    }
-    __syncthreads();
     // 2. rows below the block: x L_pp^T = a, one row per thread of warps
     //    1..7; warp 0 meanwhile forms the block's inverse for the solve
     if (warp == 0) {
@@ -233,47 +288,19 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
       for (int e = tid * 4; e < 32 * nr; e += CH_NT * 4)
         *reinterpret_cast<float4*>(Lg + e) = *reinterpret_cast<const float4*>(Pp + e);
     }
-    // 3. trailing update: block (rb, q), p < q <= rb < np, of panel q minus
-    //    L[rb rows, panel p] L[q rows, panel p]^T; one warp per block
+    // 3. trailing update with look-ahead: warp 0 updates the next diagonal
+    //    block (tile 0) and factors it; warp 4, which shares its SM
+    //    sub-partition, stays idle so that the latency-bound factorization
+    //    runs alone there; the other six warps update the remaining blocks
     const int nt = np - 1 - p, ntile = nt * (nt + 1) / 2;
-    const int r0 = (lane & 7) * 4, cb = (lane >> 3) * 8;
-    for (int ti = warp; ti < ntile; ti += CH_NT / 32) {
-      int q = p + 1, rem = ti;
-      while (rem >= np - q) {
-        rem -= np - q;
-        ++q;
-      }
-      const int rb = q + rem;
-      const float* Ap = Pp + (32 * rb - 32 * p) + r0;
-      const float* Bp = Pp + (32 * q - 32 * p) + cb;
-      float acc[4][8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-#pragma unroll 4
-      for (int k = 0; k < 32; ++k) {
-        const float4 a = *reinterpret_cast<const float4*>(Ap + k * nr);
-        const float4 b0 = *reinterpret_cast<const float4*>(Bp + k * nr);
-        const float4 b1 = *reinterpret_cast<const float4*>(Bp + k * nr + 4);
-        const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-      }
-      const int nq = sp - 32 * q;
-      float* Cq = P + ch_poff(q, sp) + (32 * rb - 32 * q) + r0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float4* o = reinterpret_cast<float4*>(Cq + (cb + j) * nq);
-        float4 v = *o;
-        v.x -= acc[0][j];
-        v.y -= acc[1][j];
-        v.z -= acc[2][j];
-        v.w -= acc[3][j];
-        *o = v;
+    if (ntile > 0) {
+      if (warp == 0) {
+        ch_syrk_tile(P, p, sp, np, 0);
+        __syncwarp();
+        ch_factor_diag(P, p + 1, sp, s, shift, rdiag, &bad);
+      } else if (warp != 4) {
+        const int wi = warp < 4 ? warp - 1 : warp - 2;
+        for (int ti = 1 + wi; ti < ntile; ti += 6) ch_syrk_tile(P, p, sp, np, ti);
       }
     }
     __syncthreads();

@@ -108,7 +108,7 @@ EXPORTED = ("fctn_last_error", "fctn_version", "fctn_footprint_bytes", "fctn_cre
             "fctn_server_finished", "fctn_server_group_stats", "fctn_quality", "fctn_grow_ranks", "fctn_autotune",
             "fctn_autotune_tiles")
 KC = {"merged": 0, "gram": 1, "reduce": 2, "eig": 3, "solve": 4, "xupdate": 5, "misc": 6, "env": 7, "rhs2": 8,
-      "eigaux": 9}
+      "eigaux": 9, "subst": 10, "resid": 11}
 
 
 class fctn_server_config(ctypes.Structure):
