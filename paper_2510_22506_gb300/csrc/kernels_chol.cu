@@ -501,6 +501,10 @@ __global__ void __launch_bounds__(256) k_bgemm(const float* __restrict__ A, cons
 // Neumaier's compensation, so the sum carries about twice the FP32
 // precision (FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU);
 // Y, the stencil of L and the final difference are FP64.
+__device__ __forceinline__ void ch_acopy4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(ch_su32(dst)), "l"(src) : "memory");
+}
+
 // H = A^T A for A (I x s, row-major FP32): the factor Gram H_t = A_(t)^T A_(t)
 // of the Gram chains.  One 32 x 32 tile of H per CTA for tiles (ta <= tb)
 // only, each written to both triangles; K = I in chunks of 64 as in k_bgemm.
@@ -578,16 +582,26 @@ __global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd,
   float* Gt = Al + RD_ROWS * s;       // [s][33]: columns j0 .. j0 + 31 of G
   const int tid = threadIdx.x, r = tid >> 5, cx = tid & 31;
   const int i0 = blockIdx.y * RD_ROWS, j0 = blockIdx.x * 32;
+  // operands staged by 4-byte asynchronous copies, all in flight at once
+  // (zeros written directly outside the matrices)
   for (int e = tid; e < RD_ROWS * s; e += 256) {
     const int rr = e / s, q = e - rr * s;
-    const bool in = i0 + rr < I;
-    Ah[e] = in ? Ac[(size_t)(i0 + rr) * s + q] : 0.0f;
-    Al[e] = in ? Alo[(size_t)(i0 + rr) * s + q] : 0.0f;
+    if (i0 + rr < I) {
+      ch_acopy4(Ah + e, Ac + (size_t)(i0 + rr) * s + q);
+      ch_acopy4(Al + e, Alo + (size_t)(i0 + rr) * s + q);
+    } else {
+      Ah[e] = 0.0f;
+      Al[e] = 0.0f;
+    }
   }
   for (int e = tid; e < s * 32; e += 256) {
     const int q = e >> 5, c = e & 31;
-    Gt[q * 33 + c] = j0 + c < s ? G[(size_t)q * s + j0 + c] : 0.0f;
+    if (j0 + c < s)
+      ch_acopy4(Gt + q * 33 + c, G + (size_t)q * s + j0 + c);
+    else
+      Gt[q * 33 + c] = 0.0f;
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   float sa = 0.f, ka = 0.f, sb = 0.f, kb = 0.f;
   const float* ah = Ah + r * s;
