@@ -967,9 +967,16 @@ int64_t max_offset(const View& v) {
 
 // Plan C = A (x) B (every shared label contracted) with C laid out as `C`.
 // The operand that holds C's innermost label plays B, so that consecutive
-// columns n are consecutive in C.
+// columns n are consecutive in C; except for small outputs with one side
+// under 64 (the chains' 36-wide bond pairs), where the wide side plays M so
+// that the narrow one pads a 64-column tile rather than a 128-row one.
 int sg_plan(const View& A0, const View& B0, const View& C, SgPlanH* out, std::vector<int>* tabs, int split = 0) {
-  const bool swap = C.n > 0 && A0.find(C.lab[C.n - 1]) >= 0;
+  bool swap = C.n > 0 && A0.find(C.lab[C.n - 1]) >= 0;
+  {
+    int64_t ma0 = 1, nb0 = 1;
+    for (int i = 0; i < C.n; ++i) (A0.find(C.lab[i]) >= 0 ? ma0 : nb0) *= C.ext[i];
+    if (ma0 * nb0 <= ((int64_t)1 << 22) && (ma0 < 64 || nb0 < 64) && ma0 != nb0) swap = ma0 < nb0;
+  }
   const View& A = swap ? B0 : A0;
   const View& B = swap ? A0 : B0;
   int64_t mext[FCTN_MAXD], ma[FCTN_MAXD], mc[FCTN_MAXD], next[FCTN_MAXD], nb[FCTN_MAXD], nc[FCTN_MAXD];

@@ -25,11 +25,21 @@ __device__ __forceinline__ float sg_tf32(float v) {
   return __uint_as_float(u);
 }
 
+// 4-byte asynchronous copy global -> shared; nbytes = 0 writes a zero
+// (the source is then not read).
+__device__ __forceinline__ void sg_acopy(float* dst, const float* src, int nbytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(nbytes)
+               : "memory");
+}
+
+constexpr int SG_ST = 3;  // pipeline stages of the operand tiles
+
 __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, const float* __restrict__ A,
                                                       const float* __restrict__ B, float* __restrict__ C,
                                                       float* __restrict__ part) {
-  __shared__ __align__(16) float As[2][SG_BK][SG_BM + 4];
-  __shared__ __align__(16) float Bs[2][SG_BK][SG_BN + 4];
+  __shared__ __align__(16) float As[SG_ST][SG_BK][SG_BM + 4];
+  __shared__ __align__(16) float Bs[SG_ST][SG_BK][SG_BN + 4];
   __shared__ int am_s[SG_BM], bn_s[SG_BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;
@@ -39,73 +49,72 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
   __syncthreads();
   // loader mappings: consecutive lanes take consecutive k (the contracted
   // digit is innermost in the operand) or consecutive rows m / columns n
-  // (the row / column digit is innermost), whichever reads memory in order
-  float ra[8], rb[4];
-  auto load = [&](int k0) {
+  // (the row / column digit is innermost), whichever reads memory in order.
+  // The tiles of step k0 go to stage buf by asynchronous copies (zeros
+  // outside the operands), SG_ST - 1 steps ahead of the multiply.
+  auto issue = [&](int k0, int buf) {
     if (sh.a_mfast) {  // A: m = tid % 128, k = tid / 128 + 2 i
+      const int a = am_s[tid & 127];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int k = k0 + (tid >> 7) + 2 * i, a = am_s[tid & 127];
-        ra[i] = (k < ke && a >= 0) ? __ldg(A + (int64_t)a + t.ak[k]) : 0.f;
+        const int kk = (tid >> 7) + 2 * i, k = k0 + kk;
+        const bool v = k < ke && a >= 0;
+        sg_acopy(&As[buf][kk][tid & 127], v ? A + (int64_t)a + t.ak[k] : A, v ? 4 : 0);
       }
     } else {  // A: k = tid % 16, m = tid / 16 + 16 i
-      const int k = k0 + (tid & 15);
+      const int kk = tid & 15, k = k0 + kk;
       const bool kv = k < ke;
       const int ao = kv ? t.ak[k] : 0;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int a = am_s[(tid >> 4) + 16 * i];
-        ra[i] = (kv && a >= 0) ? __ldg(A + (int64_t)a + ao) : 0.f;
+        const int mm = (tid >> 4) + 16 * i, a = am_s[mm];
+        const bool v = kv && a >= 0;
+        sg_acopy(&As[buf][kk][mm], v ? A + (int64_t)a + ao : A, v ? 4 : 0);
       }
     }
     if (sh.b_nfast) {  // B: n = tid % 64, k = tid / 64 + 4 i
+      const int b = bn_s[tid & 63];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int k = k0 + (tid >> 6) + 4 * i, b = bn_s[tid & 63];
-        rb[i] = (k < ke && b >= 0) ? __ldg(B + (int64_t)b + t.bk[k]) : 0.f;
+        const int kk = (tid >> 6) + 4 * i, k = k0 + kk;
+        const bool v = k < ke && b >= 0;
+        sg_acopy(&Bs[buf][kk][tid & 63], v ? B + (int64_t)b + t.bk[k] : B, v ? 4 : 0);
       }
     } else {  // B: k = tid % 16, n = tid / 16 + 16 i
-      const int k = k0 + (tid & 15);
+      const int kk = tid & 15, k = k0 + kk;
       const bool kv = k < ke;
       const int bo = kv ? t.bk[k] : 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int b = bn_s[(tid >> 4) + 16 * i];
-        rb[i] = (kv && b >= 0) ? __ldg(B + (int64_t)b + bo) : 0.f;
+        const int nn = (tid >> 4) + 16 * i, b = bn_s[nn];
+        const bool v = kv && b >= 0;
+        sg_acopy(&Bs[buf][kk][nn], v ? B + (int64_t)b + bo : B, v ? 4 : 0);
       }
     }
-  };
-  auto store = [&](int buf) {
-    if (sh.a_mfast) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) As[buf][(tid >> 7) + 2 * i][tid & 127] = ra[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) As[buf][tid & 15][(tid >> 4) + 16 * i] = ra[i];
-    }
-    if (sh.b_nfast) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) Bs[buf][(tid >> 6) + 4 * i][tid & 63] = rb[i];
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) Bs[buf][tid & 15][(tid >> 4) + 16 * i] = rb[i];
-    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
   float acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  // rows of this thread: ty*4 .. +3 and 64 + ty*4 .. +3 (two float4 reads per k)
-  int buf = 0;
-  if (kb < ke) {
-    load(kb);
-    store(0);
+  const int nsteps = ke > kb ? (ke - kb + SG_BK - 1) / SG_BK : 0;
+  // prologue: stages 0 .. SG_ST - 2 (empty groups keep the wait counts uniform)
+#pragma unroll
+  for (int st = 0; st < SG_ST - 1; ++st) {
+    if (st < nsteps)
+      issue(kb + st * SG_BK, st);
+    else
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  __syncthreads();
-  for (int k0 = kb; k0 < ke; k0 += SG_BK) {
-    const bool more = k0 + SG_BK < ke;
-    if (more) load(k0 + SG_BK);
+  for (int i = 0; i < nsteps; ++i) {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(SG_ST - 2) : "memory");
+    __syncthreads();  // stage i visible to all; stage (i - 1) % SG_ST free for reuse
+    if (i + SG_ST - 1 < nsteps)
+      issue(kb + (i + SG_ST - 1) * SG_BK, (i + SG_ST - 1) % SG_ST);
+    else
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int buf = i % SG_ST;
 #pragma unroll
     for (int kk = 0; kk < SG_BK; ++kk) {
       const float4 a0 = *(const float4*)&As[buf][kk][ty * 4];
@@ -114,16 +123,12 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int ii = 0; ii < 8; ++ii)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    if (more) {
-      store(buf ^ 1);
-      __syncthreads();
-      buf ^= 1;
+        for (int j = 0; j < 4; ++j) acc[ii][j] = fmaf(av[ii], bv[j], acc[ii][j]);
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   // this thread's four columns: one 16-byte store per row when they are
   // consecutive in the output (and aligned), else element by element
   const int nb = n0 + tx * 4;
