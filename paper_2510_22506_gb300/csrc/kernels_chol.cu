@@ -505,6 +505,76 @@ __device__ __forceinline__ void ch_acopy4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(ch_su32(dst)), "l"(src) : "memory");
 }
 
+// The same product with all of K (<= BG_KS16) staged at once by 16-byte
+// asynchronous copies (A rows and B rows of the tile are contiguous when
+// K % 4 == 0 and N % 4 == 0), then multiplied from shared memory.
+constexpr int BG_KS16 = 256;
+constexpr int BG_AST = BG_KS16 + 4, BG_BST = 36;  // row strides (16-byte rows)
+__host__ __device__ inline size_t bg16_smem_bytes() { return ((size_t)32 * BG_AST + (size_t)BG_KS16 * BG_BST) * 4; }
+
+__device__ __forceinline__ void ch_acopy16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ch_su32(dst)), "l"(src) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bgemm16(const float* __restrict__ A, const float* __restrict__ B, int M,
+                                                 int N, int K, float* __restrict__ out32, double* __restrict__ A64,
+                                                 float* __restrict__ Ac, float* __restrict__ Alo) {
+  extern __shared__ __align__(16) float b16[];
+  float* As = b16;                  // [32][BG_AST]: As[m][k] = A[m0 + m][k]
+  float* Bs = b16 + 32 * BG_AST;    // [K][BG_BST]:  Bs[k][n] = B[k][n0 + n]
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+  const int K4 = K / 4;
+  for (int e = tid; e < 32 * K4; e += 256) {
+    const int m = e / K4, k4 = e - m * K4;
+    float* dst = As + m * BG_AST + 4 * k4;
+    if (m0 + m < M)
+      ch_acopy16(dst, A + (size_t)(m0 + m) * K + 4 * k4);
+    else
+      *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int e = tid; e < K * 8; e += 256) {
+    const int k = e >> 3, n4 = e & 7;
+    float* dst = Bs + k * BG_BST + 4 * n4;
+    if (n0 + 4 * n4 + 3 < N)
+      ch_acopy16(dst, B + (size_t)k * N + n0 + 4 * n4);
+    else
+      for (int u = 0; u < 4; ++u) dst[u] = n0 + 4 * n4 + u < N ? B[(size_t)k * N + n0 + 4 * n4 + u] : 0.0f;
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const float* a0p = As + ty * BG_AST;
+  const float* a1p = As + (ty + 16) * BG_AST;
+#pragma unroll 8
+  for (int k = 0; k < K; ++k) {
+    const float a0 = a0p[k], a1 = a1p[k];
+    const float b0 = Bs[k * BG_BST + tx], b1 = Bs[k * BG_BST + tx + 16];
+    acc[0][0] = fmaf(a0, b0, acc[0][0]);
+    acc[0][1] = fmaf(a0, b1, acc[0][1]);
+    acc[1][0] = fmaf(a1, b0, acc[1][0]);
+    acc[1][1] = fmaf(a1, b1, acc[1][1]);
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int m = m0 + ty + 16 * a, n = n0 + tx + 16 * b;
+      if (m >= M || n >= N) continue;
+      const size_t o = (size_t)m * N + n;
+      if (MODE == BG_STORE) {
+        out32[o] = acc[a][b];
+      } else {
+        const double v = MODE == BG_SET ? (double)acc[a][b] : A64[o] + (double)acc[a][b];
+        A64[o] = v;
+        const float hi = (float)v;
+        Ac[o] = hi;
+        Alo[o] = (float)(v - (double)hi);
+      }
+    }
+}
+
 // H = A^T A for A (I x s, row-major FP32): the factor Gram H_t = A_(t)^T A_(t)
 // of the Gram chains.  One 32 x 32 tile of H per CTA for tiles (ta <= tb)
 // only, each written to both triangles; K = I in chunks of 64 as in k_bgemm.
@@ -550,6 +620,52 @@ __global__ void __launch_bounds__(256) k_gram_at(const float* __restrict__ A, in
       acc[1][0] = fmaf(x1, y0, acc[1][0]);
       acc[1][1] = fmaf(x1, y1, acc[1][1]);
     }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
+      if (a >= s || b >= s) continue;
+      H[(size_t)a * s + b] = acc[u][v];
+      H[(size_t)b * s + a] = acc[u][v];
+    }
+}
+
+// k_gram_at with all of K = I (<= BG_KS16) staged at once by 16-byte
+// asynchronous copies (s % 4 == 0): tile columns a0.., b0.. of every row.
+__global__ void __launch_bounds__(256) k_gram_at16(const float* __restrict__ A, int I, int s, float* __restrict__ H) {
+  extern __shared__ __align__(16) float g16[];
+  float* As = g16;                 // [I][BG_BST]: As[k][c] = A[k][a0 + c]
+  float* Bs = g16 + BG_KS16 * BG_BST;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int nt = (s + 31) / 32;
+  int t = blockIdx.x, ta = 0;
+  while (t >= nt - ta) {
+    t -= nt - ta;
+    ++ta;
+  }
+  const int a0 = 32 * ta, b0 = 32 * (ta + t);
+  for (int e = tid; e < I * 16; e += 256) {
+    const int k = e >> 4, h = (e >> 3) & 1, c4 = e & 7;  // h: 0 the a-tile, 1 the b-tile
+    const int col0 = (h ? b0 : a0) + 4 * c4;
+    float* dst = (h ? Bs : As) + k * BG_BST + 4 * c4;
+    if (col0 + 3 < s)
+      ch_acopy16(dst, A + (size_t)k * s + col0);
+    else
+      for (int u = 0; u < 4; ++u) dst[u] = col0 + u < s ? A[(size_t)k * s + col0 + u] : 0.0f;
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+  for (int k = 0; k < I; ++k) {
+    const float x0 = As[k * BG_BST + ty], x1 = As[k * BG_BST + ty + 16];
+    const float y0 = Bs[k * BG_BST + tx], y1 = Bs[k * BG_BST + tx + 16];
+    acc[0][0] = fmaf(x0, y0, acc[0][0]);
+    acc[0][1] = fmaf(x0, y1, acc[0][1]);
+    acc[1][0] = fmaf(x1, y0, acc[1][0]);
+    acc[1][1] = fmaf(x1, y1, acc[1][1]);
   }
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -671,6 +787,24 @@ void launch_chol_subst(const float* Rt, int I, int s, const float* L, const floa
 void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, float* out32, double* A64, float* Ac,
                        float* Alo, cudaStream_t st) {
   dim3 grid((unsigned)((s + 31) / 32), (unsigned)((I + 31) / 32));
+  const bool v16 = I % 4 == 0 && s % 4 == 0 && I <= BG_KS16 && ((uintptr_t)Qm & 15) == 0 && ((uintptr_t)B & 15) == 0;
+  if (v16) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_bgemm16<BG_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bg16_smem_bytes());
+      cudaFuncSetAttribute(k_bgemm16<BG_SET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bg16_smem_bytes());
+      cudaFuncSetAttribute(k_bgemm16<BG_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bg16_smem_bytes());
+      attr = true;
+    }
+    const size_t sm = bg16_smem_bytes();
+    if (mode == BG_STORE)
+      k_bgemm16<BG_STORE><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    else if (mode == BG_SET)
+      k_bgemm16<BG_SET><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    else
+      k_bgemm16<BG_ADD><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    return;
+  }
   if (mode == BG_STORE)
     k_bgemm<BG_STORE><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
   else if (mode == BG_SET)
@@ -681,6 +815,16 @@ void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, 
 
 void launch_gram_at(const float* A, int I, int s, float* H, cudaStream_t st) {
   const int nt = (s + 31) / 32;
+  if (s % 4 == 0 && I <= BG_KS16 && ((uintptr_t)A & 15) == 0) {
+    static bool attr = false;
+    const size_t sm = (size_t)2 * BG_KS16 * BG_BST * 4;
+    if (!attr) {
+      cudaFuncSetAttribute(k_gram_at16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    k_gram_at16<<<nt * (nt + 1) / 2, 256, sm, st>>>(A, I, s, H);
+    return;
+  }
   k_gram_at<<<nt * (nt + 1) / 2, 256, 0, st>>>(A, I, s, H);
 }
 
