@@ -77,7 +77,10 @@ CLASS_KERNEL = {
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
 # current kernel on this workload (profiles/); absent when not captured since
 # the kernel last changed.
-TRAFFIC = {}
+TRAFFIC = {
+    ("c4", "tf32", "eig"): (0.22e6, "dram__bytes_read.sum + dram__bytes_write.sum of one k_chol_factor launch (129 CTAs), "
+                                    "ncu --set full on the 256x256x31x8 TF32 sweep (profiles/chol_solve_256x256x31x8_tf32.md)"),
+}
 
 
 def dist_env():
