@@ -1389,8 +1389,8 @@ int copy_out(fctn_handle* h, void* dst, const void* src, size_t bytes, int where
 }
 
 
-// The trace terms of Eq. 2 for every factor (one launch).
-void launch_traces(fctn_handle* h) {
+// The trace terms of Eq. 2 for every factor (one launch on stream st).
+void launch_traces(fctn_handle* h, cudaStream_t st) {
   const double sgn = h->p.laplacian_sign == FCTN_LAPLACIAN_PRINTED ? -1.0 : 1.0;
   TraceArgs a{};
   for (int k = 0; k < h->N; ++k) {
@@ -1401,7 +1401,7 @@ void launch_traces(fctn_handle* h) {
     a.c1[k] = -sgn;
     a.lam[k] = h->p.lambda[k];
   }
-  launch_trace_all(a, h->N, h->traces, h->st);
+  launch_trace_all(a, h->N, h->traces, st);
 }
 
 // Rotation threshold of the FP32 Gram eigensolver: the caller's, else one
@@ -1850,6 +1850,16 @@ int route_sweep(fctn_handle* h) {
       h->launches += sg_launches(r.z) - 1;
     }
   }
+  // the trace terms of Eq. 2 need only the new factors: on the side stream,
+  // beside M_0 and the X update
+  if (fork) {
+    if (!h->dry) {
+      CK(cudaEventRecord(h->ev_fork, h->st));
+      CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    }
+    LAUNCH_ON(1, launch_traces(h, h->side));
+    if (!h->dry) CK(cudaEventRecord(h->ev_join, h->side));
+  }
   // M_0 of the new factors 1 .. N-1, then Eq. 10 with F = A_(0) M_0
   if ((rc = route_build_m0(h))) return rc;
   GramPlan g = gram_plan(h, 0);
@@ -1878,7 +1888,11 @@ int route_sweep(fctn_handle* h) {
            launch_xupdate_f32((const float*)h->Ac[0], r.M0, (float*)h->X, h->bits, rho, g, h->red, h->st));
     r.xt_valid = false;  // X moved without its transposed copy
   }
-  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h));
+  if (fork) {
+    if (!h->dry) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+  } else {
+    LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h, h->st));
+  }
   LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, nred, h->traces, h->N, h->stats, h->st));
   h->t++;
   return FCTN_OK;
@@ -1938,7 +1952,7 @@ int sweep_body(fctn_handle* h) {
              launch_xupdate_fused_f32(h->pp[last], (const float*)L, (const float*)R, (const float*)h->Ac[last],
                                       (float*)h->X, h->bits, h->p.rho, g, h->red, h->st));
   }
-  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h));
+  LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_traces(h, h->st));
   LAUNCH(FCTN_KC_MISC, 0.0, 0.0, launch_finalize(h->red, xupdate_blocks(g), h->traces, h->N, h->stats, h->st));
   h->t++;
   return FCTN_OK;
