@@ -148,8 +148,10 @@ typedef struct fctn_params {
                              BF16 too; bits 1-2: pipeline stages of X_(1) M_1^T (rule,
                              2, 4, 6); bits 3-4: its K split over about (304, 152, 608,
                              76) CTAs; bits 5-6: K split of the CUDA-core contractions
-                             over about (304, 152, 608, 1) CTAs.  Only the summation
-                             order of the contractions changes with it                  */
+                             over about (304, 152, 608, 1) CTAs; bit 7: programmatic
+                             dependent launches in the chain of the Cholesky solve.
+                             Only the summation order of the contractions changes
+                             with it                                                    */
   int32_t solve_method;   /* FCTN_SOLVE_*: the solve of Eq. 5 (see above)               */
 } fctn_params;
 
@@ -251,10 +253,12 @@ int fctn_autotune(const fctn_params* p, const void* Y, const uint8_t* mask, cons
 
 /* The autotuner of the head-mode route: times `sweeps` sweeps (after twice as
  * many untimed ones) of a probe handle per tile code in cand[0..ncand) (NULL:
- * the built-in list {0, 1, 2, 4, 8, 16, 32, 64, 96}, one choice changed per
- * candidate) on the caller's inputs, and returns the fastest in *best and,
+ * the built-in list {0, 1, 2, 4, 8, 16, 32, 64, 96, 128, 136, 160}, one
+ * choice changed per candidate, and bit 7 alone and with the two 152-CTA K
+ * splits; ncand is then ignored and ms_out needs 12 entries) on the caller's
+ * inputs, and returns the fastest in *best and,
  * if ms_out is not NULL, each candidate's ms per sweep.  Errors as
- * fctn_autotune; a candidate outside [0, 127] is FCTN_E_ARG. */
+ * fctn_autotune; a candidate outside [0, 255] is FCTN_E_ARG. */
 int fctn_autotune_tiles(const fctn_params* p, const void* Y, const uint8_t* mask, const void* const* factors,
                         int where, const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best,
                         double* ms_out);

@@ -743,7 +743,7 @@ int check_params(const fctn_params* p) {
     return fail(FCTN_E_ARG, "eig_max_sweeps %d outside [0, 1000]", p->eig_max_sweeps);
   if (!(p->eig_tol >= 0.0 && p->eig_tol < 1.0)) return fail(FCTN_E_ARG, "eig_tol must lie in [0, 1)");
   if (!(p->finish_fp32_at >= 0.0)) return fail(FCTN_E_ARG, "finish_fp32_at must be >= 0");
-  if (p->tile_code < 0 || p->tile_code > 127) return fail(FCTN_E_ARG, "tile_code %d outside [0, 127]", p->tile_code);
+  if (p->tile_code < 0 || p->tile_code > 255) return fail(FCTN_E_ARG, "tile_code %d outside [0, 255]", p->tile_code);
   if (p->solve_method < FCTN_SOLVE_AUTO || p->solve_method > FCTN_SOLVE_CHOL)
     return fail(FCTN_E_ARG, "unknown solve method %d", p->solve_method);
   if (!(p->rho > 0)) return fail(FCTN_E_ARG, "rho must be > 0");
@@ -1443,6 +1443,9 @@ int chol_solve(fctn_handle* h, int k, bool rt_done = false) {
   float* W = (float*)h->Z;
   float* Ac = (float*)h->Ac[k];
   const double ge = 2.0 * (double)I * I * s, sub = 2.0 * (double)I * s * s;
+  // the solve's chain runs after the join with the factorization branch, so
+  // its kernels may launch programmatically (nothing else needs the SMs)
+  PdlScope pdl(h->hr.on && (h->p.tile_code & 128));
   if (!rt_done)  // Q^T Y (the head route forms it before joining the factorization branch)
     LAUNCH(FCTN_KC_SOLVE, 0.0, ge,
            launch_basis_gemm(0, h->QT32[k], (const float*)h->Ys, I, s, h->cholRt, nullptr, nullptr, nullptr, h->st));
@@ -2517,17 +2520,18 @@ int fctn_autotune_tiles(const fctn_params* p, const void* Y, const uint8_t* mask
                         double* ms_out) {
   // the built-in rule; CUDA-core products; 2 / 4 pipeline stages; K split of
   // X_(1) M_1^T over 152 / 608 CTAs; K split of the CUDA-core contractions
-  // over 152 / 608 CTAs / none
-  static const int32_t builtin[9] = {0, 1, 2, 4, 8, 16, 32, 64, 96};
+  // over 152 / 608 CTAs / none; programmatic dependent launches in the solve
+  // chain, alone and with the two K splits over 152 CTAs
+  static const int32_t builtin[12] = {0, 1, 2, 4, 8, 16, 32, 64, 96, 128, 136, 160};
   if (!p || !Y || !mask || !factors || !best) return fail(FCTN_E_ARG, "NULL argument");
   if (sweeps < 1 || sweeps > 1000) return fail(FCTN_E_ARG, "sweeps %d outside [1, 1000]", sweeps);
   if (!cand) {
     cand = builtin;
-    ncand = 9;
+    ncand = 12;
   }
   if (ncand < 1 || ncand > 64) return fail(FCTN_E_ARG, "ncand %d outside [1, 64]", ncand);
   for (int i = 0; i < ncand; ++i)
-    if (cand[i] < 0 || cand[i] > 127) return fail(FCTN_E_ARG, "candidate %d outside [0, 127]", cand[i]);
+    if (cand[i] < 0 || cand[i] > 255) return fail(FCTN_E_ARG, "candidate %d outside [0, 255]", cand[i]);
   int rc = check_params(p);
   if (rc) return rc;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -14,6 +14,42 @@
 #define FCTN_MAXC 8   // digits of its contracted index
 #define FCTN_CON_TABLE 4096  // contracted-index offsets kept in shared memory
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may
+// become resident while its predecessor in the stream is still running: it
+// first lets its own successor launch, then waits for the predecessor's
+// completion (and memory) before it touches any data, so stream order is
+// kept while the launch latency overlaps the predecessor's tail.
+__device__ __forceinline__ void pdl_prologue() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+#endif
+}
+// Whether launch_pdl sets the programmatic attribute (per host thread): on
+// only around chains that no concurrent branch needs SMs for, since a kernel
+// resident early holds its SM resources while it waits.
+extern thread_local bool g_pdl;
+struct PdlScope {
+  bool prev;
+  explicit PdlScope(bool on) : prev(g_pdl) { g_pdl = on; }
+  ~PdlScope() { g_pdl = prev; }
+};
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Sum over z = 0 .. n - 1 of part[z * MN + e] in split order with Neumaier's
 // compensation (about twice the FP32 precision; FP64 adds run at 1/64 of the
 // FP32 rate), eight loads in flight: the fixed-order reduce of K-split partials.

@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
                                                        double c0, double c1, double rho, float* __restrict__ Lout,
                                                        float* __restrict__ Dout, int* status,
                                                        const __grid_constant__ ChMaps maps) {
+  pdl_prologue();
   // TMA boxes need a 128-byte aligned destination: checked below, the
   // scalar path is taken otherwise
   extern __shared__ __align__(128) float P[];
@@ -320,6 +321,7 @@ __host__ __device__ inline size_t ch_subst_bytes(int s) {
 __global__ void __launch_bounds__(CH_NT) k_chol_subst(const float* __restrict__ Rt, int I, int s,
                                                       const float* __restrict__ Lp, const float* __restrict__ Dinv,
                                                       float* __restrict__ W, int* status) {
+  pdl_prologue();
   extern __shared__ __align__(16) float smf[];
   __shared__ __align__(8) uint64_t bar;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -438,6 +440,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_bgemm(const float* __restrict__ A, const float* __restrict__ B, int M, int N,
                                                int K, float* __restrict__ out32, double* __restrict__ A64,
                                                float* __restrict__ Ac, float* __restrict__ Alo) {
+  pdl_prologue();
   __shared__ float As[32][BG_KC + 1];
   __shared__ float Bs[BG_KC][33];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -520,6 +523,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_bgemm16(const float* __restrict__ A, const float* __restrict__ B, int M,
                                                  int N, int K, float* __restrict__ out32, double* __restrict__ A64,
                                                  float* __restrict__ Ac, float* __restrict__ Alo) {
+  pdl_prologue();
   extern __shared__ __align__(16) float b16[];
   float* As = b16;                  // [32][BG_AST]: As[m][k] = A[m0 + m][k]
   float* Bs = b16 + 32 * BG_AST;    // [K][BG_BST]:  Bs[k][n] = B[k][n0 + n]
@@ -579,6 +583,7 @@ __global__ void __launch_bounds__(256) k_bgemm16(const float* __restrict__ A, co
 // of the Gram chains.  One 32 x 32 tile of H per CTA for tiles (ta <= tb)
 // only, each written to both triangles; K = I in chunks of 64 as in k_bgemm.
 __global__ void __launch_bounds__(256) k_gram_at(const float* __restrict__ A, int I, int s, float* __restrict__ H) {
+  pdl_prologue();
   __shared__ float As[BG_KC][33];
   __shared__ float Bs[BG_KC][33];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -635,6 +640,7 @@ __global__ void __launch_bounds__(256) k_gram_at(const float* __restrict__ A, in
 // k_gram_at with all of K = I (<= BG_KS16) staged at once by 16-byte
 // asynchronous copies (s % 4 == 0): tile columns a0.., b0.. of every row.
 __global__ void __launch_bounds__(256) k_gram_at16(const float* __restrict__ A, int I, int s, float* __restrict__ H) {
+  pdl_prologue();
   extern __shared__ __align__(16) float g16[];
   float* As = g16;                 // [I][BG_BST]: As[k][c] = A[k][a0 + c]
   float* Bs = g16 + BG_KS16 * BG_BST;
@@ -692,6 +698,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const double* __restrict__ Yd,
                                                   const float* __restrict__ Ac, const float* __restrict__ Alo,
                                                   const float* __restrict__ G, int I, int s, double lam, double rho,
                                                   double c0, double c1, float* __restrict__ R) {
+  pdl_prologue();
   extern __shared__ __align__(16) float rsm[];
   float* Ah = rsm;                    // [RD_ROWS][s]
   float* Al = Ah + RD_ROWS * s;       // [RD_ROWS][s]
@@ -771,7 +778,7 @@ void launch_chol_factor(const float* G, int I, int s, double lam, double c0, dou
   const int np = ch_npan(s), sp = 32 * np;
   for (int q = 0; q < np && maps.on; ++q)
     if (tma_map_f32(&maps.m[q], G, s, s, s, sp - 32 * q, 32) != FCTN_OK) maps.on = 0;
-  k_chol_factor<<<chol_groups(I), CH_NT, bytes, st>>>(G, s, I, lam, c0, c1, rho, L, Dinv, status, maps);
+  launch_pdl(k_chol_factor, chol_groups(I), dim3(CH_NT), bytes, st, G, s, I, lam, c0, c1, rho, L, Dinv, status, maps);
 }
 
 void launch_chol_subst(const float* Rt, int I, int s, const float* L, const float* Dinv, float* W, int* status,
@@ -781,7 +788,7 @@ void launch_chol_subst(const float* Rt, int I, int s, const float* L, const floa
     cudaFuncSetAttribute(k_chol_subst, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_chol_subst<<<chol_groups(I), CH_NT, ch_subst_bytes(s), st>>>(Rt, I, s, L, Dinv, W, status);
+  launch_pdl(k_chol_subst, chol_groups(I), dim3(CH_NT), ch_subst_bytes(s), st, Rt, I, s, L, Dinv, W, status);
 }
 
 void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, float* out32, double* A64, float* Ac,
@@ -798,19 +805,19 @@ void launch_basis_gemm(int mode, const float* Qm, const float* B, int I, int s, 
     }
     const size_t sm = bg16_smem_bytes();
     if (mode == BG_STORE)
-      k_bgemm16<BG_STORE><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+      launch_pdl(k_bgemm16<BG_STORE>, grid, dim3(256), sm, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
     else if (mode == BG_SET)
-      k_bgemm16<BG_SET><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+      launch_pdl(k_bgemm16<BG_SET>, grid, dim3(256), sm, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
     else
-      k_bgemm16<BG_ADD><<<grid, 256, sm, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+      launch_pdl(k_bgemm16<BG_ADD>, grid, dim3(256), sm, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
     return;
   }
   if (mode == BG_STORE)
-    k_bgemm<BG_STORE><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    launch_pdl(k_bgemm<BG_STORE>, grid, dim3(256), 0, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
   else if (mode == BG_SET)
-    k_bgemm<BG_SET><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    launch_pdl(k_bgemm<BG_SET>, grid, dim3(256), 0, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
   else
-    k_bgemm<BG_ADD><<<grid, 256, 0, st>>>(Qm, B, I, s, I, out32, A64, Ac, Alo);
+    launch_pdl(k_bgemm<BG_ADD>, grid, dim3(256), 0, st, Qm, B, I, s, I, out32, A64, Ac, Alo);
 }
 
 void launch_gram_at(const float* A, int I, int s, float* H, cudaStream_t st) {
@@ -822,10 +829,10 @@ void launch_gram_at(const float* A, int I, int s, float* H, cudaStream_t st) {
       cudaFuncSetAttribute(k_gram_at16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       attr = true;
     }
-    k_gram_at16<<<nt * (nt + 1) / 2, 256, sm, st>>>(A, I, s, H);
+    launch_pdl(k_gram_at16, nt * (nt + 1) / 2, dim3(256), sm, st, A, I, s, H);
     return;
   }
-  k_gram_at<<<nt * (nt + 1) / 2, 256, 0, st>>>(A, I, s, H);
+  launch_pdl(k_gram_at, nt * (nt + 1) / 2, dim3(256), 0, st, A, I, s, H);
 }
 
 void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const float* Alo, const float* G, int I,
@@ -837,5 +844,5 @@ void launch_resid_df(const double* Yd, const double* A64, const float* Ac, const
   }
   const size_t bytes = ((size_t)2 * RD_ROWS * s + (size_t)s * 33) * 4;
   dim3 grid((unsigned)((s + 31) / 32), (unsigned)((I + RD_ROWS - 1) / RD_ROWS));
-  k_resid_df<<<grid, 256, bytes, st>>>(Yd, A64, Ac, Alo, G, I, s, lam, rho, c0, c1, R);
+  launch_pdl(k_resid_df, grid, dim3(256), bytes, st, Yd, A64, Ac, Alo, G, I, s, lam, rho, c0, c1, R);
 }

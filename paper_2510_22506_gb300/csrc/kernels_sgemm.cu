@@ -15,6 +15,8 @@
 
 #include "fctn_internal.cuh"
 
+thread_local bool g_pdl = false;  // see launch_pdl
+
 namespace {
 
 constexpr int SG_BM = 128, SG_BN = 64, SG_BK = 16, SG_THREADS = 256;
@@ -38,6 +40,7 @@ constexpr int SG_ST = 3;  // pipeline stages of the operand tiles
 __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, const float* __restrict__ A,
                                                       const float* __restrict__ B, float* __restrict__ C,
                                                       float* __restrict__ part) {
+  pdl_prologue();
   __shared__ __align__(16) float As[SG_ST][SG_BK][SG_BM + 4];
   __shared__ __align__(16) float Bs[SG_ST][SG_BK][SG_BN + 4];
   __shared__ int am_s[SG_BM], bn_s[SG_BN];
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(SG_THREADS) k_sgemm(SgShape sh, SgTabs t, cons
 
 // C[cm[m] + cn[n]] = sum over the K split (in split order, compensated) of the partials.
 __global__ void k_sg_reduce(SgShape sh, SgTabs t, const float* __restrict__ part, float* __restrict__ C) {
+  pdl_prologue();
   const int64_t MN = (int64_t)sh.M * sh.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
     const float s = split_sum(part, sh.ksplit, MN, e);
@@ -180,6 +184,7 @@ __global__ void k_sg_reduce(SgShape sh, SgTabs t, const float* __restrict__ part
 // Yd = Yraw + rho * A_old (Eq. 5 right-hand side), Ys = float(Yd); n = I s.
 __global__ void k_finish_rhs(const float* __restrict__ Yraw, const double* __restrict__ Aold, double rho,
                              double* __restrict__ Yd, float* __restrict__ Ys, int64_t n) {
+  pdl_prologue();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const double y = (double)Yraw[e] + rho * Aold[e];
     Yd[e] = y;
@@ -190,6 +195,7 @@ __global__ void k_finish_rhs(const float* __restrict__ Yraw, const double* __res
 // Gd = double(Gs), symmetrised ((G + G^T) / 2 in FP32 first, so that Gs and
 // Gd hold the same symmetric matrix); s x s.
 __global__ void k_finish_gram(float* __restrict__ Gs, double* __restrict__ Gd, int s) {
+  pdl_prologue();
   const int64_t n = (int64_t)s * s;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / s), j = (int)(e - (int64_t)i * s);
@@ -207,6 +213,7 @@ __global__ void k_finish_gram(float* __restrict__ Gs, double* __restrict__ Gd, i
 // Rounding: 0 = none, 1 = to nearest TF32 (kept in FP32 storage).
 __global__ void k_transpose_round(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                                   float* __restrict__ dst, int64_t ldd, int round) {
+  pdl_prologue();
   __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -231,6 +238,7 @@ __global__ void k_transpose_round(const float* __restrict__ src, int64_t rows, i
 // dst[r * ldd + c] = round(src[r * lds + c]) (a padded, optionally rounded copy).
 __global__ void k_copy_round(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                              float* __restrict__ dst, int64_t ldd, int round) {
+  pdl_prologue();
   const int64_t n = rows * ldd;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / ldd, c = e - r * ldd;
@@ -247,6 +255,7 @@ __global__ void k_copy_round(const float* __restrict__ src, int64_t rows, int64_
 // BF16 copies of the same two kinds (operands of the BF16 tensor-core GEMMs).
 __global__ void k_transpose_bf16(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                                  __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  pdl_prologue();
   __shared__ float tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -262,6 +271,7 @@ __global__ void k_transpose_bf16(const float* __restrict__ src, int64_t rows, in
 
 __global__ void k_copy_bf16(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                             __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  pdl_prologue();
   const int64_t n = rows * ldd;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / ldd, c = e - r * ldd;
@@ -305,40 +315,40 @@ void launch_sgemm(const SgShape& sh, const SgTabs& t, const float* A, const floa
                   cudaStream_t st) {
   if (sh.M <= 0 || sh.N <= 0) return;
   dim3 grid((sh.M + SG_BM - 1) / SG_BM, (sh.N + SG_BN - 1) / SG_BN, sh.ksplit);
-  k_sgemm<<<grid, SG_THREADS, 0, st>>>(sh, t, A, B, C, part);
+  launch_pdl(k_sgemm, grid, dim3(SG_THREADS), 0, st, sh, t, A, B, C, part);
   if (sh.ksplit > 1) {
     const int64_t mn = (int64_t)sh.M * sh.N;
-    k_sg_reduce<<<grid_for(mn, 256), 256, 0, st>>>(sh, t, part, C);
+    launch_pdl(k_sg_reduce, grid_for(mn, 256), dim3(256), 0, st, sh, t, part, C);
   }
 }
 
 void launch_finish_rhs(const float* Yraw, const double* Aold, double rho, double* Yd, float* Ys, int64_t n,
                        cudaStream_t st) {
-  k_finish_rhs<<<grid_for(n, 256), 256, 0, st>>>(Yraw, Aold, rho, Yd, Ys, n);
+  launch_pdl(k_finish_rhs, grid_for(n, 256), dim3(256), 0, st, Yraw, Aold, rho, Yd, Ys, n);
 }
 
 void launch_finish_gram(float* Gs, double* Gd, int s, cudaStream_t st) {
-  k_finish_gram<<<grid_for((int64_t)s * s, 256), 256, 0, st>>>(Gs, Gd, s);
+  launch_pdl(k_finish_gram, grid_for((int64_t)s * s, 256), dim3(256), 0, st, Gs, Gd, s);
 }
 
 void launch_transpose_f32(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
                           int round_tf32, cudaStream_t st) {
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  k_transpose_round<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd, round_tf32);
+  launch_pdl(k_transpose_round, grid, dim3(32, 8), 0, st, src, rows, cols, lds, dst, ldd, round_tf32);
 }
 
 void launch_copy_f32(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
                      int round_tf32, cudaStream_t st) {
-  k_copy_round<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, dst, ldd, round_tf32);
+  launch_pdl(k_copy_round, grid_for(rows * ldd, 256), dim3(256), 0, st, src, rows, cols, lds, dst, ldd, round_tf32);
 }
 
 void launch_transpose_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst,
                            int64_t ldd, cudaStream_t st) {
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd);
+  launch_pdl(k_transpose_bf16, grid, dim3(32, 8), 0, st, src, rows, cols, lds, dst, ldd);
 }
 
 void launch_copy_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, __nv_bfloat16* dst, int64_t ldd,
                       cudaStream_t st) {
-  k_copy_bf16<<<grid_for(rows * ldd, 256), 256, 0, st>>>(src, rows, cols, lds, dst, ldd);
+  launch_pdl(k_copy_bf16, grid_for(rows * ldd, 256), dim3(256), 0, st, src, rows, cols, lds, dst, ldd);
 }

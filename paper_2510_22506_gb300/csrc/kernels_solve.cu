@@ -1684,6 +1684,7 @@ constexpr int TRACE_BLOCKS = 32;
 // The trace terms of every factor in one launch: block (b, k) sums rows
 // b, b + TRACE_BLOCKS, ... of factor k (threads over the columns).
 __global__ void k_trace_all(TraceArgs a, double* __restrict__ out) {
+  pdl_prologue();
   __shared__ double red[32];
   const int k = blockIdx.y;
   const double* A = a.A[k];
@@ -1708,6 +1709,7 @@ __global__ void k_trace_all(TraceArgs a, double* __restrict__ out) {
 
 __global__ void k_finalize(const double* __restrict__ red, int nblocks, const double* __restrict__ traces, int N,
                            double* __restrict__ stats) {
+  pdl_prologue();
   __shared__ double sh[3][256];
   double v[3] = {0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -1786,10 +1788,10 @@ void launch_resid_f64(const double* Y, const double* A, const double* G, int I, 
   k_resid<double><<<I, 128, 0, st>>>(Y, A, G, I, s, lam, rho, c0, c1, R);
 }
 void launch_trace_all(const TraceArgs& a, int N, double* out, cudaStream_t st) {
-  k_trace_all<<<dim3(TRACE_BLOCKS, (unsigned)N), 256, 0, st>>>(a, out);
+  launch_pdl(k_trace_all, dim3(TRACE_BLOCKS, (unsigned)N), dim3(256), 0, st, a, out);
 }
 void launch_finalize(const double* red, int nblocks, const double* traces, int N, double* stats, cudaStream_t st) {
-  k_finalize<<<1, 256, 0, st>>>(red, nblocks, traces, N, stats);
+  launch_pdl(k_finalize, dim3(1), dim3(256), 0, st, red, nblocks, traces, N, stats);
 }
 
 void launch_extrap_f32(double* A, const double* Aold, double alpha, double beta, float* Ac, int64_t n,

@@ -117,6 +117,7 @@ namespace {
 template <class Op>
 __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB, TgArgs a) {
+  pdl_prologue();
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   constexpr int MAXS = 8;
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
 // Sum of the K-split partials of a TG_PARTIAL launch (split order, compensated):
 // out[row * N + col] = sum_z part[z][row][col].
 __global__ void k_tg_reduce(const float* __restrict__ part, int ksplit, int64_t MN, float* __restrict__ out) {
+  pdl_prologue();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
     out[e] = split_sum(part, ksplit, MN, e);
   }
@@ -425,17 +427,17 @@ void launch_tg_gemm(const void* mapA, const void* mapB, const TgArgs& a, int bf1
       cudaFuncSetAttribute(k_tg_gemm<TgBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
       attr[1] = true;
     }
-    k_tg_gemm<TgBF16><<<grid, TG_THREADS, smem, st>>>(*(const CUtensorMap*)mapA, *(const CUtensorMap*)mapB, a);
+    launch_pdl(k_tg_gemm<TgBF16>, grid, dim3(TG_THREADS), smem, st, *(const CUtensorMap*)mapA, *(const CUtensorMap*)mapB, a);
   } else {
     if (!attr[0]) {
       cudaFuncSetAttribute(k_tg_gemm<TgTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 202 * 1024);
       attr[0] = true;
     }
-    k_tg_gemm<TgTF32><<<grid, TG_THREADS, smem, st>>>(*(const CUtensorMap*)mapA, *(const CUtensorMap*)mapB, a);
+    launch_pdl(k_tg_gemm<TgTF32>, grid, dim3(TG_THREADS), smem, st, *(const CUtensorMap*)mapA, *(const CUtensorMap*)mapB, a);
   }
 }
 
 void launch_tg_reduce(const float* part, int ksplit, int64_t MN, float* out, cudaStream_t st) {
   int64_t b = (MN + 255) / 256;
-  k_tg_reduce<<<(unsigned)(b < 608 ? (b < 1 ? 1 : b) : 608), 256, 0, st>>>(part, ksplit, MN, out);
+  launch_pdl(k_tg_reduce, dim3((unsigned)(b < 608 ? (b < 1 ? 1 : b) : 608)), dim3(256), 0, st, part, ksplit, MN, out);
 }

@@ -334,7 +334,7 @@ def fctn_autotune(params, Y, mask, factors, candidates=None, sweeps=3, stream=No
     return best.value, {c: ms[i] for i, c in enumerate(cand)}
 
 
-TILE_CANDIDATES = (0, 1, 2, 4, 8, 16, 32, 64, 96)
+TILE_CANDIDATES = (0, 1, 2, 4, 8, 16, 32, 64, 96, 128, 136, 160)
 
 
 def fctn_autotune_tiles(params, Y, mask, factors, candidates=None, sweeps=3, stream=None):

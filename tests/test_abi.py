@@ -64,7 +64,7 @@ def test_footprint_scales_with_size(F):
     dict(rhs_ctas=-1),
     dict(rhs_ctas=5000),
     dict(tile_code=-1),
-    dict(tile_code=128),
+    dict(tile_code=256),
     dict(eig_tol=1.5),
     dict(finish_fp32_at=-1.0),
     dict(solve_method=3),

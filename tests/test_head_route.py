@@ -145,7 +145,7 @@ def tile_case():
     return d, st
 
 
-@pytest.mark.parametrize("code", [0, 1, 2, 4, 6, 8, 16, 24, 32, 64, 96])
+@pytest.mark.parametrize("code", [0, 1, 2, 4, 6, 8, 16, 24, 32, 64, 96, 128, 136, 160])
 @pytest.mark.parametrize("precision", ["fp32", "tf32"])
 def test_tile_codes_keep_parity(F, tile_case, code, precision):
     """Tile codes change only launch shapes and summation orders: FP32 stays
