@@ -76,6 +76,9 @@ struct SgPlanH {
   SgShape sh{};
   size_t tab = 0;
   bool swap = false;
+  bool tcok = false;       // served by the tensor-core contraction while the route's products are TF32
+  bool round_out = false;  // there its output is an operand of the next tensor-core step: rounded to TF32
+  TccShape tcs{};
 };
 
 // Head-mode association of a sweep (order 1, ..., N; head = mode 1, index 0
@@ -1244,6 +1247,28 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
       r.ty.mode = TG_PARTIAL;
       r.tz.mode = TG_STORE;
       r.tf.mode = TG_XUPDATE;
+      // The M_0 chain and the right-hand-side chains from Z on the tensor
+      // cores too (the Gram chains stay FP32: the conditioning of Eq. 5
+      // rests on them).  Their operands arrive rounded to TF32 from their
+      // producers (Z from its GEMM, the chain intermediates from the
+      // previous step) except the factors, which the kernel rounds as it
+      // stages them.
+      auto tcplan = [&](SgPlanH& q, bool a0_factor, bool round_out) {
+        tcc_shape(q.sh, sgs, &q.tcs);
+        q.tcs.round_a = q.swap ? 1 : (a0_factor ? 1 : 0);
+        q.tcs.round_b = q.swap ? (a0_factor ? 1 : 0) : 1;
+        q.tcok = true;
+        q.round_out = round_out;
+        track(&r.part_main, (int64_t)tcc_part_elems(q.tcs));
+      };
+      for (int i = 0; i < r.nm0; ++i) tcplan(r.m0[i], i == 0, i < r.nm0 - 1);
+      for (int k = 1; k < N; ++k)
+        for (int q = 0; q < r.nys[k]; ++q) tcplan(r.ys[k][q], false, q < r.nys[k] - 1);
+      r.tz.round_tf32 = 1;  // Z: an operand of the right-hand-side chains
+      if (r.part_main > cap) {
+        r = HeadRoute{};
+        return FCTN_OK;
+      }
     }
   }
   // table offsets are relative to this plan's block, which starts at tabs->size()
@@ -1623,12 +1648,24 @@ SgTabs sg_tabs(const fctn_handle* h, const SgPlanH& q) {
 }
 
 // C = A (x) B by plan q on stream st (operands passed swapped when the plan says so).
+// The tensor-core contraction serves a plan that has one while the route's
+// products are TF32 / BF16 (not after the switch to FP32 products).
+bool sg_on_tc(const fctn_handle* h, const SgPlanH& q) { return q.tcok && h->hr.tc && !h->hr.fp32_now; }
 void run_sg(const fctn_handle* h, const SgPlanH& q, const float* A, const float* B, float* C, float* part,
             cudaStream_t st) {
+  if (sg_on_tc(h, q)) {
+    TccShape ts = q.tcs;
+    ts.sh.round_tf32 = q.sh.round_tf32 || q.round_out;
+    launch_tcc(ts, sg_tabs(h, q), q.swap ? B : A, q.swap ? A : B, C, part, h->status, st);
+    return;
+  }
   launch_sgemm(q.sh, sg_tabs(h, q), q.swap ? B : A, q.swap ? A : B, C, part, st);
 }
 double sg_flops(const SgPlanH& q) { return 2.0 * (double)q.sh.M * q.sh.N * q.sh.K; }
-int sg_launches(const SgPlanH& q) { return q.sh.ksplit > 1 ? 2 : 1; }
+int sg_launches(const fctn_handle* h, const SgPlanH& q) {
+  if (sg_on_tc(h, q)) return tcc_launches(q.tcs);
+  return q.sh.ksplit > 1 ? 2 : 1;
+}
 
 // M_0 from the present factors 1 .. N-1 (the planned chain order).
 int route_build_m0(fctn_handle* h) {
@@ -1641,7 +1678,7 @@ int route_build_m0(fctn_handle* h) {
     q.sh.round_tf32 = (i == r.nm0 - 1 && tf32_ops) ? 1 : 0;
     LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q),
            run_sg(h, q, cur, (const float*)h->Ac[r.m0fac[i + 1]], o, r.pm, h->st));
-    h->launches += sg_launches(q) - 1;
+    h->launches += sg_launches(h, q) - 1;
     cur = o;
   }
   if (r.tc && !r.fp32_now) {
@@ -1786,10 +1823,10 @@ int route_sweep(fctn_handle* h) {
         float* o = (q == r.nenv[k] - 1) ? (float*)h->Gs : r.E[q % 2];
         const SgPlanH& pl = r.env[k][q];
         if (fork) {
-          LAUNCH_ON(sg_launches(pl), run_sg(h, pl, cur, r.H[ids[q + 1]], o, r.ps, gs));
+          LAUNCH_ON(sg_launches(h, pl), run_sg(h, pl, cur, r.H[ids[q + 1]], o, r.ps, gs));
         } else {
           LAUNCH(FCTN_KC_ENV, 0.0, sg_flops(pl), run_sg(h, pl, cur, r.H[ids[q + 1]], o, r.ps, gs));
-          h->launches += sg_launches(pl) - 1;
+          h->launches += sg_launches(h, pl) - 1;
         }
         cur = o;
       }
@@ -1813,7 +1850,7 @@ int route_sweep(fctn_handle* h) {
              launch_tg_reduce(r.tpart, a.ksplit, (int64_t)h->I[0] * r.s0, r.Yraw, h->st));
     } else if (k == 0) {
       LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.y0), run_sg(h, r.y0, X, r.M0, r.Yraw, r.pm, h->st));
-      h->launches += sg_launches(r.y0) - 1;
+      h->launches += sg_launches(h, r.y0) - 1;
     } else {
       const int q0 = r.yshare[k];
       const float* cur = q0 > 0 ? r.U[(q0 - 1) % 2] : r.Zb;
@@ -1822,7 +1859,7 @@ int route_sweep(fctn_handle* h) {
         const SgPlanH& pl = r.ys[k][q];
         LAUNCH(FCTN_KC_RHS2, 0.0, sg_flops(pl),
                run_sg(h, pl, cur, (const float*)h->Ac[r.yfac[k][q]], o, r.pm, h->st));
-        h->launches += sg_launches(pl) - 1;
+        h->launches += sg_launches(h, pl) - 1;
         cur = o;
       }
     }
@@ -1850,7 +1887,7 @@ int route_sweep(fctn_handle* h) {
     } else if (k == 0) {  // Z = X_(0)^T A_(0) with the new head factor
       LAUNCH(FCTN_KC_GRAM, (double)h->P * 4.0, sg_flops(r.z),
              run_sg(h, r.z, X, (const float*)h->Ac[0], r.Zb, r.pm, h->st));
-      h->launches += sg_launches(r.z) - 1;
+      h->launches += sg_launches(h, r.z) - 1;
     }
   }
   // the trace terms of Eq. 2 need only the new factors: on the side stream,

@@ -202,6 +202,23 @@ void sg_shape(int M, int N, int K, SgShape* sh, int split_ctas = 0);  // split_c
 size_t sg_part_elems(const SgShape& sh);
 void launch_sgemm(const SgShape& sh, const SgTabs& t, const float* A, const float* B, float* C, float* part,
                   cudaStream_t st);
+// C = sum over the K split (in split order) of the partials [z][M][N] of a split contraction.
+void launch_sg_reduce(const SgShape& sh, const SgTabs& t, const float* part, float* C, cudaStream_t st);
+// The same contraction on the tensor cores (TF32, operands gathered through
+// the tables and rounded to nearest TF32): launch shape, partial elements,
+// launches (2 with a K split), launch (A, B, tables as for launch_sgemm).
+struct TccShape {
+  SgShape sh;            // M, N, K, loader directions, rounding of C; K split of this kernel
+  int BN, S;             // columns per CTA (multiple of 16, <= 128), pipeline stages
+  int round_a, round_b;  // operands A, B (as launch_tcc takes them) the kernel rounds to TF32
+                         // (0: already rounded by their producer)
+  int flip;              // sh describes the transposed product C^T = B A^T (the launch swaps the roles)
+};
+void tcc_shape(const SgShape& sg, int split_ctas, TccShape* ts);
+size_t tcc_part_elems(const TccShape& ts);
+int tcc_launches(const TccShape& ts);
+void launch_tcc(const TccShape& ts, const SgTabs& t, const float* A, const float* B, float* C, float* part,
+                int* status, cudaStream_t st);
 // Yd = Yraw + rho A_old, Ys = float(Yd) (n = I s); Gd = double(Gs) after symmetrising Gs.
 void launch_finish_rhs(const float* Yraw, const double* Aold, double rho, double* Yd, float* Ys, int64_t n,
                        cudaStream_t st);
@@ -268,7 +285,7 @@ struct TgArgs {
   int64_t ldt;
   __nv_bfloat16* Xb;
   __nv_bfloat16* XTb;
-  int round_tf32;
+  int round_tf32;  // TG_XUPDATE: XT rounded to TF32; TG_STORE: out rounded to TF32
   double* red;
   int* status;
 };

@@ -322,6 +322,10 @@ void launch_sgemm(const SgShape& sh, const SgTabs& t, const float* A, const floa
   }
 }
 
+void launch_sg_reduce(const SgShape& sh, const SgTabs& t, const float* part, float* C, cudaStream_t st) {
+  launch_pdl(k_sg_reduce, grid_for((int64_t)sh.M * sh.N, 256), dim3(256), 0, st, sh, t, part, C);
+}
+
 void launch_finish_rhs(const float* Yraw, const double* Aold, double rho, double* Yd, float* Ys, int64_t n,
                        cudaStream_t st) {
   launch_pdl(k_finish_rhs, grid_for(n, 256), dim3(256), 0, st, Yraw, Aold, rho, Yd, Ys, n);

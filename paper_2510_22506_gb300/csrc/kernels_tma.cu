@@ -24,7 +24,7 @@
 namespace {
 
 constexpr int TG_THREADS = 192;
-constexpr long long kTgSpin = 1ll << 24;
+constexpr long long kTgSpin = 1ll << 22;  // tries of up to 256 ns each (about 1 s)
 
 __device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -39,9 +39,9 @@ __device__ __forceinline__ bool mb_wait(uint64_t* bar, uint32_t par, volatile in
   for (long long it = 0; it < kTgSpin; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(a), "r"(par)
+        : "r"(a), "r"(par), "r"(256u)
         : "memory");
     if (ok) return true;
     if (abort && *abort) return false;
@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(TG_THREADS) k_tg_gemm(const __grid_constant__ 
                                           : a.out + (int64_t)row * a.ldo + n0 + c0;
           float f[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) f[j] = nk > 0 ? __uint_as_float(v[j]) : 0.f;
+          for (int j = 0; j < 16; ++j) {
+            f[j] = nk > 0 ? __uint_as_float(v[j]) : 0.f;
+            if (a.mode == TG_STORE && a.round_tf32) f[j] = tf32_round(f[j]);
+          }
           if (n0 + c0 + 16 <= a.N && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
             for (int u = 0; u < 4; ++u)
