@@ -188,9 +188,19 @@ def sweep_floor_bytes(dims, R):
     return (len(dims) + 2) * 4.0 * P + P / 8.0
 
 
+# the M_1 chain and the right-hand-side chains run on the tensor cores in the
+# TF32 / BF16 precisions: bound by the gathered operand bytes
+CLASS_KERNEL_TC = {
+    "rhs2": ("k_tcc (right-hand sides 2..N from Z; tcgen05 TF32, operands gathered through offset tables)", "hbm"),
+    "merged": ("k_tcc (M_1 chain; tcgen05 TF32) + operand copies", "hbm"),
+}
+
+
 def class_roofline(cls, prof, peaks, peak_src, precision, svals, eig_sweeps, dims=None):
     """Achieved rate of one kernel class (one kernel per launch) against its roof."""
     kernel, bound = CLASS_KERNEL.get(cls, (cls, "hbm"))
+    if precision in ("tf32", "bf16") and cls in CLASS_KERNEL_TC:
+        kernel, bound = CLASS_KERNEL_TC[cls]
     n = max(prof["launches"], 1)
     avg_s = prof["ms"] / n / 1e3
     if bound == "chol" and eig_sweeps == 0:

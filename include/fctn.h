@@ -66,7 +66,8 @@ enum {
 enum {
   FCTN_FP64 = 0,  /* everything in double: the parity path                             */
   FCTN_FP32 = 1,  /* plain single precision on the CUDA cores                          */
-  FCTN_TF32 = 2,  /* tcgen05 TF32 contractions, FP32 accumulation                      */
+  FCTN_TF32 = 2,  /* tcgen05 TF32 contractions, FP32 accumulation (the factor Grams of
+                     the head-mode route stay FP32 on the CUDA cores)                */
   FCTN_BF16 = 3   /* tcgen05 BF16 contractions, FP32 accumulation.  With the head-mode
                      route (reuse, plain order, N >= 3) the right-hand-side products
                      take BF16 operands and the reconstruction F of Eq. 10 TF32;

@@ -1662,6 +1662,10 @@ void run_sg(const fctn_handle* h, const SgPlanH& q, const float* A, const float*
   launch_sgemm(q.sh, sg_tabs(h, q), q.swap ? B : A, q.swap ? A : B, C, part, st);
 }
 double sg_flops(const SgPlanH& q) { return 2.0 * (double)q.sh.M * q.sh.N * q.sh.K; }
+// algorithmic bytes of a contraction: every operand element read once, C written once (FP32)
+double sg_bytes(const SgPlanH& q) {
+  return 4.0 * ((double)q.sh.M * q.sh.K + (double)q.sh.N * q.sh.K + (double)q.sh.M * q.sh.N);
+}
 int sg_launches(const fctn_handle* h, const SgPlanH& q) {
   if (sg_on_tc(h, q)) return tcc_launches(q.tcs);
   return q.sh.ksplit > 1 ? 2 : 1;
@@ -1676,7 +1680,7 @@ int route_build_m0(fctn_handle* h) {
     float* o = (i == r.nm0 - 1) ? r.M0 : r.U[i % 2];
     SgPlanH q = r.m0[i];
     q.sh.round_tf32 = (i == r.nm0 - 1 && tf32_ops) ? 1 : 0;
-    LAUNCH(FCTN_KC_MERGED, 0.0, sg_flops(q),
+    LAUNCH(FCTN_KC_MERGED, sg_bytes(q), sg_flops(q),
            run_sg(h, q, cur, (const float*)h->Ac[r.m0fac[i + 1]], o, r.pm, h->st));
     h->launches += sg_launches(h, q) - 1;
     cur = o;
@@ -1857,7 +1861,7 @@ int route_sweep(fctn_handle* h) {
       for (int q = q0; q < r.nys[k]; ++q) {
         float* o = (q == r.nys[k] - 1) ? r.Yraw : r.U[q % 2];
         const SgPlanH& pl = r.ys[k][q];
-        LAUNCH(FCTN_KC_RHS2, 0.0, sg_flops(pl),
+        LAUNCH(FCTN_KC_RHS2, sg_bytes(pl), sg_flops(pl),
                run_sg(h, pl, cur, (const float*)h->Ac[r.yfac[k][q]], o, r.pm, h->st));
         h->launches += sg_launches(h, pl) - 1;
         cur = o;
