@@ -65,13 +65,15 @@ __device__ inline int ch_rows(int g, int I, int* r) {
 
 __device__ __forceinline__ unsigned ch_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Bounded wait: tries of up to 256 ns each (the thread sleeps until the
+// phase completes or the time runs out), about 1 s in all.
 __device__ __forceinline__ bool ch_wait(uint64_t* bar, unsigned phase) {
-  for (long long it = 0; it < (1ll << 26); ++it) {
+  for (long long it = 0; it < (1ll << 22); ++it) {
     unsigned r;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(r)
-        : "r"(ch_su32(bar)), "r"(phase));
+        : "r"(ch_su32(bar)), "r"(phase), "r"(256u));
     if (r) return true;
   }
   return false;
@@ -139,6 +141,34 @@ __device__ __noinline__ void ch_factor_diag(float* __restrict__ P, int p, int sp
   for (int c = 0; c < 32; ++c)
     if (c <= lane) Pp[c * nr + lane] = d[c];
   if (!ok && lane == 0) *bad = 1;
+}
+
+// Rows 8 w .. 8 w + 7 of the next diagonal block (block (p + 1, p + 1), all
+// 32 columns) minus their trailing update from panel p: the four warps
+// w = 0..3, one per SM sub-partition, update that block together before
+// warp 0 factors it.
+__device__ __forceinline__ void ch_syrk_diag_rows(float* __restrict__ P, int p, int sp, int w) {
+  const int lane = threadIdx.x & 31;
+  const int nr = sp - 32 * p, nq = nr - 32;
+  const float* Pp = P + ch_poff(p, sp);
+  const int r = 8 * w + (lane & 7), cb = (lane >> 3) * 8;
+  const float* Ap = Pp + 32 + r;
+  const float* Bp = Pp + 32 + cb;
+  float acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+#pragma unroll 8
+  for (int k = 0; k < 32; ++k) {
+    const float a = Ap[k * nr];
+    const float4 b0 = *reinterpret_cast<const float4*>(Bp + k * nr);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bp + k * nr + 4);
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = fmaf(a, bv[j], acc[j]);
+  }
+  float* Cq = P + ch_poff(p + 1, sp) + r;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) Cq[(cb + j) * nq] -= acc[j];
 }
 
 // Trailing-update tile ti of panel p (one warp): block (rb, q), p < q <= rb <
@@ -289,20 +319,24 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
       for (int e = tid * 4; e < 32 * nr; e += CH_NT * 4)
         *reinterpret_cast<float4*>(Lg + e) = *reinterpret_cast<const float4*>(Pp + e);
     }
-    // 3. trailing update with look-ahead: warp 0 updates the next diagonal
-    //    block (tile 0) and factors it; warp 4, which shares its SM
-    //    sub-partition, stays idle so that the latency-bound factorization
-    //    runs alone there; the other six warps update the remaining blocks
+    // 3. trailing update with look-ahead: warps 0-3 (one per SM
+    //    sub-partition) update the next diagonal block (tile 0), 8 rows
+    //    each, and warp 0 factors it as soon as the four are done (named
+    //    barrier 1: warps 1-3 arrive without waiting); warps 1-7 update the
+    //    remaining blocks
     const int nt = np - 1 - p, ntile = nt * (nt + 1) / 2;
     if (ntile > 0) {
-      if (warp == 0) {
-        ch_syrk_tile(P, p, sp, np, 0);
-        __syncwarp();
-        ch_factor_diag(P, p + 1, sp, s, shift, rdiag, &bad);
-      } else if (warp != 4) {
-        const int wi = warp < 4 ? warp - 1 : warp - 2;
-        for (int ti = 1 + wi; ti < ntile; ti += 6) ch_syrk_tile(P, p, sp, np, ti);
+      if (warp < 4) {
+        ch_syrk_diag_rows(P, p, sp, warp);
+        if (warp == 0) {
+          asm volatile("bar.sync 1, 128;\n" ::: "memory");
+          ch_factor_diag(P, p + 1, sp, s, shift, rdiag, &bad);
+        } else {
+          asm volatile("bar.arrive 1, 128;\n" ::: "memory");
+        }
       }
+      if (warp != 0)
+        for (int ti = warp; ti < ntile; ti += CH_NT / 32 - 1) ch_syrk_tile(P, p, sp, np, ti);
     }
     __syncthreads();
   }
