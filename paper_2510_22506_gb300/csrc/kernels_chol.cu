@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
   __shared__ int bad;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = ch_npan(s), sp = 32 * np;
-  const float shift = (float)(lam * (c0 + 2.0 * c1 * cospi(2.0 * (double)g / (double)I)) + rho);
+  // the shift c_g = lam mu_g + rho (Eq. 6), computed in FP64 by one thread
+  // (FP64 is scarce on this GPU) and read by all after the loads
+  __shared__ float shift_s;
   // G into the panels.  G is symmetric, so column col of panel q (rows
   // 32 q .. s - 1) is the row segment G[col][32 q .. s).  With tensor maps
   // (s % 4 == 0): one TMA box per panel (zero outside G), then the identity
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
   // the pivots in step 1.
   __shared__ __align__(8) uint64_t gbar;
   if (tid == 0) bad = 0;
+  if (tid == 32) shift_s = (float)(lam * (c0 + 2.0 * c1 * cospi(2.0 * (double)g / (double)I)) + rho);
   if (maps.on && (ch_su32(P) & 127u) == 0) {
     if (tid == 0) {
       ch_bar_init(&gbar);
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(CH_NT) k_chol_factor(const float* __restrict__
     }
   }
   __syncthreads();
+  const float shift = shift_s;
   if (warp == 0) ch_factor_diag(P, 0, sp, s, shift, rdiag, &bad);
   __syncthreads();
   for (int p = 0; p < np; ++p) {
