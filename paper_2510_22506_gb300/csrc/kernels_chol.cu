@@ -124,18 +124,32 @@ __device__ __noinline__ void ch_factor_diag(float* __restrict__ P, int p, int sp
     if (c == lane && 32 * p + c < s) d[c] += shift;  // G + c I
   }
   bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    float piv = __shfl_sync(CH_FULL, d[j], j);
+  // Column j's pivot and 1 / sqrt(pivot) are formed as soon as column j - 1
+  // has updated it, ahead of the rest of column j - 1's update, so that the
+  // chain from pivot to pivot is not queued behind those shuffles.
+  auto pivot = [&](float v, float& piv, float& rs) {
+    piv = v;
     if (!(piv > 0.0f)) {
       ok = false;
       piv = 1.0f;
     }
-    const float rs = rsqrtf(piv);
-    d[j] = (lane == j) ? piv * rs : d[j] * rs;
+    rs = rsqrtf(piv);
+  };
+  float piv, rs;
+  pivot(__shfl_sync(CH_FULL, d[0], 0), piv, rs);
 #pragma unroll
-    for (int c = j + 1; c < 32; ++c) d[c] = fmaf(-d[j], __shfl_sync(CH_FULL, d[j], c), d[c]);
+  for (int j = 0; j < 32; ++j) {
+    d[j] = (lane == j) ? piv * rs : d[j] * rs;
     if (lane == 0) rdiag[j] = rs;
+    float npiv = 1.0f, nrs = 1.0f;
+    if (j + 1 < 32) {
+      d[j + 1] = fmaf(-d[j], __shfl_sync(CH_FULL, d[j], j + 1), d[j + 1]);
+      pivot(__shfl_sync(CH_FULL, d[j + 1], j + 1), npiv, nrs);
+    }
+#pragma unroll
+    for (int c = j + 2; c < 32; ++c) d[c] = fmaf(-d[j], __shfl_sync(CH_FULL, d[j], c), d[c]);
+    piv = npiv;
+    rs = nrs;
   }
 #pragma unroll
   for (int c = 0; c < 32; ++c)
