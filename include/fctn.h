@@ -148,7 +148,7 @@ typedef struct fctn_params {
                              0 = built-in rules.  bit 0: CUDA-core products in TF32 /
                              BF16 too; bits 1-2: pipeline stages of X_(1) M_1^T (rule,
                              2, 4, 6); bits 3-4: its K split over about (304, 152, 608,
-                             76) CTAs; bits 5-6: K split of the CUDA-core contractions
+                             76) CTAs; bits 5-6: K split of the table-driven contractions
                              over about (304, 152, 608, 1) CTAs; bit 7: programmatic
                              dependent launches in the chain of the Cholesky solve.
                              Only the summation order of the contractions changes

@@ -1100,7 +1100,8 @@ int plan_route(fctn_handle* h, std::vector<int>* tabs) {
   r.P0 = h->Pk[0];
   int rc = FCTN_OK;
   std::vector<int> t0;  // tables of this plan (appended at the end, or dropped)
-  // tile code (fctn_autotune_tiles): K-split target of the CUDA-core contractions
+  // tile code (fctn_autotune_tiles): K-split target of the table-driven
+  // contractions (CUDA-core and tensor-core)
   static const int kSgSplit[4] = {0, 152, 4 * 152, 1};
   const int sgs = kSgSplit[(h->p.tile_code >> 5) & 3];
   auto track = [](int64_t* mx, int64_t v) { *mx = v > *mx ? v : *mx; };
@@ -2560,7 +2561,7 @@ int fctn_autotune_tiles(const fctn_params* p, const void* Y, const uint8_t* mask
                         int where, const int32_t* cand, int ncand, int sweeps, void* cuda_stream, int32_t* best,
                         double* ms_out) {
   // the built-in rule; CUDA-core products; 2 / 4 pipeline stages; K split of
-  // X_(1) M_1^T over 152 / 608 CTAs; K split of the CUDA-core contractions
+  // X_(1) M_1^T over 152 / 608 CTAs; K split of the table-driven contractions
   // over 152 / 608 CTAs / none; programmatic dependent launches in the solve
   // chain, alone and with the two K splits over 152 CTAs
   static const int32_t builtin[12] = {0, 1, 2, 4, 8, 16, 32, 64, 96, 128, 136, 160};
