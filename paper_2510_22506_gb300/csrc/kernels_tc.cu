@@ -436,11 +436,23 @@ int tc_plan(const PairPlan& p, const GramPlan& g, int precision, TcPlan* tp) {
 void launch_gram_tc(const PairPlan& p, const float* L, const float* R, const float* X, float* part,
                     const GramPlan& g, const TcPlan& tp, int precision, float* Mout, int* status, cudaStream_t st) {
   dim3 grid(tp.n_groups, 1, g.ksplit);
+  // The shared-memory limit is set once to the most any plan asks for (tc_plan
+  // keeps tp.smem <= 200 KB), not to this launch's size: a launch recorded in
+  // a graph with a larger size than a later launch set the limit to would no
+  // longer fit the function's limit when it is launched on its own (as a
+  // profiler replaying graph nodes one by one does).
+  static bool attr[2] = {false, false};
   if (precision == FCTN_BF16) {
-    cudaFuncSetAttribute(k_gram_tc<OpBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    if (!attr[1]) {
+      cudaFuncSetAttribute(k_gram_tc<OpBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr[1] = true;
+    }
     k_gram_tc<OpBF16><<<grid, TC_THREADS, tp.smem, st>>>(p, L, R, X, part, g, tp, Mout, status);
   } else {
-    cudaFuncSetAttribute(k_gram_tc<OpTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    if (!attr[0]) {
+      cudaFuncSetAttribute(k_gram_tc<OpTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr[0] = true;
+    }
     k_gram_tc<OpTF32><<<grid, TC_THREADS, tp.smem, st>>>(p, L, R, X, part, g, tp, Mout, status);
   }
 }
